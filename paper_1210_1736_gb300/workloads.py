@@ -1,0 +1,114 @@
+"""Named synthetic workloads: grid layout (cells, radii, flattening) plus seeded
+particles.  Pure data and sampling; no particle-mesh arithmetic.
+
+A geometry is given as ``(nx, ny, nz, R, q)``: nx*ny*nz active cells whose
+usable part spans the diameter 2R in x and y, with cells flattened by q in z.
+Each side (library and oracle) derives the cell lengths itself.
+
+Workloads
+---------
+plummer32   65,536-particle Plummer sphere (M = a = G = 1) truncated at
+            r = 3.375 a, single 32^3 grid of cell length 0.25 (grid side 8a),
+            FP64, dt = 0.01, 10 steps.
+galaxy_1m   disc (400k) + Hernquist bulge (100k) + truncated NFW halo (500k);
+            grids: coarse 128^3 (R_sys = 32), medium 128^3 flattened q = 1/4
+            (R_out = 6), fine 128x128x32 (R_core = 1.5); dt = 0.01.
+galaxy_small  the same model scaled to 48k particles on 32^3 / 32^3 / 32x32x8
+            grids (fast enough for the oracle inside a test).
+merger_4m   galaxy scaled to 4M particles plus a 100k Plummer satellite; six
+            geometries (galaxy 128^3, 128^3, 256x256x32; satellite 64^3 x 3).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import synth
+
+GALAXY_RADII = dict(r_core=1.5, r_out=6.0, r_sys=32.0)
+
+
+def _galaxy_spec(n_c, n_m, n_f, q_m=0.25, centre=(0.0, 0.0, 0.0)):
+    R = GALAXY_RADII
+    return dict(
+        coarse=(n_c, n_c, n_c, R["r_sys"], 1.0),
+        medium=(n_m, n_m, n_m, R["r_out"], q_m),
+        fine=(n_f[0], n_f[1], n_f[2], R["r_core"], 1.0),
+        r_core=R["r_core"], r_out=R["r_out"], centre=centre, recentre=True)
+
+
+def plummer32(seed_id=0):
+    rng = synth.rng_for(seed_id, 0)
+    pos, vel, m = synth.plummer(65536, rng, M=1.0, a=1.0, r_trunc=3.375)
+    n = pos.shape[1]
+    return dict(
+        name="plummer32", precision="fp64", dt=0.01, steps=10,
+        system=dict(r_sys=3.5, sys_centre=(0.0, 0.0, 0.0), G=1.0, h000=1.0),
+        galaxies=[dict(coarse=(32, 32, 32, 3.5, 1.0), medium=None, fine=None,
+                       r_core=0.0, r_out=0.0, centre=(0.0, 0.0, 0.0), recentre=False)],
+        pos=pos, vel=vel, m=m, gal=np.zeros(n, dtype=np.int32))
+
+
+def _galaxy_particles(n_total, seed_id):
+    nd, nb = int(round(0.4 * n_total)), int(round(0.1 * n_total))
+    nh = n_total - nd - nb
+    pos, vel, m = synth.galaxy(nd, nb, nh, synth.rng_for(seed_id, 1),
+                               synth.rng_for(seed_id, 2), synth.rng_for(seed_id, 3))
+    return pos, vel, m
+
+
+def galaxy(n_total=1_000_000, n_c=128, n_m=128, n_f=(128, 128, 32), seed_id=1,
+           precision="fp32", name=None):
+    pos, vel, m = _galaxy_particles(n_total, seed_id)
+    pos, vel, m = synth.scramble(synth.rng_for(seed_id, 9), pos, vel, m)
+    n = pos.shape[1]
+    return dict(
+        name=name or f"galaxy_{n_total}", precision=precision, dt=0.01, steps=100,
+        system=dict(r_sys=GALAXY_RADII["r_sys"], sys_centre=(0.0, 0.0, 0.0), G=1.0, h000=1.0),
+        galaxies=[_galaxy_spec(n_c, n_m, n_f)],
+        pos=pos, vel=vel, m=m, gal=np.zeros(n, dtype=np.int32))
+
+
+def galaxy_1m(precision="fp32"):
+    return galaxy(1_000_000, 128, 128, (128, 128, 32), seed_id=1, precision=precision,
+                  name="galaxy_1m")
+
+
+def galaxy_small(precision="fp32", n_total=48_000, seed_id=11):
+    return galaxy(n_total, 32, 32, (32, 32, 8), seed_id=seed_id, precision=precision,
+                  name="galaxy_small")
+
+
+def merger(n_gal=4_000_000, n_sat=100_000, grids=((128,), (128,), (256, 256, 32), (64,)),
+           seed_id=2, precision="fp32", name="merger_4m"):
+    """Galaxy plus a Plummer satellite (M = 0.1 M_disc, a = 0.05) at apocentre
+    8 R_d on an orbit of eccentricity 0.5, inclined 30 degrees; the apocentre
+    speed is the point-mass value sqrt(G M(<8) (1 - e) / 8)."""
+    pos, vel, m = _galaxy_particles(n_gal, seed_id)
+    ps, vs, ms = synth.plummer(n_sat, synth.rng_for(seed_id, 4), M=0.1, a=0.05, r_trunc=0.5)
+    R_A, e, inc = 8.0, 0.5, np.deg2rad(30.0)
+    m_enc = float(m[np.linalg.norm(pos, axis=0) < R_A].sum())
+    v_apo = np.sqrt(m_enc * (1 - e) / R_A)
+    ps = ps + np.array([[R_A], [0.0], [0.0]])
+    vs = vs + np.array([[0.0], [v_apo * np.cos(inc)], [v_apo * np.sin(inc)]])
+    n_c = grids[0][0]
+    n_m = grids[1][0]
+    n_f = grids[2]
+    ns = grids[3][0]
+    sat = dict(coarse=(ns, ns, ns, GALAXY_RADII["r_sys"], 1.0),
+               medium=(ns, ns, ns, 0.5, 1.0), fine=(ns, ns, ns, 0.125, 1.0),
+               r_core=0.125, r_out=0.5, centre=(R_A, 0.0, 0.0), recentre=True)
+    allpos = np.concatenate([pos, ps], axis=1)
+    allvel = np.concatenate([vel, vs], axis=1)
+    allm = np.concatenate([m, ms])
+    gal = np.concatenate([np.zeros(pos.shape[1], np.int32), np.ones(n_sat, np.int32)])
+    allpos, allvel, allm, gal = synth.scramble(synth.rng_for(seed_id, 9), allpos, allvel, allm, gal)
+    return dict(
+        name=name, precision=precision, dt=0.01, steps=500,
+        system=dict(r_sys=GALAXY_RADII["r_sys"], sys_centre=(0.0, 0.0, 0.0), G=1.0, h000=1.0),
+        galaxies=[_galaxy_spec(n_c, n_m, n_f), sat],
+        pos=allpos, vel=allvel, m=allm, gal=gal)
+
+
+def mass_bound(m):
+    """Upper bound on sum |m| handed to both sides (fixes the fixed-point scale)."""
+    return float(np.abs(np.asarray(m, dtype=np.float64)).sum())

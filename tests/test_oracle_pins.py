@@ -1,0 +1,309 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test targets a different way the oracle could be wrong: the grid geometry
+(Table 3), the admissible flattening (Sec. 2.2.2), the doubled-grid FFT against
+the plain sum of Eq. (eq:poisson), the symmetry of H-hat, Eq. (eqn:diff)
+against Newton's law and against zero self-force, momentum conservation of the
+central difference, second-order convergence and the Poisson equation for a
+smooth body with a closed-form field, the leap-frog map's closed form, and the
+mass bookkeeping of the five grids.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+RNG = np.random.default_rng(1210_1736)
+
+
+def _read_table(path):
+    rows = []
+    for line in open(path):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        rows.append(line.split())
+    return rows
+
+
+# --------------------------------------------------------------- geometry ---
+
+def test_table3_vertical_resolution(golden_dir):
+    rows = _read_table(os.path.join(golden_dir, "table3_vertical_resolution.txt"))
+    Ns = [64, 128, 256, 512]
+    radii = dict(_read_table(os.path.join(golden_dir, "sec41_grid_radii.txt")))
+    r_core, r_out, r_sys = (float(radii[k]) * 1000 for k in ("r_core", "r_out", "r_sys"))
+    checked = 0
+    for row in rows:
+        q = float(row[0])
+        for N, printed in zip(Ns, row[1:]):
+            lz = O.cell_length(r_out, N, q)
+            if printed == "-":
+                assert q < O.q_crit(r_core, r_out, r_sys, N)
+                continue
+            assert q >= O.q_crit(r_core, r_out, r_sys, N) - 1e-12
+            p = int(printed)
+            assert p in (math.floor(lz), round(lz)), (q, N, lz, p)
+            checked += 1
+    assert checked == 15
+
+
+def test_qcrit_values():
+    assert O.q_crit(3.5, 28, 105, 64) == pytest.approx(0.25)
+    assert O.q_crit(3.5, 28, 105, 128) == pytest.approx(0.125)
+    assert O.q_crit(3.5, 28, 105, 256) == pytest.approx(0.125)
+
+
+def test_fixed_shift_headroom():
+    for mb in [1.0, 0.75, 11.35, 1e-3, 2.0**20, 3.0]:
+        s = O.fixed_shift(mb)
+        assert mb * 2.0**s <= 2.0**62
+        assert mb * 2.0**(s + 1) > 2.0**62
+
+
+# ---------------------------------------------------- cell assignment ---
+
+def test_cell_index_tie_break_and_box():
+    l = 0.25
+    n = 32
+    # u = x/l + 16; x = (k + 0.5) l sits on a cell edge and goes up (floor(u + 1/2)).
+    x = np.array([0.0, 0.5 * l, -0.5 * l, 1.49 * l, (n / 2 - 2.5) * l, -(n / 2 - 1.5) * l])
+    a = O.cell_index(O.offset_f32(x, 0.0), l, n)
+    assert list(a) == [16, 17, 16, 17, n - 2, 2]
+    assert list(O.in_box(a, n)) == [True, True, True, True, False, True]
+
+
+# ------------------------------------------------------- potential ---
+
+def _random_rho(g, npart):
+    rho = np.zeros(g.shape)
+    idx = (RNG.integers(0, g.nz, npart), RNG.integers(0, g.ny, npart), RNG.integers(0, g.nx, npart))
+    np.add.at(rho, idx, RNG.uniform(0.1, 2.0, npart))
+    return rho
+
+
+@pytest.mark.parametrize("shape,q", [((8, 8, 8), 1.0), ((8, 8, 4), 0.5), ((16, 8, 8), 0.25),
+                                     ((8, 16, 4), 1.0)])
+def test_fft_equals_direct_sum(shape, q):
+    """Sec. 2.1: the doubled-grid FFT convolution is the exact isolated sum."""
+    nx, ny, nz = shape
+    g = O.Geometry(nx, ny, nz, 0.3, 0.3 * q)
+    rho = _random_rho(g, 64)
+    a = O.potential_fft(rho, g, 1.7, 1.0)
+    b = O.potential_direct(rho, g, 1.7, 1.0)
+    assert np.max(np.abs(a - b)) <= 1e-12 * np.max(np.abs(b))
+
+
+def test_single_mass_closed_form():
+    """One cell of mass m: Phi[a] = G m / (distance between cell centres)."""
+    g = O.Geometry(16, 8, 8, 0.2, 0.1)
+    rho = np.zeros(g.shape)
+    p = (3, 5, 11)  # z, y, x
+    rho[p] = 2.5
+    phi = O.potential_fft(rho, g, 1.0, 1.0)
+    z, y, x = np.meshgrid(np.arange(8), np.arange(8), np.arange(16), indexing="ij")
+    dist = np.sqrt(((x - p[2]) * 0.2) ** 2 + ((y - p[1]) * 0.2) ** 2 + ((z - p[0]) * 0.1) ** 2)
+    expect = np.where(dist > 0, 2.5 / np.where(dist > 0, dist, 1), 2.5 / 0.2)
+    assert np.allclose(phi, expect, rtol=1e-12, atol=0)
+
+
+def test_green_hat_real_and_even():
+    """Sec. 2.1: H-hat shares the symmetries of H (real, even)."""
+    g = O.Geometry(8, 8, 4, 1.0, 0.25)
+    Hf = np.fft.fftn(O.green_doubled(g, 1.0))
+    assert np.max(np.abs(Hf.imag)) < 1e-11 * np.max(np.abs(Hf.real))
+    flip = Hf[(-np.arange(8)) % 8][:, (-np.arange(16)) % 16][:, :, (-np.arange(16)) % 16]
+    assert np.allclose(Hf, flip, rtol=0, atol=1e-11 * np.max(np.abs(Hf)))
+
+
+# ---------------------------------------------------------- forces ---
+
+def _one_grid_system(g, r_sys=100.0):
+    return O.System(galaxies=[O.Galaxy(coarse=g)], r_sys=r_sys, mass_bound=16.0)
+
+
+def _state(pos, m):
+    n = pos.shape[1]
+    return O.State(pos=pos, vel=np.zeros_like(pos), m=m, gal=np.zeros(n, np.int64),
+                   flags=np.zeros(n, np.int64), centres=np.zeros((1, 3)))
+
+
+def _acc(st, system):
+    flags, own = O.classify(st, system)
+    rho, flags, s = O.deposit(st, system, flags, own)
+    phi = O.solve_all(rho, system, s)
+    return O.accelerations(st, system, phi, flags)
+
+
+def test_zero_self_force():
+    """h000 = 1 on a cubic grid: an isolated particle anywhere in its cell
+    feels no force from its own mass (reading of the self-term)."""
+    g = O.Geometry(16, 16, 16, 0.5, 0.5)
+    sysm = _one_grid_system(g)
+    for _ in range(5):
+        pos = RNG.uniform(-2.0, 2.0, (3, 1))
+        acc = _acc(_state(pos, np.array([1.0])), sysm)
+        assert np.max(np.abs(acc)) < 1e-13
+
+
+@pytest.mark.parametrize("q", [1.0, 0.5])
+def test_newton_far_field(q):
+    """A point mass at a cell centre attracts a distant particle with G m / d^2
+    along the joining line (error O(l^2/d^2) of the central difference)."""
+    l = 0.05
+    g = O.Geometry(64, 64, int(64 / q), l, q * l)
+    sysm = _one_grid_system(g)
+    src = np.array([0.0, 0.0, 0.0])
+    rng = np.random.default_rng(7)
+    for _ in range(4):
+        d = rng.normal(size=3)
+        d = d / np.linalg.norm(d) * 1.2
+        tgt = src + d
+        pos = np.stack([src, tgt], axis=1)
+        st = _state(pos, np.array([3.0, 1e-6]))
+        acc = _acc(st, sysm)[:, 1]
+        newton = -3.0 * d / np.linalg.norm(d) ** 3
+        assert np.linalg.norm(acc - newton) < 0.01 * np.linalg.norm(newton)
+
+
+def test_momentum_conservation_central_difference():
+    """With every particle on its cell centre only the central difference of
+    Eq. (eqn:diff) acts; it is antisymmetric and commutes with the symmetric
+    convolution, so sum m a = 0 to rounding."""
+    g = O.Geometry(32, 32, 16, 0.2, 0.1)
+    sysm = _one_grid_system(g)
+    n = 300
+    cells = np.stack([RNG.integers(4, 28, n), RNG.integers(4, 28, n), RNG.integers(3, 13, n)])
+    pos = np.stack([(cells[0] - 16) * 0.2, (cells[1] - 16) * 0.2, (cells[2] - 8) * 0.1])
+    m = RNG.uniform(0.5, 1.5, n)
+    acc = _acc(_state(pos, m), sysm)
+    tot = (m * acc).sum(axis=1)
+    scale = (m * np.abs(acc)).sum()
+    assert np.max(np.abs(tot)) < 1e-13 * scale
+
+
+def _poly_body(n, R=1.0, box=3.0):
+    """Cell masses of rho = (1 - r^2/R^2)^2 (midpoint rule) on an n^3 grid of
+    side `box`, and its closed-form acceleration a(r) = -G M(r)/r^2."""
+    l = box / n
+    c = (np.arange(n) - n // 2) * l
+    z, y, x = np.meshgrid(c, c, c, indexing="ij")
+    r = np.sqrt(x * x + y * y + z * z)
+    rho = np.where(r < R, (1 - (r / R) ** 2) ** 2, 0.0)
+    g = O.Geometry(n, n, n, l, l)
+    Mr = 4 * np.pi * (r**3 / 3 - 2 * r**5 / (5 * R**2) + r**7 / (7 * R**4))
+    Mr = np.where(r < R, Mr, 4 * np.pi * (R**3 / 3 - 2 * R**3 / 5 + R**3 / 7))
+    return g, rho * l**3, rho, (x, y, z, r, Mr)
+
+
+def _grid_force(g, masses):
+    phi = O.potential_fft(masses, g, 1.0, 1.0)
+    n = g.nx
+    k, j, i = np.meshgrid(np.arange(2, n - 2), np.arange(2, n - 2), np.arange(2, n - 2), indexing="ij")
+    delta = np.zeros((3,) + i.shape)
+    return phi, O.accel_from_grid(phi, g, i, j, k, delta), (k, j, i)
+
+
+def test_smooth_body_second_order_and_poisson():
+    """Closed-form field of a smooth body: the force error drops ~4x when l
+    halves, and the 7-point Laplacian of Phi gives -4 pi G rho (Eq. eq:poisson
+    is Poisson's equation with Phi = -potential)."""
+    errs = []
+    for n in (24, 48):
+        g, masses, rho, (x, y, z, r, Mr) = _poly_body(n)
+        phi, acc, (k, j, i) = _grid_force(g, masses)
+        rr = r[k, j, i]
+        sel = (rr > 0.15) & (rr < 0.8)
+        exact = -Mr[k, j, i] / np.maximum(rr, 1e-30) ** 3 * np.stack([x[k, j, i], y[k, j, i], z[k, j, i]])
+        e = np.sqrt(np.sum((acc - exact)[:, sel] ** 2) / np.sum(exact[:, sel] ** 2))
+        errs.append(e)
+        l = g.l_xy
+        lap = (phi[k, j, i + 1] + phi[k, j, i - 1] + phi[k, j + 1, i] + phi[k, j - 1, i]
+               + phi[k + 1, j, i] + phi[k - 1, j, i] - 6 * phi[k, j, i]) / l**2
+        inner = rr < 0.6
+        rel = np.abs(lap[inner] + 4 * np.pi * rho[k, j, i][inner]) / (4 * np.pi)
+        assert rel.max() < (0.06 if n == 24 else 0.02)
+    assert errs[1] < 0.02, errs
+    assert errs[0] / errs[1] > 3.0
+
+
+# -------------------------------------------------------- leap-frog ---
+
+def test_leapfrog_closed_form_harmonic():
+    """Kick-drift on a = -w^2 x is the linear map whose orbit is
+    x_n = A cos(n theta) + B sin(n theta) with cos(theta) = 1 - (w dt)^2 / 2."""
+    w, dt = 1.3, 0.05
+    x = np.array([[0.7]])
+    v = np.array([[0.2]])            # v(-dt/2)
+    live = np.array([True])
+    xs = [x[0, 0]]
+    for _ in range(400):
+        v = O.kick(v, -w * w * x, dt, live)
+        x = O.drift(x, v, dt, live)
+        xs.append(x[0, 0])
+    th = math.acos(1 - (w * dt) ** 2 / 2)
+    x0, x1 = xs[0], xs[1]
+    A = x0
+    B = (x1 - A * math.cos(th)) / math.sin(th)
+    n = np.arange(len(xs))
+    assert np.allclose(xs, A * np.cos(n * th) + B * np.sin(n * th), rtol=0, atol=1e-12)
+
+
+# ------------------------------------------- nested grids, mass sets ---
+
+def _nested_plummer(npart=60000, seed=3):
+    from paper_1210_1736_gb300 import synth
+    from paper_1210_1736_gb300.workloads import mass_bound
+    pos, vel, m = synth.plummer(npart, np.random.default_rng(seed), M=1.0, a=0.4, r_trunc=4.0)
+    fine = O.Geometry(32, 32, 32, O.cell_length(0.6, 32), O.cell_length(0.6, 32))
+    med = O.Geometry(32, 32, 32, O.cell_length(1.6, 32), 0.5 * O.cell_length(1.6, 32))
+    coarse = O.Geometry(32, 32, 32, O.cell_length(6.0, 32), O.cell_length(6.0, 32))
+    gal = O.Galaxy(coarse=coarse, medium=med, fine=fine, r_core=0.6, r_out=1.6)
+    system = O.System(galaxies=[gal], r_sys=6.0, mass_bound=mass_bound(m))
+    st = O.State(pos=pos, vel=vel, m=m, gal=np.zeros(npart, np.int64),
+                 flags=np.zeros(npart, np.int64), centres=np.zeros((1, 3)))
+    return system, st
+
+
+def test_mass_set_bookkeeping():
+    system, st = _nested_plummer(20000)
+    flags, own = O.classify(st, system)
+    rho, flags, s = O.deposit(st, system, flags, own)
+    live = (flags & 1) == 0
+    q = O.quantize_mass(st.m, s)
+    r = rho[0]
+    assert r[1].sum() == r[2].sum() == q[live & (own == 0)].sum()
+    assert r[3].sum() == q[live & (own == 1)].sum()
+    assert r[4].sum() == r[1].sum() + r[3].sum()
+    assert r[1].sum() + r[3].sum() + r[5].sum() == q[live].sum()
+    assert (own[live] == 0).sum() > 1000 and (own[live] == 1).sum() > 1000 and (own[live] == 2).sum() > 100
+
+
+def test_nested_force_matches_plummer_field():
+    """The combination rule (Sec. 2.1) gives the Plummer field everywhere:
+    core, shell and outer particles each within a few per cent RMS."""
+    system, st = _nested_plummer(60000)
+    acc = _acc(st, system)
+    flags, own = O.classify(st, system)
+    r = np.linalg.norm(st.pos, axis=0)
+    a = 0.4
+    # M = 1 Plummer truncated at r = 4: inside, the field of the full sphere.
+    exact = -st.pos / (r * r + a * a) ** 1.5
+    live = (flags & 1) == 0
+    for reg, rmin in ((0, 0.15), (1, 0.7), (2, 1.8)):
+        sel = live & (own == reg) & (r > rmin) & (r < 3.5)
+        err = np.sqrt(np.sum((acc - exact)[:, sel] ** 2) / np.sum(exact[:, sel] ** 2))
+        assert err < 0.05, (reg, err)
+
+
+def test_planted_mistake_in_combination_rule_is_caught(monkeypatch):
+    """Swapping the shell combination (2+3+5 -> 4+5) in the oracle breaks the
+    nested-field pin: the pins can see a wrong grid choice."""
+    orig = O.pm_oracle.combination
+    monkeypatch.setattr(O.pm_oracle, "combination",
+                        lambda reg: (4, 5) if reg == 1 else orig(reg))
+    with pytest.raises(AssertionError):
+        test_nested_force_matches_plummer_field()
