@@ -1,0 +1,177 @@
+/*
+ * pm.h - C ABI of the GB300 nested-grid particle-mesh gravity step
+ *        (Superbox-10: Bien, Brandt & Just 2012, MNRAS).
+ *
+ * One step of the method (Sec. 2.1 and 2.2 of the paper), per galaxy and per
+ * grid level (grids 1-5: fine, medium x2, coarse x2):
+ *   recentre grids 1-3, assign mass to cells (Eq. eqn:cell), zero-pad to the
+ *   doubled isolated-boundary grid, forward 3D real FFT, multiply by the
+ *   precomputed Green's function H-hat (Eq. eqn:greens, eq:symmetry), inverse
+ *   FFT (Eq. eq:poisson evaluated exactly), finite-difference forces with
+ *   first-order Taylor interpolation (Eq. eqn:diff) summed by the potential
+ *   combination rule, and the leap-frog kick-drift.
+ *
+ * Conventions shared by every call:
+ *   - Units: Phi = +G sum rho H is positive; the acceleration is +grad Phi.
+ *   - Grid arrays are laid out [z][y][x] with x fastest.
+ *   - Particle arrays are device memory owned by the caller, structure of
+ *     arrays, float for PM_FP32 contexts and double for PM_FP64 contexts.
+ *   - Every call is asynchronous on the context's stream (pm_set_stream)
+ *     unless stated; only the pm_get_* and pm_diagnostics calls synchronise.
+ *   - Every call returns PM_OK (0) or a negative PM_E_* status and never
+ *     throws; pm_last_error() gives a message for the calling thread.
+ *   - Particles flagged lost (PM_FLAG_LOST) contribute nothing and are not
+ *     moved; the flag is set by pm_deposit and never cleared by the library.
+ */
+#ifndef PM_H
+#define PM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PM_OK           0
+#define PM_E_ARG       -1   /* invalid argument, size or pointer            */
+#define PM_E_QCRIT     -2   /* medium-grid flattening below q_crit          */
+#define PM_E_NESTING   -3   /* grid 1 not inside grid 2, or grid 2 not inside grid 4 */
+#define PM_E_OVERFLOW  -4   /* mass bound leaves no fixed-point headroom    */
+#define PM_E_CUDA      -5   /* a CUDA runtime call failed                   */
+#define PM_E_STATE     -6   /* call not valid in the context's state        */
+
+#define PM_FP32 1
+#define PM_FP64 2
+
+#define PM_FLAG_LOST 1u
+
+#define PM_MAX_GALAXIES 8
+
+typedef struct pm_ctx pm_ctx;
+
+/* One grid (Sec. 2.1, Eq. eqn:cell; flattening Sec. 2.2.2): nx*ny*nz active
+ * cells, each a power of two in [8, 256]; cell lengths l_xy (x and y) and
+ * l_z = q*l_xy.  A geometry with nx == 0 is absent. */
+typedef struct {
+    int32_t nx, ny, nz;
+    double  l_xy, l_z;
+} pm_geometry;
+
+/* One galaxy's grids (Sec. 2.1): fine = grid 1, medium = grids 2 and 3,
+ * coarse = grids 4 and 5.  Grids 1-3 are centred on `centre` and, when
+ * `recentre` is nonzero, move each step to the centre of mass of the
+ * galaxy's live particles within r_core of the previous centre.  Grids 4-5
+ * are centred on the system centre.  Regions: core r < r_core (and inside
+ * grids 1 and 2), shell r < r_out (inside grid 2), outer otherwise.  A galaxy
+ * without medium grid has only grid 5 (a plain single-grid PM). */
+typedef struct {
+    pm_geometry coarse, medium, fine;
+    double  r_core, r_out;
+    double  centre[3];
+    int32_t recentre;
+} pm_galaxy;
+
+/* The whole system.  Particles farther than r_sys from sys_centre, or outside
+ * the usable box (two empty boundary cells, Sec. 2.1) of any coarse grid,
+ * are lost.  mass_bound >= sum |m| fixes the 64-bit fixed-point mass scale
+ * 2^s with s = 62 - ceil(log2(mass_bound)).  h000 is the Green's function
+ * self-term H(0,0,0) in units of 1/l_xy (the paper leaves it open; 1 gives
+ * zero self-force on cubic cells). */
+typedef struct {
+    int32_t precision;           /* PM_FP32 or PM_FP64                     */
+    int32_t ngal;                /* 1 .. PM_MAX_GALAXIES                   */
+    double  G, h000, r_sys;
+    double  sys_centre[3];
+    double  mass_bound;
+} pm_system;
+
+/* Caller-owned device arrays (pointers to float or double per precision). */
+typedef struct {
+    void *x, *y, *z, *vx, *vy, *vz, *m;
+    const int32_t *gal;          /* galaxy index of each particle          */
+    uint32_t *flags;             /* bit 0: lost                            */
+    int64_t n;                   /* number of particles, >= 0              */
+} pm_particles;
+
+/* Host helpers (no GPU needed). */
+/* Cell length of a grid whose N-4 usable cells span 2R, flattened by q
+ * (Sec. 2.1 boundary cells; Sec. 4.1 Table 3): 2 R q / (N - 4). */
+double pm_cell_length(double R, int32_t N, double q);
+/* Smallest admissible flattening of grids 2-3 (Sec. 2.2.2):
+ * max(R_core/R_out, 4/(N-4) * R_sys/R_out). */
+double pm_q_crit(double r_core, double r_out, double r_sys, int32_t N);
+/* Fixed-point shift s for a mass bound, or INT32_MIN if the bound is not
+ * positive and finite. */
+int32_t pm_fixed_shift(double mass_bound);
+/* Message of the last failing call on this thread ("" if none). */
+const char *pm_last_error(void);
+
+/* Builds every grid, its H-hat table (FP64 on the device, stored in the
+ * context precision) and all work buffers on the current CUDA device.
+ * `stream` is a cudaStream_t (NULL = legacy default stream) on which later
+ * calls are ordered.  Validates: powers of two, q >= q_crit for flattened
+ * medium grids (PM_E_QCRIT), grid 1 inside grid 2 inside grid 4
+ * (PM_E_NESTING), galaxies after the first not flattened (Sec. 2.2.2).
+ * Synchronises once.  *out is NULL on failure. */
+int pm_create_grids(const pm_system *sys, const pm_galaxy *gals, void *stream,
+                    pm_ctx **out);
+void pm_destroy(pm_ctx *ctx);
+int pm_set_stream(pm_ctx *ctx, void *stream);
+
+/* Step a1 (Sec. 2.1 recentring): move grids 1-3 of recentring galaxies to
+ * the centre of mass of their live particles within r_core (exact integer
+ * accumulation, order independent). */
+int pm_recentre(pm_ctx *ctx, const pm_particles *p);
+
+/* Steps a2-a3 (Eq. eqn:cell, Sec. 2.1 grids 1-5, Sec. 2.2.1 individual
+ * masses): classify every particle, set lost flags, and add its fixed-point
+ * mass to the int64 density of each grid it belongs to.  Densities are
+ * zeroed first; the result is bit-exact and independent of thread order. */
+int pm_deposit(pm_ctx *ctx, const pm_particles *p);
+
+/* Steps a4-a7 (Sec. 2.1): for every grid, zero-pad, forward real 3D FFT,
+ * multiply by H-hat, inverse FFT, keep the active region -> Phi. */
+int pm_solve(pm_ctx *ctx);
+
+/* Step a8 (Eq. eqn:diff + combination rule): acceleration of each particle
+ * into caller-owned device arrays ax, ay, az (zero for lost particles).
+ * Uses the potentials of the last pm_solve. */
+int pm_force(pm_ctx *ctx, const pm_particles *p, void *ax, void *ay, void *az);
+
+/* v += dt * a with a from the last pm_solve (leap-frog start: dt = -dt0/2). */
+int pm_kick(pm_ctx *ctx, const pm_particles *p, double dt);
+
+/* Steps a1-a9, nsteps times: recentre, deposit, solve, force and leap-frog
+ * kick-drift (Sec. 2.1): v(t+dt/2) = v(t-dt/2) + dt a(t);
+ * x(t+dt) = x(t) + dt v(t+dt/2).  The step is captured once as a CUDA graph
+ * per (particle arrays, n, dt) and replayed. */
+int pm_step(pm_ctx *ctx, const pm_particles *p, double dt, int32_t nsteps);
+
+/* Step a10 (energy and angular momentum, Sec. 6.4 quantities): recentre is
+ * not applied; deposit + solve at the current positions, then with
+ * v(t) = v(t-dt/2) + dt/2 a(t): out[0] = K = sum m v^2/2, out[1] = W =
+ * -1/2 sum m Phi(x), out[2] = K + W, out[3..5] = L = sum m x cross v,
+ * out[6] = number of live particles.  FP64 sums.  Synchronises. */
+int pm_diagnostics(pm_ctx *ctx, const pm_particles *p, double dt, double *out);
+
+/* Test and inspection hooks (synchronise).  set = 1..5 as in the paper. */
+int pm_get_density(pm_ctx *ctx, int32_t gal, int32_t set, int64_t *host_out);
+int pm_get_potential(pm_ctx *ctx, int32_t gal, int32_t set, void *host_out);
+int pm_get_centres(pm_ctx *ctx, double *host_out);          /* ngal*3 */
+int pm_set_centres(pm_ctx *ctx, const double *host_in);     /* ngal*3 */
+int pm_count_lost(pm_ctx *ctx, const pm_particles *p, int64_t *host_out);
+int pm_info(pm_ctx *ctx, int64_t *host_out);  /* [shift, nsets, ngeom, bytes] */
+
+/* Per-phase device time of the next `nsteps` steps, run without the graph,
+ * with CUDA events on the context's launch stream between phases:
+ * ms_out[0] recentre, [1] deposit (incl. zeroing), [2] x forward pass,
+ * [3] y forward pass, [4] z pass (forward, H-hat multiply, inverse),
+ * [5] y inverse pass, [6] x inverse pass, [7] force + kick-drift,
+ * [8] whole steps; each the total over the steps.  Synchronises. */
+int pm_step_timed(pm_ctx *ctx, const pm_particles *p, double dt, int32_t nsteps,
+                  float *ms_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PM_H */

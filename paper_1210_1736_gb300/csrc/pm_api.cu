@@ -1,0 +1,681 @@
+// C ABI of the nested-grid particle-mesh step (declared in include/pm.h).
+//
+// The context owns every grid buffer: per galaxy and mass set an int64
+// density, an FP32/FP64 spectrum work buffer ([z][y in 2ny][kx in nx+1]) and
+// the potential; per distinct geometry the H-hat octant.  Particle arrays are
+// the caller's.  All work is ordered on the caller's stream; pm_step replays a
+// CUDA graph of one full step captured on a private stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "pm.h"
+#include "pm_launch.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define PM_CK(call)                                                                                  \
+    do {                                                                                             \
+        cudaError_t e_ = (call);                                                                     \
+        if (e_ != cudaSuccess)                                                                       \
+            return fail(PM_E_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                        __LINE__);                                                                   \
+    } while (0)
+
+#define PM_TRY(expr)               \
+    do {                           \
+        int rc_ = (expr);          \
+        if (rc_ != PM_OK) return rc_; \
+    } while (0)
+
+bool pow2_in_range(int n) { return n >= 8 && n <= 256 && (n & (n - 1)) == 0; }
+
+bool geom_present(const pm_geometry &g) { return g.nx != 0; }
+
+bool geom_valid(const pm_geometry &g) {
+    return pow2_in_range(g.nx) && pow2_in_range(g.ny) && pow2_in_range(g.nz) && std::isfinite(g.l_xy) &&
+           std::isfinite(g.l_z) && g.l_xy > 0 && g.l_z > 0;
+}
+
+bool geom_equal(const pm_geometry &a, const pm_geometry &b) {
+    return a.nx == b.nx && a.ny == b.ny && a.nz == b.nz && a.l_xy == b.l_xy && a.l_z == b.l_z;
+}
+
+// Half extent of the usable box along x/y and z: (n/2 - 2) l.
+double ext_xy(const pm_geometry &g, int n) { return (n / 2 - 2) * g.l_xy; }
+double ext_z(const pm_geometry &g) { return (g.nz / 2 - 2) * g.l_z; }
+
+int ceil_log2(double v) {
+    int e;
+    double f = std::frexp(v, &e);
+    return (f == 0.5) ? e - 1 : e;
+}
+
+GeomK make_geomk(const pm_geometry &g) {
+    GeomK k;
+    std::memset(&k, 0, sizeof(k));
+    if (!geom_present(g)) return k;
+    k.nx = g.nx; k.ny = g.ny; k.nz = g.nz;
+    k.gxy = (float)(1.0 / g.l_xy);
+    k.gz = (float)(1.0 / g.l_z);
+    k.lxy = g.l_xy; k.lz = g.l_z;
+    k.c_gx = 1.0 / (2.0 * g.l_xy);
+    k.c_gz = 1.0 / (2.0 * g.l_z);
+    k.c_hxx = 1.0 / (g.l_xy * g.l_xy);
+    k.c_hzz = 1.0 / (g.l_z * g.l_z);
+    k.c_mxy = 1.0 / (4.0 * g.l_xy * g.l_xy);
+    k.c_mxz = 1.0 / (4.0 * g.l_xy * g.l_z);
+    return k;
+}
+
+struct GeoBuf {
+    pm_geometry g;
+    long long A, workN, hatN;
+    void *hhat = nullptr;
+    std::vector<std::pair<int, int>> sets;   // (galaxy, set index 0..4)
+};
+
+}  // namespace
+
+struct pm_ctx {
+    pm_system sys;
+    pm_galaxy gal[PM_MAX_GALAXIES];
+    int prec = PM_FP32;
+    size_t esz = 4;
+    int shift = 0;
+    double mscale = 1.0;
+    std::vector<GeoBuf> geos;
+    int set_geo[PM_MAX_GALAXIES][PM_SETS];
+    long long *rho[PM_MAX_GALAXIES][PM_SETS];
+    void *phi[PM_MAX_GALAXIES][PM_SETS];
+    void *work[PM_MAX_GALAXIES][PM_SETS];
+    long long *rho_all = nullptr;
+    size_t rho_bytes = 0;
+    SysK hs;
+    SysK *d_sys = nullptr;
+    double *d_cen = nullptr;
+    unsigned long long *d_csum = nullptr;
+    double *d_diag = nullptr;
+    unsigned long long *d_cnt = nullptr;
+    void *d_tw[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaStream_t user = nullptr;
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    pm_particles gkey;
+    double gdt = 0;
+    size_t bytes = 0;
+    std::vector<void *> allocs;
+    bool any_recentre = false;
+};
+
+namespace {
+
+int dev_alloc(pm_ctx *c, void **p, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) return fail(PM_E_CUDA, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    c->allocs.push_back(*p);
+    c->bytes += bytes;
+    return PM_OK;
+}
+
+int tw_index(int L) {
+    int i = 0;
+    while ((16 << i) < L) ++i;
+    return i;
+}
+
+template <typename T> PartK<T> part_k(const pm_particles *p) {
+    PartK<T> k;
+    k.x = (T *)p->x; k.y = (T *)p->y; k.z = (T *)p->z;
+    k.vx = (T *)p->vx; k.vy = (T *)p->vy; k.vz = (T *)p->vz;
+    k.m = (const T *)p->m;
+    k.gal = p->gal;
+    k.flags = p->flags;
+    k.n = p->n;
+    return k;
+}
+
+int check_particles(const pm_particles *p) {
+    if (!p) return fail(PM_E_ARG, "particles is NULL");
+    if (p->n < 0) return fail(PM_E_ARG, "negative particle count %lld", (long long)p->n);
+    if (p->n > 0 && (!p->x || !p->y || !p->z || !p->vx || !p->vy || !p->vz || !p->m || !p->gal || !p->flags))
+        return fail(PM_E_ARG, "a particle array pointer is NULL");
+    return PM_OK;
+}
+
+// --- H-hat: FP64 octant of H, three cosine sums, scaled into storage ---
+int build_hhat(pm_ctx *c, GeoBuf &gb) {
+    const pm_geometry &g = gb.g;
+    const int P = g.nx + 1, Q = g.ny + 1, R = g.nz + 1;
+    const long long n = (long long)P * Q * R;
+    double *h = nullptr, *t1 = nullptr, *cm = nullptr;
+    PM_CK(cudaMalloc(&h, n * sizeof(double)));
+    PM_CK(cudaMalloc(&t1, n * sizeof(double)));
+    const int nmax = std::max(P, std::max(Q, R));
+    PM_CK(cudaMalloc(&cm, (size_t)nmax * nmax * sizeof(double)));
+    std::vector<double> hm((size_t)nmax * nmax);
+    auto cosmat = [&](int nn) {   // w_i cos(pi m i / nn), m, i in [0, nn]
+        const int n1 = nn + 1;
+        for (int m = 0; m < n1; ++m)
+            for (int i = 0; i < n1; ++i) {
+                const long long r = ((long long)m * i) % (2LL * nn);
+                const double w = (i == 0 || i == nn) ? 1.0 : 2.0;
+                hm[(size_t)m * n1 + i] = w * std::cos(M_PI * (double)r / (double)nn);
+            }
+        return cudaMemcpyAsync(cm, hm.data(), (size_t)n1 * n1 * sizeof(double), cudaMemcpyHostToDevice, c->user);
+    };
+    cudaStream_t st = c->user;
+    PM_CK(pm_green_octant(h, g.nx, g.ny, g.nz, g.l_z / g.l_xy, c->sys.h000, st));
+    PM_CK(cosmat(g.nx));
+    PM_CK(pm_axis_transform(h, t1, cm, P, (long long)R * Q, 1, st));
+    PM_CK(cudaStreamSynchronize(st));
+    PM_CK(cosmat(g.ny));
+    PM_CK(pm_axis_transform(t1, h, cm, Q, R, P, st));
+    PM_CK(cudaStreamSynchronize(st));
+    PM_CK(cosmat(g.nz));
+    PM_CK(pm_axis_transform(h, t1, cm, R, 1, (long long)Q * P, st));
+    const double scale = c->sys.G / (g.l_xy * 8.0 * g.nx * g.ny * g.nz);
+    if (c->prec == PM_FP32) PM_CK(pm_store_hhat<float>(t1, (float *)gb.hhat, n, scale, st));
+    else PM_CK(pm_store_hhat<double>(t1, (double *)gb.hhat, n, scale, st));
+    PM_CK(cudaStreamSynchronize(st));
+    cudaFree(h);
+    cudaFree(t1);
+    cudaFree(cm);
+    return PM_OK;
+}
+
+template <typename T> int upload_twiddles(pm_ctx *c) {
+    typedef typename cplx_t<T>::type C;
+    for (int i = 0; i < 6; ++i) {
+        const int L = 16 << i;
+        std::vector<C> tw(L);
+        for (int m = 0; m < L; ++m) {
+            const double a = 2.0 * M_PI * (double)m / (double)L;
+            tw[m].x = (T)std::cos(a);
+            tw[m].y = (T)(-std::sin(a));
+        }
+        PM_TRY(dev_alloc(c, &c->d_tw[i], L * sizeof(C)));
+        PM_CK(cudaMemcpyAsync(c->d_tw[i], tw.data(), L * sizeof(C), cudaMemcpyHostToDevice, c->user));
+        PM_CK(cudaStreamSynchronize(c->user));
+    }
+    return PM_OK;
+}
+
+// ---- the passes of pm_solve, one launch per geometry -----------------------
+enum { PASS_XFWD = 0, PASS_YFWD, PASS_ZCONV, PASS_YINV, PASS_XINV, NPASS };
+
+template <typename T> int launch_pass(pm_ctx *c, int pass, cudaStream_t st) {
+    for (const GeoBuf &gb : c->geos) {
+        const pm_geometry &g = gb.g;
+        for (size_t b0 = 0; b0 < gb.sets.size(); b0 += PM_MAX_BATCH) {
+            const int nb = (int)std::min<size_t>(PM_MAX_BATCH, gb.sets.size() - b0);
+            FftArgs a;
+            std::memset(&a, 0, sizeof(a));
+            for (int s = 0; s < nb; ++s) {
+                const int gi = gb.sets[b0 + s].first, k = gb.sets[b0 + s].second;
+                a.rho[s] = c->rho[gi][k];
+                a.work[s] = c->work[gi][k];
+                a.phi[s] = c->phi[gi][k];
+            }
+            a.hhat = gb.hhat;
+            a.nx = g.nx; a.ny = g.ny; a.nz = g.nz; a.P = g.nx + 1;
+            a.scale = std::ldexp(1.0, -c->shift);
+            cudaError_t e;
+            switch (pass) {
+                case PASS_XFWD:
+                    a.tw = c->d_tw[tw_index(2 * g.nx)];
+                    a.nitems = (long long)g.ny * g.nz / 2;
+                    e = pm_launch_xfwd<T>(a, nb, st);
+                    break;
+                case PASS_YFWD:
+                case PASS_YINV:
+                    a.tw = c->d_tw[tw_index(2 * g.ny)];
+                    a.nitems = (long long)g.nz * a.P;
+                    e = pm_launch_col<T>(a, pass == PASS_YFWD ? COL_YFWD : COL_YINV, nb, st);
+                    break;
+                case PASS_ZCONV:
+                    a.tw = c->d_tw[tw_index(2 * g.nz)];
+                    a.nitems = (long long)2 * g.ny * a.P;
+                    e = pm_launch_col<T>(a, COL_ZCONV, nb, st);
+                    break;
+                default:
+                    a.tw = c->d_tw[tw_index(2 * g.nx)];
+                    a.nitems = (long long)g.ny * g.nz / 2;
+                    e = pm_launch_xinv<T>(a, nb, st);
+                    break;
+            }
+            if (e != cudaSuccess) return fail(PM_E_CUDA, "FFT pass %d launch failed: %s", pass, cudaGetErrorString(e));
+        }
+    }
+    return PM_OK;
+}
+
+template <typename T> int enqueue_solve(pm_ctx *c, cudaStream_t st, cudaEvent_t *ev) {
+    for (int pass = 0; pass < NPASS; ++pass) {
+        PM_TRY(launch_pass<T>(c, pass, st));
+        if (ev) PM_CK(cudaEventRecord(ev[pass], st));
+    }
+    return PM_OK;
+}
+
+template <typename T> int enqueue_deposit(pm_ctx *c, const pm_particles *p, cudaStream_t st) {
+    PM_CK(cudaMemsetAsync(c->rho_all, 0, c->rho_bytes, st));
+    PM_CK(pm_launch_deposit<T>(part_k<T>(p), c->d_sys, c->d_cen, st));
+    return PM_OK;
+}
+
+template <typename T> int enqueue_recentre(pm_ctx *c, const pm_particles *p, cudaStream_t st) {
+    if (!c->any_recentre) return PM_OK;
+    PM_CK(pm_launch_recentre<T>(part_k<T>(p), c->d_sys, c->d_cen, c->d_csum, c->sys.ngal, st));
+    return PM_OK;
+}
+
+// One full step; ev (optional, 8 events) marks the phase boundaries.
+template <typename T> int enqueue_step(pm_ctx *c, const pm_particles *p, double dt, cudaStream_t st,
+                                       cudaEvent_t *ev) {
+    PM_TRY(enqueue_recentre<T>(c, p, st));
+    if (ev) PM_CK(cudaEventRecord(ev[0], st));
+    PM_TRY(enqueue_deposit<T>(c, p, st));
+    if (ev) PM_CK(cudaEventRecord(ev[1], st));
+    PM_TRY(enqueue_solve<T>(c, st, ev ? ev + 2 : nullptr));
+    PM_CK(pm_launch_force<T>(0, part_k<T>(p), c->d_sys, c->d_cen, dt, nullptr, nullptr, nullptr, nullptr, st));
+    if (ev) PM_CK(cudaEventRecord(ev[7], st));
+    return PM_OK;
+}
+
+void destroy_graph(pm_ctx *c) {
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->gexec = nullptr;
+    c->graph = nullptr;
+}
+
+template <typename T> int step_impl(pm_ctx *c, const pm_particles *p, double dt, int nsteps) {
+    const bool same = c->gexec && std::memcmp(&c->gkey, p, sizeof(pm_particles)) == 0 && c->gdt == dt;
+    if (!same) {
+        destroy_graph(c);
+        PM_CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+        int rc = enqueue_step<T>(c, p, dt, c->cap, nullptr);
+        cudaGraph_t gr = nullptr;
+        cudaError_t e = cudaStreamEndCapture(c->cap, &gr);
+        if (rc != PM_OK) { if (gr) cudaGraphDestroy(gr); return rc; }
+        if (e != cudaSuccess) return fail(PM_E_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+        c->graph = gr;
+        e = cudaGraphInstantiate(&c->gexec, gr, 0);
+        if (e != cudaSuccess) { destroy_graph(c); return fail(PM_E_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e)); }
+        c->gkey = *p;
+        c->gdt = dt;
+    }
+    for (int s = 0; s < nsteps; ++s) PM_CK(cudaGraphLaunch(c->gexec, c->user));
+    return PM_OK;
+}
+
+template <typename T> int step_timed_impl(pm_ctx *c, const pm_particles *p, double dt, int nsteps, float *ms) {
+    const int NE = 9;
+    std::vector<cudaEvent_t> ev((size_t)nsteps * NE);
+    for (auto &e : ev) PM_CK(cudaEventCreate(&e));
+    int rc = PM_OK;
+    for (int s = 0; s < nsteps && rc == PM_OK; ++s) {
+        cudaEvent_t *e = ev.data() + (size_t)s * NE;
+        cudaEventRecord(e[0], c->user);
+        rc = enqueue_step<T>(c, p, dt, c->user, e + 1);
+    }
+    for (int k = 0; k < 9; ++k) ms[k] = 0.f;
+    if (rc == PM_OK) {
+        cudaError_t er = cudaStreamSynchronize(c->user);
+        if (er != cudaSuccess) rc = fail(PM_E_CUDA, "step_timed sync: %s", cudaGetErrorString(er));
+    }
+    if (rc == PM_OK) {
+        for (int s = 0; s < nsteps; ++s) {
+            cudaEvent_t *e = ev.data() + (size_t)s * NE;
+            for (int k = 0; k < 8; ++k) {
+                float t = 0.f;
+                cudaEventElapsedTime(&t, e[k], e[k + 1]);
+                ms[k] += t;
+            }
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e[0], e[8]);
+            ms[8] += t;
+        }
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    return rc;
+}
+
+template <typename T> int force_impl(pm_ctx *c, int mode, const pm_particles *p, double dt, void *ax, void *ay,
+                                     void *az, double *diag) {
+    PM_CK(pm_launch_force<T>(mode, part_k<T>(p), c->d_sys, c->d_cen, dt, (T *)ax, (T *)ay, (T *)az, diag, c->user));
+    return PM_OK;
+}
+
+}  // namespace
+
+// ============================================================================
+extern "C" {
+
+double pm_cell_length(double R, int32_t N, double q) { return 2.0 * R * q / (double)(N - 4); }
+
+double pm_q_crit(double r_core, double r_out, double r_sys, int32_t N) {
+    return std::fmax(r_core / r_out, 4.0 / (double)(N - 4) * r_sys / r_out);
+}
+
+int32_t pm_fixed_shift(double mass_bound) {
+    if (!(mass_bound > 0) || !std::isfinite(mass_bound)) return INT32_MIN;
+    return 62 - ceil_log2(mass_bound);
+}
+
+const char *pm_last_error(void) { return g_err.c_str(); }
+
+int pm_create_grids(const pm_system *sys, const pm_galaxy *gals, void *stream, pm_ctx **out) {
+    if (!out) return fail(PM_E_ARG, "out is NULL");
+    *out = nullptr;
+    if (!sys || !gals) return fail(PM_E_ARG, "sys or gals is NULL");
+    if (sys->precision != PM_FP32 && sys->precision != PM_FP64)
+        return fail(PM_E_ARG, "precision must be PM_FP32 or PM_FP64");
+    if (sys->ngal < 1 || sys->ngal > PM_MAX_GALAXIES) return fail(PM_E_ARG, "ngal %d out of range", sys->ngal);
+    if (!(sys->mass_bound > 0) || !std::isfinite(sys->mass_bound)) return fail(PM_E_ARG, "mass_bound must be positive and finite");
+    if (!std::isfinite(sys->G) || !std::isfinite(sys->h000) || !(sys->r_sys > 0) || !std::isfinite(sys->r_sys))
+        return fail(PM_E_ARG, "G, h000 must be finite and r_sys positive");
+    const int shift = 62 - ceil_log2(sys->mass_bound);
+    if (shift < -60 || shift > 1000) return fail(PM_E_OVERFLOW, "mass_bound %g leaves no fixed-point range", sys->mass_bound);
+
+    for (int gi = 0; gi < sys->ngal; ++gi) {
+        const pm_galaxy &G = gals[gi];
+        if (!geom_present(G.coarse) || !geom_valid(G.coarse))
+            return fail(PM_E_ARG, "galaxy %d: coarse grid must be present, powers of two in [8,256], positive lengths", gi);
+        if (geom_present(G.fine) && !geom_present(G.medium))
+            return fail(PM_E_ARG, "galaxy %d: a fine grid needs a medium grid", gi);
+        if (geom_present(G.medium)) {
+            if (!geom_valid(G.medium)) return fail(PM_E_ARG, "galaxy %d: invalid medium grid", gi);
+            if (!(G.r_out > 0) || !(G.r_core >= 0) || G.r_core > G.r_out)
+                return fail(PM_E_NESTING, "galaxy %d: need 0 <= r_core <= r_out, r_out > 0", gi);
+            const double q = G.medium.l_z / G.medium.l_xy;
+            if (q < 1.0) {
+                if (gi != 0) return fail(PM_E_QCRIT, "galaxy %d: only the first galaxy may be flattened", gi);
+                const double qc = pm_q_crit(G.r_core, G.r_out, sys->r_sys, G.medium.nx);
+                if (q < qc * (1.0 - 1e-12)) return fail(PM_E_QCRIT, "galaxy %d: q = %g below q_crit = %g", gi, q, qc);
+            }
+            if (ext_xy(G.medium, G.medium.nx) > ext_xy(G.coarse, G.coarse.nx) ||
+                ext_xy(G.medium, G.medium.ny) > ext_xy(G.coarse, G.coarse.ny) || ext_z(G.medium) > ext_z(G.coarse))
+                return fail(PM_E_NESTING, "galaxy %d: medium grid larger than coarse grid", gi);
+        }
+        if (geom_present(G.fine)) {
+            if (!geom_valid(G.fine)) return fail(PM_E_ARG, "galaxy %d: invalid fine grid", gi);
+            if (ext_xy(G.fine, G.fine.nx) > ext_xy(G.medium, G.medium.nx) ||
+                ext_xy(G.fine, G.fine.ny) > ext_xy(G.medium, G.medium.ny) || ext_z(G.fine) > ext_z(G.medium))
+                return fail(PM_E_NESTING, "galaxy %d: fine grid larger than medium grid", gi);
+        }
+        if (G.recentre && !(G.r_core > 0)) return fail(PM_E_ARG, "galaxy %d: recentring needs r_core > 0", gi);
+    }
+
+    pm_ctx *c = new pm_ctx();
+    c->sys = *sys;
+    for (int gi = 0; gi < sys->ngal; ++gi) c->gal[gi] = gals[gi];
+    c->prec = sys->precision;
+    c->esz = sys->precision == PM_FP32 ? 4 : 8;
+    c->shift = shift;
+    c->mscale = std::ldexp(1.0, shift);
+    c->user = (cudaStream_t)stream;
+    std::memset(c->set_geo, -1, sizeof(c->set_geo));
+    std::memset(c->rho, 0, sizeof(c->rho));
+    std::memset(c->phi, 0, sizeof(c->phi));
+    std::memset(c->work, 0, sizeof(c->work));
+    std::memset(&c->gkey, 0, sizeof(c->gkey));
+
+    auto cleanup = [&](int rc) { pm_destroy(c); return rc; };
+    if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess)
+        return cleanup(fail(PM_E_CUDA, "cudaStreamCreate failed"));
+    cudaError_t ea = (c->prec == PM_FP32) ? pm_set_attrs<float>() : pm_set_attrs<double>();
+    if (ea != cudaSuccess) return cleanup(fail(PM_E_CUDA, "kernel attributes: %s", cudaGetErrorString(ea)));
+
+    // geometries and mass sets
+    auto add_set = [&](int gi, int k, const pm_geometry &g) {
+        int id = -1;
+        for (size_t i = 0; i < c->geos.size(); ++i)
+            if (geom_equal(c->geos[i].g, g)) id = (int)i;
+        if (id < 0) {
+            GeoBuf gb;
+            gb.g = g;
+            gb.A = (long long)g.nx * g.ny * g.nz;
+            gb.workN = (long long)g.nz * 2 * g.ny * (g.nx + 1);
+            gb.hatN = (long long)(g.nx + 1) * (g.ny + 1) * (g.nz + 1);
+            c->geos.push_back(gb);
+            id = (int)c->geos.size() - 1;
+        }
+        c->geos[id].sets.push_back({gi, k});
+        c->set_geo[gi][k] = id;
+    };
+    for (int gi = 0; gi < sys->ngal; ++gi) {
+        const pm_galaxy &G = gals[gi];
+        if (geom_present(G.fine)) add_set(gi, 0, G.fine);
+        if (geom_present(G.medium)) {
+            add_set(gi, 1, G.medium);
+            add_set(gi, 2, G.medium);
+            add_set(gi, 3, G.coarse);
+        }
+        add_set(gi, 4, G.coarse);
+        if (G.recentre) c->any_recentre = true;
+    }
+    size_t rho_total = 0;
+    for (int gi = 0; gi < sys->ngal; ++gi)
+        for (int k = 0; k < PM_SETS; ++k)
+            if (c->set_geo[gi][k] >= 0) rho_total += (size_t)c->geos[c->set_geo[gi][k]].A;
+    int rc;
+    if ((rc = dev_alloc(c, (void **)&c->rho_all, rho_total * 8))) return cleanup(rc);
+    c->rho_bytes = rho_total * 8;
+    size_t off = 0;
+    for (int gi = 0; gi < sys->ngal; ++gi)
+        for (int k = 0; k < PM_SETS; ++k) {
+            const int id = c->set_geo[gi][k];
+            if (id < 0) continue;
+            const GeoBuf &gb = c->geos[id];
+            c->rho[gi][k] = c->rho_all + off;
+            off += (size_t)gb.A;
+            if ((rc = dev_alloc(c, &c->phi[gi][k], gb.A * c->esz))) return cleanup(rc);
+            if ((rc = dev_alloc(c, &c->work[gi][k], gb.workN * 2 * c->esz))) return cleanup(rc);
+            if (cudaMemsetAsync(c->work[gi][k], 0, gb.workN * 2 * c->esz, c->user) != cudaSuccess)
+                return cleanup(fail(PM_E_CUDA, "memset failed"));
+        }
+    for (GeoBuf &gb : c->geos) {
+        if ((rc = dev_alloc(c, &gb.hhat, gb.hatN * c->esz))) return cleanup(rc);
+        if ((rc = build_hhat(c, gb))) return cleanup(rc);
+    }
+    if ((rc = (c->prec == PM_FP32 ? upload_twiddles<float>(c) : upload_twiddles<double>(c)))) return cleanup(rc);
+
+    // system description for the particle kernels
+    SysK &hs = c->hs;
+    std::memset(&hs, 0, sizeof(hs));
+    hs.ngal = sys->ngal;
+    hs.rsys2 = (float)(sys->r_sys * sys->r_sys);
+    for (int k = 0; k < 3; ++k) hs.sc[k] = sys->sys_centre[k];
+    hs.mscale = c->mscale;
+    for (int gi = 0; gi < sys->ngal; ++gi) {
+        const pm_galaxy &G = gals[gi];
+        GalK &K = hs.gal[gi];
+        K.fine = make_geomk(G.fine);
+        K.med = make_geomk(G.medium);
+        K.coarse = make_geomk(G.coarse);
+        K.rc2 = (float)(G.r_core * G.r_core);
+        K.ro2 = (float)(G.r_out * G.r_out);
+        K.recentre = G.recentre ? 1 : 0;
+        K.sD = G.r_core > 0 ? 24 - ceil_log2(G.r_core) : 0;
+        for (int k = 0; k < PM_SETS; ++k) {
+            K.rho[k] = (unsigned long long *)c->rho[gi][k];
+            K.phi[k] = c->phi[gi][k];
+        }
+    }
+    if ((rc = dev_alloc(c, (void **)&c->d_sys, sizeof(SysK)))) return cleanup(rc);
+    if ((rc = dev_alloc(c, (void **)&c->d_cen, sizeof(double) * 3 * PM_MAX_GALAXIES))) return cleanup(rc);
+    if ((rc = dev_alloc(c, (void **)&c->d_csum, sizeof(unsigned long long) * 4 * PM_MAX_GALAXIES))) return cleanup(rc);
+    if ((rc = dev_alloc(c, (void **)&c->d_diag, sizeof(double) * 8))) return cleanup(rc);
+    if ((rc = dev_alloc(c, (void **)&c->d_cnt, sizeof(unsigned long long)))) return cleanup(rc);
+    double cen[3 * PM_MAX_GALAXIES] = {0};
+    for (int gi = 0; gi < sys->ngal; ++gi)
+        for (int k = 0; k < 3; ++k) cen[3 * gi + k] = gals[gi].centre[k];
+    if (cudaMemcpyAsync(c->d_sys, &hs, sizeof(SysK), cudaMemcpyHostToDevice, c->user) != cudaSuccess ||
+        cudaMemcpyAsync(c->d_cen, cen, sizeof(cen), cudaMemcpyHostToDevice, c->user) != cudaSuccess ||
+        cudaMemsetAsync(c->d_csum, 0, sizeof(unsigned long long) * 4 * PM_MAX_GALAXIES, c->user) != cudaSuccess ||
+        cudaStreamSynchronize(c->user) != cudaSuccess)
+        return cleanup(fail(PM_E_CUDA, "context upload failed: %s", cudaGetErrorString(cudaGetLastError())));
+    *out = c;
+    return PM_OK;
+}
+
+void pm_destroy(pm_ctx *c) {
+    if (!c) return;
+    if (c->user) cudaStreamSynchronize(c->user);
+    destroy_graph(c);
+    for (void *p : c->allocs) cudaFree(p);
+    if (c->cap) cudaStreamDestroy(c->cap);
+    delete c;
+}
+
+int pm_set_stream(pm_ctx *c, void *stream) {
+    if (!c) return fail(PM_E_ARG, "ctx is NULL");
+    c->user = (cudaStream_t)stream;
+    return PM_OK;
+}
+
+#define PM_DISPATCH(c, F, ...) ((c)->prec == PM_FP32 ? F<float>(__VA_ARGS__) : F<double>(__VA_ARGS__))
+
+int pm_recentre(pm_ctx *c, const pm_particles *p) {
+    if (!c) return fail(PM_E_ARG, "ctx is NULL");
+    PM_TRY(check_particles(p));
+    return PM_DISPATCH(c, enqueue_recentre, c, p, c->user);
+}
+
+int pm_deposit(pm_ctx *c, const pm_particles *p) {
+    if (!c) return fail(PM_E_ARG, "ctx is NULL");
+    PM_TRY(check_particles(p));
+    return PM_DISPATCH(c, enqueue_deposit, c, p, c->user);
+}
+
+int pm_solve(pm_ctx *c) {
+    if (!c) return fail(PM_E_ARG, "ctx is NULL");
+    return PM_DISPATCH(c, enqueue_solve, c, c->user, nullptr);
+}
+
+int pm_force(pm_ctx *c, const pm_particles *p, void *ax, void *ay, void *az) {
+    if (!c) return fail(PM_E_ARG, "ctx is NULL");
+    PM_TRY(check_particles(p));
+    if (p->n > 0 && (!ax || !ay || !az)) return fail(PM_E_ARG, "acceleration array is NULL");
+    return PM_DISPATCH(c, force_impl, c, 1, p, 0.0, ax, ay, az, nullptr);
+}
+
+int pm_kick(pm_ctx *c, const pm_particles *p, double dt) {
+    if (!c) return fail(PM_E_ARG, "ctx is NULL");
+    PM_TRY(check_particles(p));
+    if (!std::isfinite(dt)) return fail(PM_E_ARG, "dt not finite");
+    return PM_DISPATCH(c, force_impl, c, 2, p, dt, nullptr, nullptr, nullptr, nullptr);
+}
+
+int pm_step(pm_ctx *c, const pm_particles *p, double dt, int32_t nsteps) {
+    if (!c) return fail(PM_E_ARG, "ctx is NULL");
+    PM_TRY(check_particles(p));
+    if (nsteps < 0 || !std::isfinite(dt)) return fail(PM_E_ARG, "nsteps < 0 or dt not finite");
+    if (nsteps == 0) return PM_OK;
+    return PM_DISPATCH(c, step_impl, c, p, dt, nsteps);
+}
+
+int pm_step_timed(pm_ctx *c, const pm_particles *p, double dt, int32_t nsteps, float *ms_out) {
+    if (!c || !ms_out) return fail(PM_E_ARG, "ctx or ms_out is NULL");
+    PM_TRY(check_particles(p));
+    if (nsteps < 1 || !std::isfinite(dt)) return fail(PM_E_ARG, "nsteps < 1 or dt not finite");
+    return PM_DISPATCH(c, step_timed_impl, c, p, dt, nsteps, ms_out);
+}
+
+int pm_diagnostics(pm_ctx *c, const pm_particles *p, double dt, double *out) {
+    if (!c || !out) return fail(PM_E_ARG, "ctx or out is NULL");
+    PM_TRY(check_particles(p));
+    PM_TRY(pm_deposit(c, p));
+    PM_TRY(pm_solve(c));
+    PM_CK(cudaMemsetAsync(c->d_diag, 0, sizeof(double) * 8, c->user));
+    PM_TRY(PM_DISPATCH(c, force_impl, c, 3, p, dt, nullptr, nullptr, nullptr, c->d_diag));
+    double h[8];
+    PM_CK(cudaMemcpyAsync(h, c->d_diag, sizeof(h), cudaMemcpyDeviceToHost, c->user));
+    PM_CK(cudaStreamSynchronize(c->user));
+    for (int k = 0; k < 7; ++k) out[k] = h[k];
+    return PM_OK;
+}
+
+int pm_get_density(pm_ctx *c, int32_t gal, int32_t set, int64_t *host_out) {
+    if (!c || !host_out) return fail(PM_E_ARG, "ctx or host_out is NULL");
+    if (gal < 0 || gal >= c->sys.ngal || set < 1 || set > PM_SETS || c->set_geo[gal][set - 1] < 0)
+        return fail(PM_E_ARG, "no grid %d for galaxy %d", set, gal);
+    const GeoBuf &gb = c->geos[c->set_geo[gal][set - 1]];
+    PM_CK(cudaMemcpyAsync(host_out, c->rho[gal][set - 1], gb.A * 8, cudaMemcpyDeviceToHost, c->user));
+    PM_CK(cudaStreamSynchronize(c->user));
+    return PM_OK;
+}
+
+int pm_get_potential(pm_ctx *c, int32_t gal, int32_t set, void *host_out) {
+    if (!c || !host_out) return fail(PM_E_ARG, "ctx or host_out is NULL");
+    if (gal < 0 || gal >= c->sys.ngal || set < 1 || set > PM_SETS || c->set_geo[gal][set - 1] < 0)
+        return fail(PM_E_ARG, "no grid %d for galaxy %d", set, gal);
+    const GeoBuf &gb = c->geos[c->set_geo[gal][set - 1]];
+    PM_CK(cudaMemcpyAsync(host_out, c->phi[gal][set - 1], gb.A * c->esz, cudaMemcpyDeviceToHost, c->user));
+    PM_CK(cudaStreamSynchronize(c->user));
+    return PM_OK;
+}
+
+int pm_get_centres(pm_ctx *c, double *host_out) {
+    if (!c || !host_out) return fail(PM_E_ARG, "ctx or host_out is NULL");
+    PM_CK(cudaMemcpyAsync(host_out, c->d_cen, sizeof(double) * 3 * c->sys.ngal, cudaMemcpyDeviceToHost, c->user));
+    PM_CK(cudaStreamSynchronize(c->user));
+    return PM_OK;
+}
+
+int pm_set_centres(pm_ctx *c, const double *host_in) {
+    if (!c || !host_in) return fail(PM_E_ARG, "ctx or host_in is NULL");
+    PM_CK(cudaMemcpyAsync(c->d_cen, host_in, sizeof(double) * 3 * c->sys.ngal, cudaMemcpyHostToDevice, c->user));
+    PM_CK(cudaStreamSynchronize(c->user));
+    return PM_OK;
+}
+
+int pm_count_lost(pm_ctx *c, const pm_particles *p, int64_t *host_out) {
+    if (!c || !host_out) return fail(PM_E_ARG, "ctx or host_out is NULL");
+    PM_TRY(check_particles(p));
+    PM_CK(cudaMemsetAsync(c->d_cnt, 0, sizeof(unsigned long long), c->user));
+    cudaError_t e = (c->prec == PM_FP32) ? pm_launch_count_lost<float>(part_k<float>(p), c->d_cnt, c->user)
+                                          : pm_launch_count_lost<double>(part_k<double>(p), c->d_cnt, c->user);
+    PM_CK(e);
+    unsigned long long h = 0;
+    PM_CK(cudaMemcpyAsync(&h, c->d_cnt, sizeof(h), cudaMemcpyDeviceToHost, c->user));
+    PM_CK(cudaStreamSynchronize(c->user));
+    *host_out = (int64_t)h;
+    return PM_OK;
+}
+
+int pm_info(pm_ctx *c, int64_t *out) {
+    if (!c || !out) return fail(PM_E_ARG, "ctx or out is NULL");
+    int nsets = 0;
+    for (const GeoBuf &gb : c->geos) nsets += (int)gb.sets.size();
+    out[0] = c->shift;
+    out[1] = nsets;
+    out[2] = (int64_t)c->geos.size();
+    out[3] = (int64_t)c->bytes;
+    return PM_OK;
+}
+
+}  // extern "C"

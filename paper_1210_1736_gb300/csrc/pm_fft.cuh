@@ -1,0 +1,194 @@
+// Register/shared-memory FFT building blocks for the doubled-grid convolution
+// (Sec. 2.1: the potential of the isolated system from the 2N-periodic
+// convolution, evaluated with FFTs of length L = 2N per axis).
+//
+// Each transform of length L is done by L/16 threads holding 16 values each;
+// stages are radix-16 (plus one radix-2/4/8 stage where L is not a power of
+// 16) in the self-sorting Stockham order, exchanging through shared memory
+// laid out [row][column] so that a warp's accesses are contiguous.
+#pragma once
+
+#include "pm_internal.cuh"
+
+namespace pmfft {
+
+constexpr int E = 16;  // values held per thread
+
+__host__ __device__ constexpr int nstages(int L) { return L <= 16 ? 1 : (L <= 256 ? 2 : 3); }
+// Forward plan: 16 | 16,L/16 | 16,16,2 (L = 512).
+__host__ __device__ constexpr int fwd_radix(int L, int s) {
+    return s == 0 ? 16 : (L == 512 ? (s == 1 ? 16 : 2) : L / 16);
+}
+// A plan is the forward plan or its reverse; reversing lets the first stage
+// of the inverse transform reuse the registers of the forward transform's
+// last stage.
+__host__ __device__ constexpr int radix(int L, int s, bool rev) {
+    return rev ? fwd_radix(L, nstages(L) - 1 - s) : fwd_radix(L, s);
+}
+__host__ __device__ constexpr int stride_before(int L, int s, bool rev) {
+    return s == 0 ? 1 : stride_before(L, s - 1, rev) * radix(L, s - 1, rev);
+}
+
+// z * exp(SIGN * 2 pi i e / 16) for a compile-time-known e.
+template <int SIGN, typename C> __device__ __forceinline__ C rot16(int e, C z) {
+    typedef decltype(z.x) T;
+    const T c1 = (T)0.92387953251128675613, s1 = (T)0.38268343236508977173,
+            r2 = (T)0.70710678118654752440;
+    e &= 15;
+    T c = 0, s = 0;
+    switch (e) {
+        case 0: return z;
+        case 4: return cmul_i<SIGN>(z);
+        case 8: { C r; r.x = -z.x; r.y = -z.y; return r; }
+        case 12: return cmul_i<-SIGN>(z);
+        case 1: c = c1; s = s1; break;
+        case 2: c = r2; s = r2; break;
+        case 3: c = s1; s = c1; break;
+        case 5: c = -s1; s = c1; break;
+        case 6: c = -r2; s = r2; break;
+        case 7: c = -c1; s = s1; break;
+        case 9: c = -c1; s = -s1; break;
+        case 10: c = -r2; s = -r2; break;
+        case 11: c = -s1; s = -c1; break;
+        case 13: c = s1; s = -c1; break;
+        case 14: c = r2; s = -r2; break;
+        case 15: c = c1; s = -s1; break;
+    }
+    if (SIGN < 0) s = -s;
+    C r;
+    r.x = z.x * c - z.y * s;
+    r.y = z.x * s + z.y * c;
+    return r;
+}
+
+// In-register DFT of length R (natural order in and out):
+// X[k] = sum_r v[r] exp(SIGN 2 pi i r k / R).
+template <int R, int SIGN, typename C> struct Dft;
+
+template <int SIGN, typename C> struct Dft<1, SIGN, C> {
+    static __device__ __forceinline__ void run(C *) {}
+};
+template <int SIGN, typename C> struct Dft<2, SIGN, C> {
+    static __device__ __forceinline__ void run(C *v) {
+        C a = cadd(v[0], v[1]), b = csub(v[0], v[1]);
+        v[0] = a; v[1] = b;
+    }
+};
+template <int SIGN, typename C> struct Dft<4, SIGN, C> {
+    static __device__ __forceinline__ void run(C *v) {
+        C t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+        C t2 = cadd(v[1], v[3]), t3 = cmul_i<SIGN>(csub(v[1], v[3]));
+        v[0] = cadd(t0, t2); v[2] = csub(t0, t2);
+        v[1] = cadd(t1, t3); v[3] = csub(t1, t3);
+    }
+};
+// Cooley-Tukey split R = N1*N2: input n = N2*n1 + n2, output k = k1 + N1*k2.
+template <int N1, int N2, int SIGN, typename C>
+__device__ __forceinline__ void dft_split(C *v) {
+    C y[N1 * N2];
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) {
+        C t[N1];
+#pragma unroll
+        for (int n1 = 0; n1 < N1; ++n1) t[n1] = v[N2 * n1 + n2];
+        Dft<N1, SIGN, C>::run(t);
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) y[n2 * N1 + k1] = rot16<SIGN>((16 / (N1 * N2)) * n2 * k1, t[k1]);
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) {
+        C t[N2];
+#pragma unroll
+        for (int n2 = 0; n2 < N2; ++n2) t[n2] = y[n2 * N1 + k1];
+        Dft<N2, SIGN, C>::run(t);
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) v[k1 + N1 * k2] = t[k2];
+    }
+}
+template <int SIGN, typename C> struct Dft<8, SIGN, C> {
+    static __device__ __forceinline__ void run(C *v) { dft_split<2, 4, SIGN>(v); }
+};
+template <int SIGN, typename C> struct Dft<16, SIGN, C> {
+    static __device__ __forceinline__ void run(C *v) { dft_split<4, 4, SIGN>(v); }
+};
+
+// Butterflies of stage S on the thread's E registers.  Thread t of a column
+// owns the stage items j = t + kk*TPC (kk < E/R); register kk*R + r holds the
+// input x[j + r*L/R] and afterwards the output y[(j/Ns)*Ns*R + j%Ns + r*Ns].
+// tw[m] = exp(-2 pi i m / L) (conjugated for SIGN > 0).
+template <int L, int S, bool REV, int SIGN, typename C>
+__device__ __forceinline__ void stage_butterflies(C *v, int t, const C *tw) {
+    constexpr int R = radix(L, S, REV), Ns = stride_before(L, S, REV), TPC = L / E;
+#pragma unroll
+    for (int kk = 0; kk < E / R; ++kk) {
+        const int j = t + kk * TPC;
+        if (Ns > 1) {
+            const int jm = j % Ns;
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                C w = tw[(jm * r * (L / (Ns * R))) & (L - 1)];
+                v[kk * R + r] = (SIGN < 0) ? cmul(v[kk * R + r], w) : cconjmul(v[kk * R + r], w);
+            }
+        }
+        Dft<R, SIGN, C>::run(v + kk * R);
+    }
+}
+
+// Row of the output of register (kk, r) of stage S.
+template <int L, int S, bool REV>
+__device__ __forceinline__ int out_row(int t, int kk, int r) {
+    constexpr int R = radix(L, S, REV), Ns = stride_before(L, S, REV), TPC = L / E;
+    const int j = t + kk * TPC;
+    return (j / Ns) * Ns * R + (j % Ns) + r * Ns;
+}
+// Row of the input of register (kk, r) of stage S.
+template <int L, int S, bool REV>
+__device__ __forceinline__ int in_row(int t, int kk, int r) {
+    constexpr int R = radix(L, S, REV), TPC = L / E;
+    return t + kk * TPC + r * (L / R);
+}
+
+// Writes stage S's outputs to shared memory (column c of a [L][ldc] array).
+template <int L, int S, bool REV, typename C>
+__device__ __forceinline__ void store_stage(C *sm, int ldc, int c, int t, const C *v) {
+    constexpr int R = radix(L, S, REV);
+#pragma unroll
+    for (int kk = 0; kk < E / R; ++kk)
+#pragma unroll
+        for (int r = 0; r < R; ++r) sm[out_row<L, S, REV>(t, kk, r) * ldc + c] = v[kk * R + r];
+}
+// Reads stage S's inputs from shared memory.
+template <int L, int S, bool REV, typename C>
+__device__ __forceinline__ void load_stage(const C *sm, int ldc, int c, int t, C *v) {
+    constexpr int R = radix(L, S, REV);
+#pragma unroll
+    for (int kk = 0; kk < E / R; ++kk)
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[kk * R + r] = sm[in_row<L, S, REV>(t, kk, r) * ldc + c];
+}
+
+// Runs stages 0..NS-1 given stage 0's inputs in registers; exchanges through
+// shared memory between stages.  On return the registers hold the last
+// stage's outputs (natural order rows in_row of the last stage).  All
+// threads of the block must call it (it synchronises).
+template <int L, bool REV, int SIGN, typename C>
+__device__ __forceinline__ void fft_core(C *v, C *sm, int ldc, int c, int t, const C *tw) {
+    constexpr int NS = nstages(L);
+    stage_butterflies<L, 0, REV, SIGN>(v, t, tw);
+    if (NS > 1) {
+        store_stage<L, 0, REV>(sm, ldc, c, t, v);
+        __syncthreads();
+        load_stage<L, (NS > 1 ? 1 : 0), REV>(sm, ldc, c, t, v);
+        __syncthreads();
+        stage_butterflies<L, (NS > 1 ? 1 : 0), REV, SIGN>(v, t, tw);
+    }
+    if (NS > 2) {
+        store_stage<L, (NS > 1 ? 1 : 0), REV>(sm, ldc, c, t, v);
+        __syncthreads();
+        load_stage<L, (NS > 2 ? 2 : 0), REV>(sm, ldc, c, t, v);
+        __syncthreads();
+        stage_butterflies<L, (NS > 2 ? 2 : 0), REV, SIGN>(v, t, tw);
+    }
+}
+
+}  // namespace pmfft

@@ -1,0 +1,115 @@
+// Internal types and device helpers of the particle-mesh library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pm.h"
+
+#define PM_SETS 5
+
+template <typename T> struct cplx_t;
+template <> struct cplx_t<float>  { typedef float2  type; };
+template <> struct cplx_t<double> { typedef double2 type; };
+
+// Geometry as the particle kernels see it.  gxy/gz are (float)(1/l): the
+// canonical FP32 cell-assignment factors; the rest are FP64 lengths and
+// finite-difference coefficients of Eq. (eqn:diff).
+struct GeomK {
+    int nx, ny, nz;
+    float gxy, gz;
+    double lxy, lz;
+    double c_gx, c_gz;     // 1/(2 l_xy), 1/(2 l_z)         central difference
+    double c_hxx, c_hzz;   // 1/l_xy^2, 1/l_z^2              second difference
+    double c_mxy, c_mxz;   // 1/(4 l_xy l_xy), 1/(4 l_xy l_z) mixed difference
+};
+
+struct GalK {
+    GeomK fine, med, coarse;   // nx == 0: absent
+    float rc2, ro2;            // (float)(r_core^2), (float)(r_out^2)
+    int recentre, sD;          // recentring flag, offset fixed-point shift
+    unsigned long long *rho[PM_SETS];   // int64 densities (two's complement)
+    const void *phi[PM_SETS];           // potentials, context precision
+};
+
+struct SysK {
+    int ngal;
+    float rsys2;
+    double sc[3];
+    double mscale;             // 2^s
+    GalK gal[PM_MAX_GALAXIES];
+};
+
+template <typename T> struct PartK {
+    T *x, *y, *z, *vx, *vy, *vz;
+    const T *m;
+    const int32_t *gal;
+    uint32_t *flags;
+    long long n;
+};
+
+// ----------------------------------------------------------------------------
+// Canonical cell assignment (Eq. eqn:cell).  Every rounding is explicit and
+// no multiply-add is fused, so this function and the CPU reference agree bit
+// for bit: d = fl32(x - c) (FP64 subtract), u = fl32(fl32(d*gamma) + N/2),
+// a = floor(fl32(u + 1/2)).
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ float pm_off32(double x, double c) {
+    return __double2float_rn(__dsub_rn(x, c));
+}
+__device__ __forceinline__ int pm_cell(float d, float g, int n) {
+    float u = __fadd_rn(__fmul_rn(d, g), (float)(n >> 1));
+    return (int)floorf(__fadd_rn(u, 0.5f));
+}
+__device__ __forceinline__ float pm_r2(float dx, float dy, float dz) {
+    return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+}
+__device__ __forceinline__ bool pm_inbox(int a, int n) { return a >= 2 && a <= n - 3; }
+
+struct Cell { int i, j, k; bool ok; };
+
+__device__ __forceinline__ Cell pm_cells(const GeomK &g, float dx, float dy, float dz) {
+    Cell c;
+    c.i = pm_cell(dx, g.gxy, g.nx);
+    c.j = pm_cell(dy, g.gxy, g.ny);
+    c.k = pm_cell(dz, g.gz, g.nz);
+    c.ok = pm_inbox(c.i, g.nx) && pm_inbox(c.j, g.ny) && pm_inbox(c.k, g.nz);
+    return c;
+}
+
+enum { REG_CORE = 0, REG_SHELL = 1, REG_OUTER = 2 };
+
+// Region of a point relative to galaxy G centred on c (Sec. 2.1): core =
+// r < R_core inside grids 1 and 2; shell = not core, r < R_out inside grid 2.
+// Returns the fine and medium cells as a by-product.
+__device__ __forceinline__ int pm_region(const GalK &G, float dx, float dy, float dz,
+                                         Cell &cf, Cell &cm) {
+    float r2 = pm_r2(dx, dy, dz);
+    cm.ok = false; cf.ok = false;
+    if (G.med.nx) cm = pm_cells(G.med, dx, dy, dz);
+    if (G.fine.nx && G.med.nx) {
+        cf = pm_cells(G.fine, dx, dy, dz);
+        if (r2 < G.rc2 && cf.ok && cm.ok) return REG_CORE;
+    }
+    if (G.med.nx && r2 < G.ro2 && cm.ok) return REG_SHELL;
+    return REG_OUTER;
+}
+
+// ----------------------------------------------------------------------------
+// Small complex helpers
+// ----------------------------------------------------------------------------
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { C r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { C r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+    C r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
+}
+template <typename C> __device__ __forceinline__ C cconjmul(C a, C b) {  // a * conj(b)
+    C r; r.x = a.x * b.x + a.y * b.y; r.y = a.y * b.x - a.x * b.y; return r;
+}
+template <typename C> __device__ __forceinline__ C czero() { C r; r.x = 0; r.y = 0; return r; }
+// multiply by SIGN*i
+template <int SIGN, typename C> __device__ __forceinline__ C cmul_i(C z) {
+    C r;
+    if (SIGN > 0) { r.x = -z.y; r.y = z.x; } else { r.x = z.y; r.y = -z.x; }
+    return r;
+}

@@ -1,0 +1,668 @@
+// Kernels of the nested-grid particle-mesh step, templated on the working
+// precision T (float or double).  Included once per precision.
+#pragma once
+
+#include "pm_fft.cuh"
+#include "pm_launch.h"
+
+namespace pmk {
+
+using pmfft::E;
+using pmfft::nstages;
+using pmfft::radix;
+
+constexpr int NT = 256;  // threads per block for every FFT pass
+
+template <int L> struct XShape {          // x passes: lines (row pairs) per block
+    static constexpr int TPC = L / E, LINES = NT / TPC, LDC = LINES + 1;
+};
+template <int L> struct CShape {          // column passes: columns per block
+    static constexpr int TPC = L / E, COLS = NT / TPC, LDC = COLS;
+};
+
+template <typename T, int L> constexpr size_t xpass_smem() {
+    return (size_t)(L + L * XShape<L>::LDC) * sizeof(typename cplx_t<T>::type);
+}
+template <typename T, int L> constexpr size_t col_smem() {
+    return (size_t)(L + L * CShape<L>::LDC) * sizeof(typename cplx_t<T>::type);
+}
+
+template <typename C> __device__ __forceinline__ void load_twiddles(C *tw, const C *g, int L) {
+    for (int i = threadIdx.x; i < L; i += blockDim.x) tw[i] = g[i];
+}
+
+// ---------------------------------------------------------------------------
+// x forward pass: int64 density rows -> half spectra along x (R2C) with the
+// zero padding of the doubled grid implicit (rows are nx long, transforms
+// L = 2nx).  Two real rows travel as one complex line and are separated
+// after the transform: A = (Z[k] + conj Z[L-k]) / 2, B = (Z[k] - conj Z[L-k]) / 2i.
+// ---------------------------------------------------------------------------
+template <typename T, int L>
+__global__ void __launch_bounds__(NT) k_xfwd(FftArgs a) {
+    typedef typename cplx_t<T>::type C;
+    typedef XShape<L> S;
+    constexpr int NX = L / 2, P = NX + 1, NS = nstages(L);
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C *tw = reinterpret_cast<C *>(smraw);
+    C *sm = tw + L;
+    const int tid = threadIdx.x;
+    load_twiddles(tw, static_cast<const C *>(a.tw), L);
+
+    const long long *rho = a.rho[blockIdx.y];
+    C *work = static_cast<C *>(a.work[blockIdx.y]);
+    const long long p0 = (long long)blockIdx.x * S::LINES;
+    const T scale = (T)a.scale;
+    const int ny = a.ny;
+
+    for (int e = tid; e < S::LINES * NX; e += NT) {
+        const int line = e / NX, x = e % NX;
+        const long long p = p0 + line;
+        C val = czero<C>();
+        if (p < a.nitems) {
+            const long long r0 = 2 * p;
+            val.x = (T)rho[r0 * NX + x] * scale;
+            val.y = (T)rho[(r0 + 1) * NX + x] * scale;
+        }
+        sm[x * S::LDC + line] = val;
+    }
+    __syncthreads();
+
+    const int c = tid % S::LINES, t = tid / S::LINES;
+    C v[E];
+    constexpr int R0 = radix(L, 0, false);
+#pragma unroll
+    for (int kk = 0; kk < E / R0; ++kk)
+#pragma unroll
+        for (int r = 0; r < R0; ++r)
+            v[kk * R0 + r] = (r < R0 / 2) ? sm[pmfft::in_row<L, 0, false>(t, kk, r) * S::LDC + c] : czero<C>();
+    __syncthreads();
+    pmfft::fft_core<L, false, -1>(v, sm, S::LDC, c, t, tw);
+    pmfft::store_stage<L, NS - 1, false>(sm, S::LDC, c, t, v);
+    __syncthreads();
+
+    for (int e = tid; e < S::LINES * P; e += NT) {
+        const int line = e / P, k = e % P;
+        const long long p = p0 + line;
+        if (p >= a.nitems) continue;
+        const C zk = sm[k * S::LDC + line];
+        const C zm = sm[((L - k) & (L - 1)) * S::LDC + line];
+        C A, B;
+        A.x = (T)0.5 * (zk.x + zm.x);
+        A.y = (T)0.5 * (zk.y - zm.y);
+        B.x = (T)0.5 * (zk.y + zm.y);
+        B.y = (T)-0.5 * (zk.x - zm.x);
+        const long long r0 = 2 * p, z = r0 / ny, y = r0 % ny;
+        C *row = work + ((size_t)z * 2 * ny + y) * P;
+        row[k] = A;
+        row[P + k] = B;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Column passes along y or z (stride > 1): each block owns COLS consecutive
+// columns; a thread reads its first-stage inputs straight from global memory
+// (a warp reads contiguous row segments) and writes its last-stage outputs
+// back in place.
+//   COL_YFWD : forward along y, inputs y < ny (rest is padding), all 2ny out
+//   COL_ZCONV: forward along z (inputs z < nz), multiply by the real, even
+//              H-hat, inverse along z, keep z < nz       (Sec. 2.1)
+//   COL_YINV : inverse along y, keep y < ny
+// ---------------------------------------------------------------------------
+template <typename T, int L, int MODE>
+__global__ void __launch_bounds__(NT) k_col(FftArgs a) {
+    typedef typename cplx_t<T>::type C;
+    typedef CShape<L> S;
+    constexpr int NS = nstages(L);
+    constexpr bool REV_IN = (MODE == COL_YINV);
+    constexpr int SIGN_IN = (MODE == COL_YINV) ? 1 : -1;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C *tw = reinterpret_cast<C *>(smraw);
+    C *sm = tw + L;
+    const int tid = threadIdx.x;
+    load_twiddles(tw, static_cast<const C *>(a.tw), L);
+
+    const int c = tid % S::COLS, t = tid / S::COLS;
+    const long long q = (long long)blockIdx.x * S::COLS + c;
+    const bool valid = q < a.nitems;
+    const int P = a.P;
+    const size_t ny2P = (size_t)2 * a.ny * P;
+    size_t off, stride;
+    if (MODE == COL_ZCONV) {
+        off = (size_t)q;
+        stride = ny2P;
+    } else {
+        off = (size_t)(q / P) * ny2P + (size_t)(q % P);
+        stride = (size_t)P;
+    }
+    C *col = static_cast<C *>(a.work[blockIdx.y]) + (valid ? off : 0);
+    __syncthreads();
+
+    C v[E];
+    constexpr int R0 = radix(L, 0, REV_IN);
+#pragma unroll
+    for (int kk = 0; kk < E / R0; ++kk)
+#pragma unroll
+        for (int r = 0; r < R0; ++r) {
+            const bool need = valid && (MODE == COL_YINV || r < R0 / 2);
+            v[kk * R0 + r] = need ? col[(size_t)pmfft::in_row<L, 0, REV_IN>(t, kk, r) * stride] : czero<C>();
+        }
+    pmfft::fft_core<L, REV_IN, SIGN_IN>(v, sm, S::LDC, c, t, tw);
+
+    if (MODE == COL_YFWD) {
+        constexpr int RL = radix(L, NS - 1, false);
+        if (valid) {
+#pragma unroll
+            for (int kk = 0; kk < E / RL; ++kk)
+#pragma unroll
+                for (int r = 0; r < RL; ++r)
+                    col[(size_t)pmfft::in_row<L, NS - 1, false>(t, kk, r) * stride] = v[kk * RL + r];
+        }
+        return;
+    }
+    if (MODE == COL_ZCONV) {
+        constexpr int RL = radix(L, NS - 1, false);
+        const T *hh = static_cast<const T *>(a.hhat);
+        const int ny = a.ny;
+        const int ky = valid ? (int)(q / P) : 0, kx = valid ? (int)(q % P) : 0;
+        const int kyr = ky <= ny ? ky : 2 * ny - ky;
+#pragma unroll
+        for (int kk = 0; kk < E / RL; ++kk)
+#pragma unroll
+            for (int r = 0; r < RL; ++r) {
+                const int kz = pmfft::in_row<L, NS - 1, false>(t, kk, r);
+                const int kzr = kz <= L / 2 ? kz : L - kz;
+                const T h = valid ? hh[((size_t)kzr * (ny + 1) + kyr) * P + kx] : (T)0;
+                v[kk * RL + r].x *= h;
+                v[kk * RL + r].y *= h;
+            }
+        pmfft::fft_core<L, true, 1>(v, sm, S::LDC, c, t, tw);
+    }
+    // inverse outputs (COL_ZCONV, COL_YINV): the last stage of the reversed
+    // plan is radix 16 and its outputs below L/2 are registers r < 8.
+    constexpr int RL = radix(L, NS - 1, true);
+    if (valid) {
+#pragma unroll
+        for (int kk = 0; kk < E / RL; ++kk)
+#pragma unroll
+            for (int r = 0; r < RL / 2; ++r)
+                col[(size_t)pmfft::in_row<L, NS - 1, true>(t, kk, r) * stride] = v[kk * RL + r];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// x inverse pass: two half-spectrum rows A, B -> Z = A + iB completed by
+// Hermitian symmetry, inverse transform, a = Re, b = Im; keep x < nx -> Phi.
+// ---------------------------------------------------------------------------
+template <typename T, int L>
+__global__ void __launch_bounds__(NT) k_xinv(FftArgs a) {
+    typedef typename cplx_t<T>::type C;
+    typedef XShape<L> S;
+    constexpr int NX = L / 2, P = NX + 1, NS = nstages(L);
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C *tw = reinterpret_cast<C *>(smraw);
+    C *sm = tw + L;
+    const int tid = threadIdx.x;
+    load_twiddles(tw, static_cast<const C *>(a.tw), L);
+
+    const C *work = static_cast<const C *>(a.work[blockIdx.y]);
+    T *phi = static_cast<T *>(a.phi[blockIdx.y]);
+    const long long p0 = (long long)blockIdx.x * S::LINES;
+    const int ny = a.ny;
+
+    for (int e = tid; e < S::LINES * P; e += NT) {
+        const int line = e / P, k = e % P;
+        const long long p = p0 + line;
+        C A = czero<C>(), B = czero<C>();
+        if (p < a.nitems) {
+            const long long r0 = 2 * p, z = r0 / ny, y = r0 % ny;
+            const C *row = work + ((size_t)z * 2 * ny + y) * P;
+            A = row[k];
+            B = row[P + k];
+        }
+        C zk;
+        if (k == 0 || k == NX) {
+            zk.x = A.x; zk.y = B.x;
+            sm[k * S::LDC + line] = zk;
+        } else {
+            zk.x = A.x - B.y; zk.y = A.y + B.x;
+            sm[k * S::LDC + line] = zk;
+            C zm;
+            zm.x = A.x + B.y; zm.y = B.x - A.y;
+            sm[(L - k) * S::LDC + line] = zm;
+        }
+    }
+    __syncthreads();
+
+    const int c = tid % S::LINES, t = tid / S::LINES;
+    C v[E];
+    pmfft::load_stage<L, 0, true>(sm, S::LDC, c, t, v);
+    __syncthreads();
+    pmfft::fft_core<L, true, 1>(v, sm, S::LDC, c, t, tw);
+    constexpr int RL = radix(L, NS - 1, true);
+#pragma unroll
+    for (int kk = 0; kk < E / RL; ++kk)
+#pragma unroll
+        for (int r = 0; r < RL / 2; ++r)
+            sm[pmfft::in_row<L, NS - 1, true>(t, kk, r) * S::LDC + c] = v[kk * RL + r];
+    __syncthreads();
+
+    for (int e = tid; e < S::LINES * NX; e += NT) {
+        const int line = e / NX, x = e % NX;
+        const long long p = p0 + line;
+        if (p >= a.nitems) continue;
+        const C val = sm[x * S::LDC + line];
+        phi[(2 * p) * NX + x] = val.x;
+        phi[(2 * p + 1) * NX + x] = val.y;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Particle kernels.  The system description is staged in shared memory.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void stage_sys(SysK &s, const SysK *g) {
+    const int *src = reinterpret_cast<const int *>(g);
+    int *dst = reinterpret_cast<int *>(&s);
+    for (int i = threadIdx.x; i < (int)(sizeof(SysK) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
+}
+
+__device__ __forceinline__ size_t cell_off(const GeomK &g, const Cell &c) {
+    return ((size_t)c.k * g.ny + c.j) * g.nx + c.i;
+}
+
+// Steps a2-a3: classification and exact fixed-point mass assignment.
+template <typename T>
+__global__ void __launch_bounds__(256) k_deposit(PartK<T> p, const SysK *sk, const double *__restrict__ cen) {
+    __shared__ SysK s;
+    stage_sys(s, sk);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += stride) {
+        const uint32_t f = p.flags[i];
+        if (f & PM_FLAG_LOST) continue;
+        const double x = (double)p.x[i], y = (double)p.y[i], z = (double)p.z[i];
+        const float sx = pm_off32(x, s.sc[0]), sy = pm_off32(y, s.sc[1]), sz = pm_off32(z, s.sc[2]);
+        bool lost = !(pm_r2(sx, sy, sz) < s.rsys2);
+        const int g = p.gal[i];
+        if (g < 0 || g >= s.ngal) lost = true;
+        Cell cc;
+        cc.i = cc.j = cc.k = 0; cc.ok = false;
+        for (int h = 0; h < s.ngal; ++h) {
+            const Cell ch = pm_cells(s.gal[h].coarse, sx, sy, sz);
+            lost = lost || !ch.ok;
+            if (h == g) cc = ch;
+        }
+        if (lost) { p.flags[i] = f | PM_FLAG_LOST; continue; }
+        const GalK &G = s.gal[g];
+        const float dx = pm_off32(x, cen[3 * g]), dy = pm_off32(y, cen[3 * g + 1]), dz = pm_off32(z, cen[3 * g + 2]);
+        Cell cf, cm;
+        const int reg = pm_region(G, dx, dy, dz, cf, cm);
+        const unsigned long long q = (unsigned long long)__double2ll_rn(__dmul_rn((double)p.m[i], s.mscale));
+        if (reg == REG_CORE) {
+            atomicAdd(G.rho[0] + cell_off(G.fine, cf), q);
+            atomicAdd(G.rho[1] + cell_off(G.med, cm), q);
+            atomicAdd(G.rho[3] + cell_off(G.coarse, cc), q);
+        } else if (reg == REG_SHELL) {
+            atomicAdd(G.rho[2] + cell_off(G.med, cm), q);
+            atomicAdd(G.rho[3] + cell_off(G.coarse, cc), q);
+        } else {
+            atomicAdd(G.rho[4] + cell_off(G.coarse, cc), q);
+        }
+    }
+}
+
+// Eq. (eqn:diff) on one grid (with an optional second potential on the same
+// grid summed point by point), accumulated into acc; optionally the
+// potential at the particle (cell value + gradient . Delta).
+template <typename T>
+__device__ __forceinline__ void stencil(const GeomK &g, const T *__restrict__ P1, const T *__restrict__ P2,
+                                        const Cell &cl, T dx, T dy, T dz, T *acc, T *phi) {
+    const long long sy = g.nx, sz = (long long)g.nx * g.ny;
+    const size_t base = cell_off(g, cl);
+    const T *b1 = P1 + base;
+    const T *b2 = P2 ? P2 + base : nullptr;
+    auto ld = [&](int di, int dj, int dk) -> T {
+        const long long o = di + dj * sy + dk * sz;
+        T v = __ldg(b1 + o);
+        if (b2) v += __ldg(b2 + o);
+        return v;
+    };
+    const T p0 = ld(0, 0, 0);
+    const T xp = ld(1, 0, 0), xm = ld(-1, 0, 0);
+    const T yp = ld(0, 1, 0), ym = ld(0, -1, 0);
+    const T zp = ld(0, 0, 1), zm = ld(0, 0, -1);
+    const T mxy = (ld(1, 1, 0) - ld(-1, 1, 0) + ld(-1, -1, 0) - ld(1, -1, 0)) * (T)g.c_mxy;
+    const T mxz = (ld(1, 0, 1) - ld(-1, 0, 1) + ld(-1, 0, -1) - ld(1, 0, -1)) * (T)g.c_mxz;
+    const T myz = (ld(0, 1, 1) - ld(0, -1, 1) + ld(0, -1, -1) - ld(0, 1, -1)) * (T)g.c_mxz;
+    const T gx = (xp - xm) * (T)g.c_gx, gy = (yp - ym) * (T)g.c_gx, gz = (zp - zm) * (T)g.c_gz;
+    const T hxx = (xp + xm - 2 * p0) * (T)g.c_hxx;
+    const T hyy = (yp + ym - 2 * p0) * (T)g.c_hxx;
+    const T hzz = (zp + zm - 2 * p0) * (T)g.c_hzz;
+    acc[0] += gx + hxx * dx + mxy * dy + mxz * dz;
+    acc[1] += gy + hyy * dy + mxy * dx + myz * dz;
+    acc[2] += gz + hzz * dz + mxz * dx + myz * dy;
+    if (phi) *phi += p0 + gx * dx + gy * dy + gz * dz;
+}
+
+// Offset of a particle from the centre of its cell (Delta of Eq. eqn:diff).
+template <typename T>
+__device__ __forceinline__ void cell_delta(const GeomK &g, const Cell &cl, T rx, T ry, T rz, T &dx, T &dy, T &dz) {
+    dx = rx - (T)(cl.i - (g.nx >> 1)) * (T)g.lxy;
+    dy = ry - (T)(cl.j - (g.ny >> 1)) * (T)g.lxy;
+    dz = rz - (T)(cl.k - (g.nz >> 1)) * (T)g.lz;
+}
+
+template <typename T> __device__ __forceinline__ T rel_off(double x, double c);
+template <> __device__ __forceinline__ float rel_off<float>(double x, double c) { return pm_off32(x, c); }
+template <> __device__ __forceinline__ double rel_off<double>(double x, double c) { return __dsub_rn(x, c); }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Step a8 (+a9): acceleration by Eq. (eqn:diff) on the grids the combination
+// rule selects for each galaxy (Sec. 2.1), then
+//   MODE 0: leap-frog kick-drift   MODE 1: write acceleration
+//   MODE 2: kick only              MODE 3: energy / angular momentum sums
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) k_force(PartK<T> p, const SysK *sk, const double *__restrict__ cen,
+                                               T dt, T *ax, T *ay, T *az, double *diag) {
+    __shared__ SysK s;
+    stage_sys(s, sk);
+    double dsum[7] = {0, 0, 0, 0, 0, 0, 0};
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += stride) {
+        if (p.flags[i] & PM_FLAG_LOST) {
+            if (MODE == 1) { ax[i] = 0; ay[i] = 0; az[i] = 0; }
+            continue;
+        }
+        const T xT = p.x[i], yT = p.y[i], zT = p.z[i];
+        const double x = (double)xT, y = (double)yT, z = (double)zT;
+        const float sx = pm_off32(x, s.sc[0]), sy = pm_off32(y, s.sc[1]), sz = pm_off32(z, s.sc[2]);
+        const T rsx = rel_off<T>(x, s.sc[0]), rsy = rel_off<T>(y, s.sc[1]), rsz = rel_off<T>(z, s.sc[2]);
+        T acc[3] = {0, 0, 0};
+        T phiv = 0;
+        T *php = (MODE == 3) ? &phiv : nullptr;
+        for (int h = 0; h < s.ngal; ++h) {
+            const GalK &G = s.gal[h];
+            const double cx = cen[3 * h], cy = cen[3 * h + 1], cz = cen[3 * h + 2];
+            const float fx = pm_off32(x, cx), fy = pm_off32(y, cy), fz = pm_off32(z, cz);
+            Cell cf, cm;
+            const int reg = pm_region(G, fx, fy, fz, cf, cm);
+            const Cell cc = pm_cells(G.coarse, sx, sy, sz);
+            if (!cc.ok) continue;  // only after positions changed without a deposit
+            T dx, dy, dz;
+            cell_delta(G.coarse, cc, rsx, rsy, rsz, dx, dy, dz);
+            stencil<T>(G.coarse, static_cast<const T *>(G.phi[4]),
+                       reg == REG_OUTER ? static_cast<const T *>(G.phi[3]) : nullptr, cc, dx, dy, dz, acc, php);
+            if (reg != REG_OUTER) {
+                const T rx = rel_off<T>(x, cx), ry = rel_off<T>(y, cy), rz = rel_off<T>(z, cz);
+                cell_delta(G.med, cm, rx, ry, rz, dx, dy, dz);
+                stencil<T>(G.med, static_cast<const T *>(G.phi[2]),
+                           reg == REG_SHELL ? static_cast<const T *>(G.phi[1]) : nullptr, cm, dx, dy, dz, acc, php);
+                if (reg == REG_CORE) {
+                    cell_delta(G.fine, cf, rx, ry, rz, dx, dy, dz);
+                    stencil<T>(G.fine, static_cast<const T *>(G.phi[0]), nullptr, cf, dx, dy, dz, acc, php);
+                }
+            }
+        }
+        if (MODE == 0) {
+            const T vx = p.vx[i] + dt * acc[0], vy = p.vy[i] + dt * acc[1], vz = p.vz[i] + dt * acc[2];
+            p.vx[i] = vx; p.vy[i] = vy; p.vz[i] = vz;
+            p.x[i] = xT + dt * vx; p.y[i] = yT + dt * vy; p.z[i] = zT + dt * vz;
+        } else if (MODE == 1) {
+            ax[i] = acc[0]; ay[i] = acc[1]; az[i] = acc[2];
+        } else if (MODE == 2) {
+            p.vx[i] += dt * acc[0]; p.vy[i] += dt * acc[1]; p.vz[i] += dt * acc[2];
+        } else {
+            const double hdt = 0.5 * (double)dt;
+            const double vx = (double)p.vx[i] + hdt * (double)acc[0];
+            const double vy = (double)p.vy[i] + hdt * (double)acc[1];
+            const double vz = (double)p.vz[i] + hdt * (double)acc[2];
+            const double m = (double)p.m[i];
+            dsum[0] += 0.5 * m * (vx * vx + vy * vy + vz * vz);
+            dsum[1] += -0.5 * m * (double)phiv;
+            dsum[3] += m * (y * vz - z * vy);
+            dsum[4] += m * (z * vx - x * vz);
+            dsum[5] += m * (x * vy - y * vx);
+            dsum[6] += 1.0;
+        }
+    }
+    if (MODE == 3) {
+        dsum[2] = dsum[0] + dsum[1];
+        __shared__ double red[8][7];
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+        for (int k = 0; k < 7; ++k) {
+            const double v = warp_sum(dsum[k]);
+            if (lane == 0) red[w][k] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < 7) {
+            double v = 0;
+            for (int k = 0; k < (int)(blockDim.x >> 5); ++k) v += red[k][threadIdx.x];
+            atomicAdd(diag + threadIdx.x, v);
+        }
+    }
+}
+
+__device__ __forceinline__ long long warp_sum_ll(long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Step a1: exact integer centre-of-mass sums within R_core of each galaxy's
+// current centre: sum M, sum M*D (M = q >> 26, D = rint(d * 2^sD)).
+template <typename T>
+__global__ void __launch_bounds__(256) k_recentre_sum(PartK<T> p, const SysK *sk, const double *__restrict__ cen,
+                                                      unsigned long long *sums) {
+    __shared__ SysK s;
+    stage_sys(s, sk);
+    long long acc[PM_MAX_GALAXIES][4];
+#pragma unroll
+    for (int h = 0; h < PM_MAX_GALAXIES; ++h)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc[h][k] = 0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += stride) {
+        if (p.flags[i] & PM_FLAG_LOST) continue;
+        const int g = p.gal[i];
+        if (g < 0 || g >= s.ngal || !s.gal[g].recentre) continue;
+        const float dx = pm_off32((double)p.x[i], cen[3 * g]);
+        const float dy = pm_off32((double)p.y[i], cen[3 * g + 1]);
+        const float dz = pm_off32((double)p.z[i], cen[3 * g + 2]);
+        if (!(pm_r2(dx, dy, dz) < s.gal[g].rc2)) continue;
+        const long long M = __double2ll_rn(__dmul_rn((double)p.m[i], s.mscale)) >> 26;
+        const int sD = s.gal[g].sD;
+        const long long Dx = __float2ll_rn(ldexpf(dx, sD));
+        const long long Dy = __float2ll_rn(ldexpf(dy, sD));
+        const long long Dz = __float2ll_rn(ldexpf(dz, sD));
+#pragma unroll
+        for (int h = 0; h < PM_MAX_GALAXIES; ++h)
+            if (h == g) { acc[h][0] += M; acc[h][1] += M * Dx; acc[h][2] += M * Dy; acc[h][3] += M * Dz; }
+    }
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int h = 0; h < PM_MAX_GALAXIES; ++h) {
+        if (h >= s.ngal) break;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const long long v = warp_sum_ll(acc[h][k]);
+            if (lane == 0 && v != 0) atomicAdd(sums + 4 * h + k, (unsigned long long)v);
+        }
+    }
+}
+
+static __global__ void k_recentre_apply(const SysK *sk, double *cen, unsigned long long *sums, int ngal) {
+    const int g = threadIdx.x;
+    if (g >= ngal) return;
+    const long long M = (long long)sums[4 * g];
+    if (sk->gal[g].recentre && M > 0) {
+        const double sc = ldexp(1.0, -sk->gal[g].sD);
+        for (int k = 0; k < 3; ++k) {
+            const long long MD = (long long)sums[4 * g + 1 + k];
+            cen[3 * g + k] = __dadd_rn(cen[3 * g + k], __dmul_rn(__ddiv_rn(__ll2double_rn(MD), __ll2double_rn(M)), sc));
+        }
+    }
+    for (int k = 0; k < 4; ++k) sums[4 * g + k] = 0;
+}
+
+template <typename T>
+__global__ void k_count_lost(PartK<T> p, unsigned long long *out) {
+    unsigned long long c = 0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += stride)
+        c += (p.flags[i] & PM_FLAG_LOST) ? 1 : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
+template <typename T>
+__global__ void k_store_hhat(const double *in, T *out, long long n, double scale) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = (T)(in[i] * scale);
+}
+
+}  // namespace pmk
+
+// ---------------------------------------------------------------------------
+// Host launchers (explicitly instantiated per precision)
+// ---------------------------------------------------------------------------
+namespace pmk_host {
+
+inline int particle_grid(long long n) {
+    long long b = (n + 255) / 256;
+    const long long cap = 152LL * 8;
+    return (int)(b < cap ? (b > 0 ? b : 1) : cap);
+}
+
+template <typename T, int L> cudaError_t attrs_L() {
+    cudaError_t e;
+    e = cudaFuncSetAttribute(pmk::k_xfwd<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pmk::xpass_smem<T, L>());
+    if (e) return e;
+    e = cudaFuncSetAttribute(pmk::k_xinv<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pmk::xpass_smem<T, L>());
+    if (e) return e;
+    e = cudaFuncSetAttribute(pmk::k_col<T, L, COL_YFWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pmk::col_smem<T, L>());
+    if (e) return e;
+    e = cudaFuncSetAttribute(pmk::k_col<T, L, COL_ZCONV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pmk::col_smem<T, L>());
+    if (e) return e;
+    return cudaFuncSetAttribute(pmk::k_col<T, L, COL_YINV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pmk::col_smem<T, L>());
+}
+
+template <typename T, int L> cudaError_t xfwd_L(const FftArgs &a, int nsets, cudaStream_t st) {
+    dim3 grid((unsigned)((a.nitems + pmk::XShape<L>::LINES - 1) / pmk::XShape<L>::LINES), nsets);
+    pmk::k_xfwd<T, L><<<grid, pmk::NT, pmk::xpass_smem<T, L>(), st>>>(a);
+    return cudaGetLastError();
+}
+template <typename T, int L> cudaError_t xinv_L(const FftArgs &a, int nsets, cudaStream_t st) {
+    dim3 grid((unsigned)((a.nitems + pmk::XShape<L>::LINES - 1) / pmk::XShape<L>::LINES), nsets);
+    pmk::k_xinv<T, L><<<grid, pmk::NT, pmk::xpass_smem<T, L>(), st>>>(a);
+    return cudaGetLastError();
+}
+template <typename T, int L> cudaError_t col_L(const FftArgs &a, int mode, int nsets, cudaStream_t st) {
+    dim3 grid((unsigned)((a.nitems + pmk::CShape<L>::COLS - 1) / pmk::CShape<L>::COLS), nsets);
+    const size_t sm = pmk::col_smem<T, L>();
+    if (mode == COL_YFWD) pmk::k_col<T, L, COL_YFWD><<<grid, pmk::NT, sm, st>>>(a);
+    else if (mode == COL_ZCONV) pmk::k_col<T, L, COL_ZCONV><<<grid, pmk::NT, sm, st>>>(a);
+    else pmk::k_col<T, L, COL_YINV><<<grid, pmk::NT, sm, st>>>(a);
+    return cudaGetLastError();
+}
+
+#define PM_SWITCH_L(L, CALL)                          \
+    switch (L) {                                      \
+        case 16: return CALL(16);                     \
+        case 32: return CALL(32);                     \
+        case 64: return CALL(64);                     \
+        case 128: return CALL(128);                   \
+        case 256: return CALL(256);                   \
+        case 512: return CALL(512);                   \
+        default: return cudaErrorInvalidValue;        \
+    }
+
+}  // namespace pmk_host
+
+template <typename T> cudaError_t pm_set_attrs() {
+    cudaError_t e;
+    if ((e = pmk_host::attrs_L<T, 16>())) return e;
+    if ((e = pmk_host::attrs_L<T, 32>())) return e;
+    if ((e = pmk_host::attrs_L<T, 64>())) return e;
+    if ((e = pmk_host::attrs_L<T, 128>())) return e;
+    if ((e = pmk_host::attrs_L<T, 256>())) return e;
+    return pmk_host::attrs_L<T, 512>();
+}
+
+template <typename T> cudaError_t pm_launch_xfwd(const FftArgs &a, int nsets, cudaStream_t st) {
+#define PM_XF(LL) pmk_host::xfwd_L<T, LL>(a, nsets, st)
+    PM_SWITCH_L(2 * a.nx, PM_XF)
+#undef PM_XF
+}
+template <typename T> cudaError_t pm_launch_xinv(const FftArgs &a, int nsets, cudaStream_t st) {
+#define PM_XI(LL) pmk_host::xinv_L<T, LL>(a, nsets, st)
+    PM_SWITCH_L(2 * a.nx, PM_XI)
+#undef PM_XI
+}
+template <typename T> cudaError_t pm_launch_col(const FftArgs &a, int mode, int nsets, cudaStream_t st) {
+    const int L = (mode == COL_ZCONV) ? 2 * a.nz : 2 * a.ny;
+#define PM_CO(LL) pmk_host::col_L<T, LL>(a, mode, nsets, st)
+    PM_SWITCH_L(L, PM_CO)
+#undef PM_CO
+}
+
+template <typename T>
+cudaError_t pm_launch_deposit(const PartK<T> &p, const SysK *sk, const double *cen, cudaStream_t st) {
+    if (p.n <= 0) return cudaSuccess;
+    pmk::k_deposit<T><<<pmk_host::particle_grid(p.n), 256, 0, st>>>(p, sk, cen);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t pm_launch_force(int mode, const PartK<T> &p, const SysK *sk, const double *cen, double dt,
+                            T *ax, T *ay, T *az, double *diag, cudaStream_t st) {
+    if (p.n <= 0) return cudaSuccess;
+    const int g = pmk_host::particle_grid(p.n);
+    switch (mode) {
+        case 0: pmk::k_force<T, 0><<<g, 256, 0, st>>>(p, sk, cen, (T)dt, ax, ay, az, diag); break;
+        case 1: pmk::k_force<T, 1><<<g, 256, 0, st>>>(p, sk, cen, (T)dt, ax, ay, az, diag); break;
+        case 2: pmk::k_force<T, 2><<<g, 256, 0, st>>>(p, sk, cen, (T)dt, ax, ay, az, diag); break;
+        case 3: pmk::k_force<T, 3><<<g, 256, 0, st>>>(p, sk, cen, (T)dt, ax, ay, az, diag); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t pm_launch_recentre(const PartK<T> &p, const SysK *sk, double *cen, unsigned long long *sums,
+                               int ngal, cudaStream_t st) {
+    if (p.n > 0) pmk::k_recentre_sum<T><<<pmk_host::particle_grid(p.n), 256, 0, st>>>(p, sk, cen, sums);
+    pmk::k_recentre_apply<<<1, 32, 0, st>>>(sk, cen, sums, ngal);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t pm_launch_count_lost(const PartK<T> &p, unsigned long long *out, cudaStream_t st) {
+    if (p.n <= 0) return cudaSuccess;
+    pmk::k_count_lost<T><<<pmk_host::particle_grid(p.n), 256, 0, st>>>(p, out);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t pm_store_hhat(const double *in, T *out, long long n, double scale, cudaStream_t st) {
+    pmk::k_store_hhat<T><<<pmk_host::particle_grid(n), 256, 0, st>>>(in, out, n, scale);
+    return cudaGetLastError();
+}
+
+#define PM_INSTANTIATE(T)                                                                                       \
+    template cudaError_t pm_set_attrs<T>();                                                                    \
+    template cudaError_t pm_launch_xfwd<T>(const FftArgs &, int, cudaStream_t);                               \
+    template cudaError_t pm_launch_xinv<T>(const FftArgs &, int, cudaStream_t);                               \
+    template cudaError_t pm_launch_col<T>(const FftArgs &, int, int, cudaStream_t);                           \
+    template cudaError_t pm_launch_deposit<T>(const PartK<T> &, const SysK *, const double *, cudaStream_t);   \
+    template cudaError_t pm_launch_force<T>(int, const PartK<T> &, const SysK *, const double *, double, T *, \
+                                            T *, T *, double *, cudaStream_t);                                 \
+    template cudaError_t pm_launch_recentre<T>(const PartK<T> &, const SysK *, double *, unsigned long long *, \
+                                               int, cudaStream_t);                                             \
+    template cudaError_t pm_launch_count_lost<T>(const PartK<T> &, unsigned long long *, cudaStream_t);       \
+    template cudaError_t pm_store_hhat<T>(const double *, T *, long long, double, cudaStream_t);

@@ -1,0 +1,281 @@
+"""ctypes binding of libpm (include/pm.h): argument marshalling only.
+
+Every step of the particle-mesh path runs in the library's CUDA kernels; this
+module only turns Python/PyTorch objects into the C structs and pointers the
+C ABI takes.  There is no fallback: if libpm.so is missing, importing the
+library raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpm.so")
+
+PM_OK, PM_E_ARG, PM_E_QCRIT, PM_E_NESTING, PM_E_OVERFLOW, PM_E_CUDA, PM_E_STATE = 0, -1, -2, -3, -4, -5, -6
+PM_FP32, PM_FP64 = 1, 2
+PM_FLAG_LOST = 1
+PM_MAX_GALAXIES = 8
+
+# Names declared in include/pm.h, with (restype, argtypes).
+_vp = C.c_void_p
+_SIGS = {}
+
+
+class pm_geometry(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+                ("l_xy", C.c_double), ("l_z", C.c_double)]
+
+
+class pm_galaxy(C.Structure):
+    _fields_ = [("coarse", pm_geometry), ("medium", pm_geometry), ("fine", pm_geometry),
+                ("r_core", C.c_double), ("r_out", C.c_double),
+                ("centre", C.c_double * 3), ("recentre", C.c_int32)]
+
+
+class pm_system(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("ngal", C.c_int32),
+                ("G", C.c_double), ("h000", C.c_double), ("r_sys", C.c_double),
+                ("sys_centre", C.c_double * 3), ("mass_bound", C.c_double)]
+
+
+class pm_particles(C.Structure):
+    _fields_ = [("x", _vp), ("y", _vp), ("z", _vp), ("vx", _vp), ("vy", _vp), ("vz", _vp),
+                ("m", _vp), ("gal", _vp), ("flags", _vp), ("n", C.c_int64)]
+
+
+_P = C.POINTER
+_SIGS.update({
+    "pm_cell_length": (C.c_double, [C.c_double, C.c_int32, C.c_double]),
+    "pm_q_crit": (C.c_double, [C.c_double, C.c_double, C.c_double, C.c_int32]),
+    "pm_fixed_shift": (C.c_int32, [C.c_double]),
+    "pm_last_error": (C.c_char_p, []),
+    "pm_create_grids": (C.c_int, [_P(pm_system), _P(pm_galaxy), _vp, _P(_vp)]),
+    "pm_destroy": (None, [_vp]),
+    "pm_set_stream": (C.c_int, [_vp, _vp]),
+    "pm_recentre": (C.c_int, [_vp, _P(pm_particles)]),
+    "pm_deposit": (C.c_int, [_vp, _P(pm_particles)]),
+    "pm_solve": (C.c_int, [_vp]),
+    "pm_force": (C.c_int, [_vp, _P(pm_particles), _vp, _vp, _vp]),
+    "pm_kick": (C.c_int, [_vp, _P(pm_particles), C.c_double]),
+    "pm_step": (C.c_int, [_vp, _P(pm_particles), C.c_double, C.c_int32]),
+    "pm_diagnostics": (C.c_int, [_vp, _P(pm_particles), C.c_double, _P(C.c_double)]),
+    "pm_get_density": (C.c_int, [_vp, C.c_int32, C.c_int32, _vp]),
+    "pm_get_potential": (C.c_int, [_vp, C.c_int32, C.c_int32, _vp]),
+    "pm_get_centres": (C.c_int, [_vp, _P(C.c_double)]),
+    "pm_set_centres": (C.c_int, [_vp, _P(C.c_double)]),
+    "pm_count_lost": (C.c_int, [_vp, _P(pm_particles), _P(C.c_int64)]),
+    "pm_info": (C.c_int, [_vp, _P(C.c_int64)]),
+    "pm_step_timed": (C.c_int, [_vp, _P(pm_particles), C.c_double, C.c_int32, _P(C.c_float)]),
+})
+
+_lib = None
+
+
+def lib():
+    """The loaded libpm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libpm.so not found at {LIB_PATH}: build it with "
+                              "`python -m paper_1210_1736_gb300.build` (no CPU fallback exists)")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+class PMError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"pm error {code}: {msg}")
+        self.code = code
+
+
+def _check(rc):
+    if rc != PM_OK:
+        raise PMError(rc, lib().pm_last_error().decode())
+    return rc
+
+
+def cell_length(R, N, q=1.0):
+    return lib().pm_cell_length(float(R), int(N), float(q))
+
+
+def q_crit(r_core, r_out, r_sys, N):
+    return lib().pm_q_crit(float(r_core), float(r_out), float(r_sys), int(N))
+
+
+def fixed_shift(mass_bound):
+    return lib().pm_fixed_shift(float(mass_bound))
+
+
+def geometry(spec):
+    """(nx, ny, nz, R, q) -> pm_geometry with l_xy = 2R/(nx-4), l_z = q l_xy;
+    None -> absent geometry."""
+    g = pm_geometry()
+    if spec is None:
+        return g
+    nx, ny, nz, R, q = spec
+    g.nx, g.ny, g.nz = int(nx), int(ny), int(nz)
+    g.l_xy = cell_length(R, nx, 1.0)
+    g.l_z = float(q) * g.l_xy
+    return g
+
+
+def describe(workload, mass_bound):
+    """pm_system and pm_galaxy[] of a workload dict (see workloads.py)."""
+    gals = (pm_galaxy * PM_MAX_GALAXIES)()
+    for i, g in enumerate(workload["galaxies"]):
+        gals[i].coarse = geometry(g["coarse"])
+        gals[i].medium = geometry(g.get("medium"))
+        gals[i].fine = geometry(g.get("fine"))
+        gals[i].r_core = float(g["r_core"])
+        gals[i].r_out = float(g["r_out"])
+        for k in range(3):
+            gals[i].centre[k] = float(g["centre"][k])
+        gals[i].recentre = 1 if g["recentre"] else 0
+    s = workload["system"]
+    sysd = pm_system()
+    sysd.precision = PM_FP32 if workload["precision"] == "fp32" else PM_FP64
+    sysd.ngal = len(workload["galaxies"])
+    sysd.G = float(s["G"])
+    sysd.h000 = float(s["h000"])
+    sysd.r_sys = float(s["r_sys"])
+    for k in range(3):
+        sysd.sys_centre[k] = float(s["sys_centre"][k])
+    sysd.mass_bound = float(mass_bound)
+    return sysd, gals
+
+
+class Particles:
+    """Device-resident structure-of-arrays particle set (torch tensors)."""
+
+    def __init__(self, pos, vel, m, gal, precision="fp32", device="cuda"):
+        import torch
+        dt = torch.float32 if precision == "fp32" else torch.float64
+        self.dtype = dt
+        pos = np.asarray(pos)
+        vel = np.asarray(vel)
+        self.x, self.y, self.z = (torch.as_tensor(np.ascontiguousarray(pos[k]), dtype=dt).to(device) for k in range(3))
+        self.vx, self.vy, self.vz = (torch.as_tensor(np.ascontiguousarray(vel[k]), dtype=dt).to(device) for k in range(3))
+        self.m = torch.as_tensor(np.ascontiguousarray(m), dtype=dt).to(device)
+        self.gal = torch.as_tensor(np.ascontiguousarray(gal), dtype=torch.int32).to(device)
+        self.flags = torch.zeros(len(self.m), dtype=torch.int32, device=device)
+        self.n = len(self.m)
+
+    def struct(self):
+        p = pm_particles()
+        for k in ("x", "y", "z", "vx", "vy", "vz", "m", "gal", "flags"):
+            setattr(p, k, getattr(self, k).data_ptr())
+        p.n = self.n
+        return p
+
+    def host(self):
+        import torch  # noqa: F401
+        pos = np.stack([t.cpu().numpy().astype(np.float64) for t in (self.x, self.y, self.z)])
+        vel = np.stack([t.cpu().numpy().astype(np.float64) for t in (self.vx, self.vy, self.vz)])
+        return pos, vel, self.flags.cpu().numpy().astype(np.int64)
+
+
+class Context:
+    """One pm_ctx: the grids, H-hat tables and work buffers of a system."""
+
+    def __init__(self, workload, mass_bound, stream=None):
+        import torch
+        self.workload = workload
+        self.sys, self.gals = describe(workload, mass_bound)
+        self.precision = workload["precision"]
+        self.np_dtype = np.float32 if self.precision == "fp32" else np.float64
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        h = _vp()
+        _check(lib().pm_create_grids(C.byref(self.sys), self.gals, _vp(stream), C.byref(h)))
+        self.h = h
+        self.shapes = {}
+        for gi, g in enumerate(workload["galaxies"]):
+            specs = {1: g.get("fine"), 2: g.get("medium"), 3: g.get("medium"), 4: g["coarse"], 5: g["coarse"]}
+            for k, sp in specs.items():
+                if sp is None or (k in (1,) and g.get("medium") is None) or (k == 4 and g.get("medium") is None):
+                    continue
+                self.shapes[(gi, k)] = (int(sp[2]), int(sp[1]), int(sp[0]))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().pm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        _check(lib().pm_set_stream(self.h, _vp(stream)))
+
+    def recentre(self, p):
+        _check(lib().pm_recentre(self.h, C.byref(p.struct())))
+
+    def deposit(self, p):
+        _check(lib().pm_deposit(self.h, C.byref(p.struct())))
+
+    def solve(self):
+        _check(lib().pm_solve(self.h))
+
+    def force(self, p):
+        import torch
+        a = [torch.empty(p.n, dtype=p.dtype, device=p.x.device) for _ in range(3)]
+        _check(lib().pm_force(self.h, C.byref(p.struct()), a[0].data_ptr(), a[1].data_ptr(), a[2].data_ptr()))
+        return a
+
+    def kick(self, p, dt):
+        _check(lib().pm_kick(self.h, C.byref(p.struct()), float(dt)))
+
+    def step(self, p, dt, nsteps=1):
+        _check(lib().pm_step(self.h, C.byref(p.struct()), float(dt), int(nsteps)))
+
+    def step_timed(self, p, dt, nsteps=1):
+        out = (C.c_float * 9)()
+        _check(lib().pm_step_timed(self.h, C.byref(p.struct()), float(dt), int(nsteps), out))
+        return list(out)
+
+    def diagnostics(self, p, dt):
+        out = (C.c_double * 8)()
+        _check(lib().pm_diagnostics(self.h, C.byref(p.struct()), float(dt), out))
+        return {"K": out[0], "W": out[1], "E": out[2], "L": np.array(out[3:6]), "n_live": int(out[6])}
+
+    def density(self, gal, k):
+        a = np.empty(self.shapes[(gal, k)], dtype=np.int64)
+        _check(lib().pm_get_density(self.h, gal, k, a.ctypes.data))
+        return a
+
+    def potential(self, gal, k):
+        a = np.empty(self.shapes[(gal, k)], dtype=self.np_dtype)
+        _check(lib().pm_get_potential(self.h, gal, k, a.ctypes.data))
+        return a
+
+    def centres(self):
+        n = self.sys.ngal
+        out = (C.c_double * (3 * n))()
+        _check(lib().pm_get_centres(self.h, out))
+        return np.array(out).reshape(n, 3)
+
+    def set_centres(self, c):
+        c = np.ascontiguousarray(np.asarray(c, dtype=np.float64).ravel())
+        _check(lib().pm_set_centres(self.h, c.ctypes.data_as(_P(C.c_double))))
+
+    def count_lost(self, p):
+        out = C.c_int64()
+        _check(lib().pm_count_lost(self.h, C.byref(p.struct()), C.byref(out)))
+        return out.value
+
+    def info(self):
+        out = (C.c_int64 * 4)()
+        _check(lib().pm_info(self.h, out))
+        return {"shift": out[0], "nsets": out[1], "ngeom": out[2], "bytes": out[3]}

@@ -110,5 +110,7 @@ def merger(n_gal=4_000_000, n_sat=100_000, grids=((128,), (128,), (256, 256, 32)
 
 
 def mass_bound(m):
-    """Upper bound on sum |m| handed to both sides (fixes the fixed-point scale)."""
-    return float(np.abs(np.asarray(m, dtype=np.float64)).sum())
+    """Upper bound on sum |m| handed to both sides (fixes the fixed-point scale);
+    1 for an empty set."""
+    s = float(np.abs(np.asarray(m, dtype=np.float64)).sum())
+    return s if s > 0 else 1.0
