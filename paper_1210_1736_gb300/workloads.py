@@ -13,8 +13,9 @@ plummer32   65,536-particle Plummer sphere (M = a = G = 1) truncated at
 galaxy_1m   disc (400k) + Hernquist bulge (100k) + truncated NFW halo (500k);
             grids: coarse 128^3 (R_sys = 32), medium 128^3 flattened q = 1/4
             (R_out = 6), fine 128x128x32 (R_core = 1.5); dt = 0.01.
-galaxy_small  the same model scaled to 48k particles on 32^3 / 32^3 / 32x32x8
-            grids (fast enough for the oracle inside a test).
+galaxy_small  the same model scaled to 48k particles on 32^3 / 32^3 (q = 0.8,
+            the smallest admissible at N = 32) / 32x32x8 grids (fast enough for
+            the oracle inside a test).
 merger_4m   galaxy scaled to 4M particles plus a 100k Plummer satellite; six
             geometries (galaxy 128^3, 128^3, 256x256x32; satellite 64^3 x 3).
 """
@@ -57,14 +58,14 @@ def _galaxy_particles(n_total, seed_id):
 
 
 def galaxy(n_total=1_000_000, n_c=128, n_m=128, n_f=(128, 128, 32), seed_id=1,
-           precision="fp32", name=None):
+           precision="fp32", name=None, q_m=0.25):
     pos, vel, m = _galaxy_particles(n_total, seed_id)
     pos, vel, m = synth.scramble(synth.rng_for(seed_id, 9), pos, vel, m)
     n = pos.shape[1]
     return dict(
         name=name or f"galaxy_{n_total}", precision=precision, dt=0.01, steps=100,
         system=dict(r_sys=GALAXY_RADII["r_sys"], sys_centre=(0.0, 0.0, 0.0), G=1.0, h000=1.0),
-        galaxies=[_galaxy_spec(n_c, n_m, n_f)],
+        galaxies=[_galaxy_spec(n_c, n_m, n_f, q_m=q_m)],
         pos=pos, vel=vel, m=m, gal=np.zeros(n, dtype=np.int32))
 
 
@@ -74,8 +75,10 @@ def galaxy_1m(precision="fp32"):
 
 
 def galaxy_small(precision="fp32", n_total=48_000, seed_id=11):
+    # q_crit(N=32) = 4/28 * 32/6 = 0.76 for these radii: the medium grid is
+    # flattened by 0.8 here (1/4 needs N >= 128)
     return galaxy(n_total, 32, 32, (32, 32, 8), seed_id=seed_id, precision=precision,
-                  name="galaxy_small")
+                  name="galaxy_small", q_m=0.8)
 
 
 def merger(n_gal=4_000_000, n_sat=100_000, grids=((128,), (128,), (256, 256, 32), (64,)),

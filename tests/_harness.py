@@ -59,4 +59,5 @@ def rel_force_errors(a_gpu, a_ref, live):
     rms_ref = np.sqrt(np.mean(np.sum(ref * ref, axis=0)))
     rms = np.sqrt(np.mean(np.sum(d * d, axis=0))) / rms_ref
     mx = np.max(np.sqrt(np.sum(d * d, axis=0))) / rms_ref
+    print(f"force error: rms {rms:.3e} max {mx:.3e} (RMS-normalised, {d.shape[1]} particles)")
     return rms, mx

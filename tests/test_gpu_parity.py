@@ -87,18 +87,20 @@ def test_plummer32_fp64_ten_steps():
     assert bad <= max(3, live.sum() // 10000), (bad, dpos.max())
 
 
-@pytest.mark.parametrize("shape", [(256, 16, 8), (8, 256, 16), (16, 8, 256), (64, 32, 128)])
+@pytest.mark.parametrize("shape", [(256, 16, 8, 1.0), (8, 256, 16, 1.0), (16, 8, 256, 1.0),
+                                   (64, 32, 128, 0.25)])
 def test_fp64_potential_all_transform_lengths(shape):
-    """Every transform length 16..512 on each axis, FP64, random masses."""
-    nx, ny, nz = shape
+    """Every transform length 16..512 on each axis, FP64, random masses; the
+    last case has flattened cells (l_z = l_xy / 4)."""
+    nx, ny, nz, q = shape
     rng = np.random.default_rng(hash(shape) % 2**32)
     n = 4000
     l = 0.1
     half = np.array([nx, ny, nz]) / 2 - 3
-    pos = (rng.uniform(-1, 1, (3, n)) * half[:, None]) * l
+    pos = (rng.uniform(-1, 1, (3, n)) * half[:, None]) * np.array([[l], [l], [l * q]])
     w = dict(name="box", precision="fp64", dt=0.01,
              system=dict(r_sys=1e9, sys_centre=(0.0, 0.0, 0.0), G=1.0, h000=1.0),
-             galaxies=[dict(coarse=(nx, ny, nz, l * (nx - 4) / 2, 1.0), medium=None, fine=None,
+             galaxies=[dict(coarse=(nx, ny, nz, l * (nx - 4) / 2, q), medium=None, fine=None,
                             r_core=0.0, r_out=0.0, centre=(0.0, 0.0, 0.0), recentre=False)],
              pos=pos, vel=np.zeros_like(pos), m=rng.uniform(0.5, 2.0, n),
              gal=np.zeros(n, np.int32))
