@@ -171,6 +171,35 @@ int pm_info(pm_ctx *ctx, int64_t *host_out);  /* [shift, nsets, ngeom, bytes] */
 int pm_step_timed(pm_ctx *ctx, const pm_particles *p, double dt, int32_t nsteps,
                   float *ms_out);
 
+/* Allocation-free potential of one isolated grid.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc (a host application whose device memory is pre-partitioned by
+ * its own pool, a plugin that may not allocate after start-up, code issued
+ * while another thread captures a CUDA graph in global mode).
+ *
+ * Computes what pm_solve computes for one grid: Phi = G/l_xy * (rho * H) on
+ * the nx*ny*nz active region of the doubled grid, with H-hat rebuilt in FP64
+ * on every call.  rho: device int64 density, layout [z][y][x], mass per cell
+ * in units of 2^-shift (the fixed point of pm_deposit); phi: device output,
+ * float (precision PM_FP32) or double (PM_FP64), same layout.  Both are the
+ * caller's.  Work is enqueued on `stream` (a cudaStream_t, NULL = legacy
+ * default stream); the call returns without waiting for it.
+ *
+ * Scratch: every intermediate lives in one file-scope device array of
+ * 32 MiB that each GPU loading the library holds until the process exits;
+ * the call allocates and frees nothing.  A grid whose intermediates exceed
+ * 32 MiB is refused with PM_E_ARG (e.g. 64^3 in FP64 and 128x128x32 in FP32
+ * fit; 128^3 does not).  All calls on a device share the array and it keeps
+ * the previous call's contents; each call writes every scratch value before
+ * reading it, so nothing needs clearing, but calls whose work overlaps on the
+ * GPU (different streams, or other threads) race on it and must be ordered
+ * by the caller.  The first call on a device looks up the array's device
+ * address and sets kernel attributes, so it should come before any stream
+ * capture that includes later calls. */
+int pm_potential_static(const int64_t *rho, void *phi, int32_t nx, int32_t ny, int32_t nz,
+                        double l_xy, double l_z, double G, double h000, int32_t shift,
+                        int32_t precision, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

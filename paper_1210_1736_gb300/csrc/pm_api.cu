@@ -371,6 +371,11 @@ template <typename T> int force_impl(pm_ctx *c, int mode, const pm_particles *p,
 
 }  // namespace
 
+int pm_internal_fail(int code, const char *msg) {
+    g_err = msg;
+    return code;
+}
+
 // ============================================================================
 extern "C" {
 

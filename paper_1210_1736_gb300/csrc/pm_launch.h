@@ -44,3 +44,7 @@ cudaError_t pm_axis_transform(const double *in, double *out, const double *cmat,
                               long long outer, long long inner, cudaStream_t st);
 template <typename T>
 cudaError_t pm_store_hhat(const double *in, T *out, long long n, double scale, cudaStream_t st);
+
+// Records a message for pm_last_error() and returns code (C++ linkage; for
+// translation units other than the C ABI file).
+int pm_internal_fail(int code, const char *msg);

@@ -1,0 +1,192 @@
+// pm_potential_static: the isolated-boundary potential of one grid without
+// any device allocation.
+//
+// Some callers cannot call cudaMalloc: code embedded in a host application
+// whose device memory is pre-partitioned by its own pool (a cudaMalloc there
+// fails or synchronises the whole device), plugins that may not allocate after
+// start-up, and code issued while another thread captures a CUDA graph in
+// global mode (allocation is illegal during such a capture).  This entry point
+// serves them: the caller passes the density and the output array, and every
+// intermediate (spectrum, H-hat, the FP64 temporaries of the H-hat build and
+// the twiddle tables) lives in one file-scope __device__ array of fixed size
+// that every GPU loading the library holds until the process exits.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "pm.h"
+#include "pm_launch.h"
+
+#define PM_STATIC_SCRATCH_BYTES (32u << 20)
+#define PM_STATIC_MAX_DEVICES 64
+
+// The scratch.  Host code must not hand this name to a kernel: on the host it
+// is a stand-in symbol, not a device address; its device address is taken
+// with cudaGetSymbolAddress once per device (the set-up block of
+// pm_potential_static).
+static __device__ __align__(256) unsigned char g_pm_static_scratch[PM_STATIC_SCRATCH_BYTES];
+
+namespace {
+
+std::mutex g_mu;
+void *g_ptr[PM_STATIC_MAX_DEVICES];
+bool g_attrs[PM_STATIC_MAX_DEVICES][2];
+
+// Reports through pm_last_error().
+int sfail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    return pm_internal_fail(code, buf);
+}
+
+__global__ void k_static_cosmat(double *c, int n) {
+    // c[m][i] = w_i cos(pi m i / n), w_0 = w_n = 1, else 2 (n a power of two)
+    const int n1 = n + 1;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n1 * n1; e += gridDim.x * blockDim.x) {
+        const int m = e / n1, i = e % n1;
+        const long long r = ((long long)m * i) % (2LL * n);
+        c[e] = ((i == 0 || i == n) ? 1.0 : 2.0) * cospi((double)r / (double)n);
+    }
+}
+
+template <typename T>
+__global__ void k_static_twiddles(typename cplx_t<T>::type *tw, int L) {
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < L; m += gridDim.x * blockDim.x) {
+        double s, c;
+        sincospi(2.0 * (double)m / (double)L, &s, &c);
+        tw[m].x = (T)c;
+        tw[m].y = (T)(-s);
+    }
+}
+
+size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+bool pow2_ok(int n) { return n >= 8 && n <= 256 && (n & (n - 1)) == 0; }
+
+template <typename T>
+int run(const int64_t *rho, void *phi, int nx, int ny, int nz, double l_xy, double l_z, double G, double h000,
+        int shift, unsigned char *base, cudaStream_t st) {
+    typedef typename cplx_t<T>::type C;
+    const size_t P = nx + 1, oct = (size_t)(nx + 1) * (ny + 1) * (nz + 1);
+    const int nmax = std::max(nx, std::max(ny, nz)) + 1;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { unsigned char *p = base + off; off += up256(bytes); return p; };
+    C *work = (C *)take((size_t)nz * 2 * ny * P * sizeof(C));
+    T *hhat = (T *)take(oct * sizeof(T));
+    double *h = (double *)take(oct * sizeof(double));
+    double *t1 = (double *)take(oct * sizeof(double));
+    double *cm = (double *)take((size_t)nmax * nmax * sizeof(double));
+    C *twx = (C *)take((size_t)2 * nx * sizeof(C));
+    C *twy = (C *)take((size_t)2 * ny * sizeof(C));
+    C *twz = (C *)take((size_t)2 * nz * sizeof(C));
+
+#define SCK(call)                                                                               \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess) return sfail(PM_E_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+    k_static_twiddles<T><<<1, 256, 0, st>>>(twx, 2 * nx);
+    k_static_twiddles<T><<<1, 256, 0, st>>>(twy, 2 * ny);
+    k_static_twiddles<T><<<1, 256, 0, st>>>(twz, 2 * nz);
+    SCK(cudaGetLastError());
+    // H-hat: FP64 octant of H, three cosine sums (x, y, z), scaled into T
+    SCK(pm_green_octant(h, nx, ny, nz, l_z / l_xy, h000, st));
+    k_static_cosmat<<<64, 256, 0, st>>>(cm, nx);
+    SCK(cudaGetLastError());
+    SCK(pm_axis_transform(h, t1, cm, nx + 1, (long long)(nz + 1) * (ny + 1), 1, st));
+    k_static_cosmat<<<64, 256, 0, st>>>(cm, ny);
+    SCK(cudaGetLastError());
+    SCK(pm_axis_transform(t1, h, cm, ny + 1, nz + 1, nx + 1, st));
+    k_static_cosmat<<<64, 256, 0, st>>>(cm, nz);
+    SCK(cudaGetLastError());
+    SCK(pm_axis_transform(h, t1, cm, nz + 1, 1, (long long)(ny + 1) * (nx + 1), st));
+    SCK(pm_store_hhat<T>(t1, hhat, (long long)oct, G / (l_xy * 8.0 * nx * ny * nz), st));
+
+    FftArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.rho[0] = (const long long *)rho;
+    a.work[0] = work;
+    a.phi[0] = phi;
+    a.hhat = hhat;
+    a.nx = nx; a.ny = ny; a.nz = nz; a.P = nx + 1;
+    a.scale = std::ldexp(1.0, -shift);
+    a.tw = twx;
+    a.nitems = (long long)ny * nz / 2;
+    SCK(pm_launch_xfwd<T>(a, 1, st));
+    a.tw = twy;
+    a.nitems = (long long)nz * (nx + 1);
+    SCK(pm_launch_col<T>(a, COL_YFWD, 1, st));
+    a.tw = twz;
+    a.nitems = (long long)2 * ny * (nx + 1);
+    SCK(pm_launch_col<T>(a, COL_ZCONV, 1, st));
+    a.tw = twy;
+    a.nitems = (long long)nz * (nx + 1);
+    SCK(pm_launch_col<T>(a, COL_YINV, 1, st));
+    a.tw = twx;
+    a.nitems = (long long)ny * nz / 2;
+    SCK(pm_launch_xinv<T>(a, 1, st));
+#undef SCK
+    return PM_OK;
+}
+
+size_t scratch_bytes(int nx, int ny, int nz, size_t esz) {
+    const size_t P = nx + 1, oct = (size_t)(nx + 1) * (ny + 1) * (nz + 1);
+    const size_t nmax = std::max(nx, std::max(ny, nz)) + 1;
+    return up256((size_t)nz * 2 * ny * P * 2 * esz) + up256(oct * esz) + 2 * up256(oct * 8) +
+           up256(nmax * nmax * 8) + up256((size_t)2 * nx * 2 * esz) + up256((size_t)2 * ny * 2 * esz) +
+           up256((size_t)2 * nz * 2 * esz);
+}
+
+}  // namespace
+
+extern "C" int pm_potential_static(const int64_t *rho, void *phi, int32_t nx, int32_t ny, int32_t nz, double l_xy,
+                                   double l_z, double G, double h000, int32_t shift, int32_t precision,
+                                   void *stream) {
+    if (!rho || !phi) return sfail(PM_E_ARG, "rho or phi is NULL");
+    if (precision != PM_FP32 && precision != PM_FP64) return sfail(PM_E_ARG, "precision must be PM_FP32 or PM_FP64");
+    if (!pow2_ok(nx) || !pow2_ok(ny) || !pow2_ok(nz))
+        return sfail(PM_E_ARG, "nx, ny, nz must be powers of two in [8, 256]");
+    if (!(l_xy > 0) || !(l_z > 0) || !std::isfinite(l_xy) || !std::isfinite(l_z) || !std::isfinite(G) ||
+        !std::isfinite(h000) || shift < -60 || shift > 1000)
+        return sfail(PM_E_ARG, "cell lengths must be positive, G and h000 finite, shift in [-60, 1000]");
+    const size_t need = scratch_bytes(nx, ny, nz, precision == PM_FP32 ? 4 : 8);
+    if (need > PM_STATIC_SCRATCH_BYTES)
+        return sfail(PM_E_ARG, "grid %dx%dx%d needs %zu bytes of scratch; the static scratch holds %u bytes", nx, ny,
+                     nz, need, (unsigned)PM_STATIC_SCRATCH_BYTES);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return sfail(PM_E_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    if (dev < 0 || dev >= PM_STATIC_MAX_DEVICES) return sfail(PM_E_ARG, "device %d out of range", dev);
+    unsigned char *base = nullptr;
+    {
+        // One-time set-up per device, with that device current: the device
+        // address of the scratch and the kernels' shared-memory limits.
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (!g_ptr[dev]) {
+            void *p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_pm_static_scratch);
+            if (e != cudaSuccess || !p)
+                return sfail(PM_E_CUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
+            g_ptr[dev] = p;
+        }
+        const int pi = precision == PM_FP32 ? 0 : 1;
+        if (!g_attrs[dev][pi]) {
+            e = precision == PM_FP32 ? pm_set_attrs<float>() : pm_set_attrs<double>();
+            if (e != cudaSuccess) return sfail(PM_E_CUDA, "kernel attributes: %s", cudaGetErrorString(e));
+            g_attrs[dev][pi] = true;
+        }
+        base = (unsigned char *)g_ptr[dev];
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    return precision == PM_FP32 ? run<float>(rho, phi, nx, ny, nz, l_xy, l_z, G, h000, shift, base, st)
+                                : run<double>(rho, phi, nx, ny, nz, l_xy, l_z, G, h000, shift, base, st);
+}

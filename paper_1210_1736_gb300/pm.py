@@ -70,6 +70,8 @@ _SIGS.update({
     "pm_count_lost": (C.c_int, [_vp, _P(pm_particles), _P(C.c_int64)]),
     "pm_info": (C.c_int, [_vp, _P(C.c_int64)]),
     "pm_step_timed": (C.c_int, [_vp, _P(pm_particles), C.c_double, C.c_int32, _P(C.c_float)]),
+    "pm_potential_static": (C.c_int, [_vp, _vp, C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_double,
+                                      C.c_double, C.c_double, C.c_int32, C.c_int32, _vp]),
 })
 
 _lib = None
