@@ -33,6 +33,7 @@ METRIC = "particle-steps/s per nested-grid step; FFT-convolve GB/s vs HBM peak"
 UNIT = "particle-steps/s"
 WORKLOAD = "galaxy_1m"
 PHASES = ["recentre", "deposit", "fft_x_fwd", "fft_y_fwd", "fft_z_conv", "fft_y_inv", "fft_x_inv", "force_kick_drift"]
+SORT_PHASE = 9
 
 
 def env_rank():
@@ -143,6 +144,7 @@ def phase_bytes(w, n, esz):
     b["recentre"] = n * (4 * esz + 8)
     b["deposit"] = n * (4 * esz + 8) + 8 * A_total
     b["force_kick_drift"] = n * (12 * esz + 4)
+    b["spatial_sort"] = 0.0
     return b
 
 
@@ -173,6 +175,7 @@ def run_ours(args):
     ctx.deposit(parts)
     ctx.solve()
     ctx.kick(parts, -0.5 * dt)
+    ctx.set_sort_interval(args.sort_every)
     ctx.step(parts, dt, Wm)
     torch.cuda.synchronize()
 
@@ -200,6 +203,7 @@ def run_ours(args):
     # ---- per-phase device times (same kernels, launched with events between phases) ----
     ph = ctx.step_timed(parts, dt, K)
     phase_ms = {p: ph[i] / K for i, p in enumerate(PHASES)}
+    phase_ms["spatial_sort"] = ph[SORT_PHASE] / K
     esz = 4
     pb = phase_bytes(w, n, esz)
     fft_phases = PHASES[2:7]
@@ -245,6 +249,7 @@ def run_ours(args):
                                "500k truncated NFW halo); grids coarse 128^3, medium 128^3 q=1/4, "
                                "fine 128x128x32; dt=0.01",
                    "particles_per_gpu": n, "grids": 5, "geometries": 3,
+                   "spatial_sort_every": args.sort_every,
                    "l2": "working set per step ~0.29 GB > 129 MB L2 (no flush needed)",
                    "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
@@ -311,6 +316,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sort-every", type=int, default=10,
+                    help="re-sort particles by cell every k steps inside the timed steps (0: never)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -162,12 +162,26 @@ int pm_set_centres(pm_ctx *ctx, const double *host_in);     /* ngal*3 */
 int pm_count_lost(pm_ctx *ctx, const pm_particles *p, int64_t *host_out);
 int pm_info(pm_ctx *ctx, int64_t *host_out);  /* [shift, nsets, ngeom, bytes] */
 
+/* Spatial sort (no counterpart in the paper; a locality optimisation of the
+ * NGP assignment of Eq. eqn:cell): permutes every particle array of p in
+ * place so that particles are ordered by galaxy, region (core, shell,
+ * outer) and cell of that region's grid (cells binned so a grid has at most
+ * 2^21 bins); lost particles go last.  Order within a cell is unspecified.
+ * If perm is not NULL (device int64[n]) it receives perm[new] = old.
+ * Results of the step do not depend on the order.  Allocates its scratch
+ * (about 44 bytes per particle) on first use. */
+int pm_sort(pm_ctx *ctx, const pm_particles *p, int64_t *perm);
+/* pm_step re-sorts the particles before every k-th step (k = 0: never, the
+ * default); resets the step counter so the next step sorts. */
+int pm_set_sort_interval(pm_ctx *ctx, int32_t k);
+
 /* Per-phase device time of the next `nsteps` steps, run without the graph,
  * with CUDA events on the context's launch stream between phases:
  * ms_out[0] recentre, [1] deposit (incl. zeroing), [2] x forward pass,
  * [3] y forward pass, [4] z pass (forward, H-hat multiply, inverse),
  * [5] y inverse pass, [6] x inverse pass, [7] force + kick-drift,
- * [8] whole steps; each the total over the steps.  Synchronises. */
+ * [8] whole steps, [9] spatial sort (steps where it is due); each the total
+ * over the steps (ms_out holds 10 floats).  Synchronises. */
 int pm_step_timed(pm_ctx *ctx, const pm_particles *p, double dt, int32_t nsteps,
                   float *ms_out);
 

@@ -28,7 +28,8 @@ def system_from_workload(w):
     s = w["system"]
     from paper_1210_1736_gb300.workloads import mass_bound
     return System(galaxies=gals, r_sys=s["r_sys"], sys_centre=tuple(s["sys_centre"]),
-                  G=s["G"], h000=s["h000"], mass_bound=mass_bound(w["m"]))
+                  G=s["G"], h000=s["h000"], mass_bound=mass_bound(w["m"]),
+                  precision=w.get("precision", "fp64"))
 
 
 def state_from_workload(w, pos=None, vel=None, m=None):

@@ -17,10 +17,14 @@ reason in the design notes of the repository):
   on a cubic grid feels exactly zero self-force under Eq. (eqn:diff).
 * "Nearest integer" in Eq. (eqn:cell) is floor(u + 1/2); cells are 0-based and
   cell N/2 is centred on the grid centre.
-* The cell index is evaluated by one canonical rounding sequence (one FP64
-  subtraction rounded to FP32, then FP32 multiply/add, no fused multiply-add) so
-  that the GPU path assigns every particle to the same cell.  It is the only
-  non-FP64 arithmetic in this module.
+* The cell index is evaluated by one canonical rounding sequence so that the
+  GPU path assigns every particle to the same cell: the offset from a centre c
+  is d = fl32(x - c) (one FP64 subtraction, rounded) for FP64 systems, and
+  d = fl32(fl32(x32 - c_hi) - c_lo) with c_hi = fl32(c), c_lo = fl32(c - c_hi)
+  for FP32 systems (positions are FP32 numbers there; the rule needs no FP64
+  arithmetic per particle); then u = fl32(fl32(d gamma) + N/2) and
+  a = floor(fl32(u + 1/2)), no fused multiply-add.  This is the only non-FP64
+  arithmetic in this module.
 * Masses are deposited as 64-bit fixed point, q = rint(m * 2^s),
   s = 62 - ceil(log2(mass_bound)); integer sums make the density exact.
 * Flattened grids (Sec. 2.2.2): cell lengths l_xy, l_xy, l_z = q*l_xy and
@@ -122,6 +126,11 @@ class System:
     G: float = 1.0
     h000: float = 1.0
     mass_bound: float = 1.0
+    precision: str = "fp64"    # selects the canonical offset rule (FP32 systems)
+
+    @property
+    def split(self) -> bool:
+        return self.precision == "fp32"
 
 
 # ---------------------------------------------------------------------------
@@ -145,9 +154,15 @@ def quantize_mass(m, s: int) -> np.ndarray:
 # Cell assignment, Eq. (eqn:cell), with the canonical rounding sequence
 # ---------------------------------------------------------------------------
 
-def offset_f32(x, c: float) -> np.ndarray:
-    """(x - c) in FP64, rounded once to FP32."""
-    return (np.asarray(x, dtype=np.float64) - np.float64(c)).astype(np.float32)
+def offset_f32(x, c: float, split: bool = False) -> np.ndarray:
+    """Canonical FP32 offset of x from c: fl32(x - c) in FP64 (split=False),
+    or fl32(fl32(x32 - c_hi) - c_lo) with c = c_hi + c_lo (split=True)."""
+    if not split:
+        return (np.asarray(x, dtype=np.float64) - np.float64(c)).astype(np.float32)
+    c_hi = np.float32(c)
+    c_lo = np.float32(np.float64(c) - np.float64(c_hi))
+    x32 = np.asarray(x, dtype=np.float64).astype(np.float32)
+    return ((x32 - c_hi).astype(np.float32) - c_lo).astype(np.float32)
 
 
 def cell_index(d32: np.ndarray, l: float, n: int) -> np.ndarray:
@@ -171,10 +186,10 @@ def r2_f32(dx, dy, dz) -> np.ndarray:
             ).astype(np.float32) + (dz * dz).astype(np.float32)
 
 
-def grid_cells(pos, centre, g: Geometry):
+def grid_cells(pos, centre, g: Geometry, split: bool = False):
     """Cell indices (a, b, c) of positions in geometry g centred on `centre`,
     and the usable-box mask."""
-    d = [offset_f32(pos[k], centre[k]) for k in range(3)]
+    d = [offset_f32(pos[k], centre[k], split) for k in range(3)]
     a = cell_index(d[0], g.l_xy, g.nx)
     b = cell_index(d[1], g.l_xy, g.ny)
     c = cell_index(d[2], g.l_z, g.nz)
@@ -182,19 +197,19 @@ def grid_cells(pos, centre, g: Geometry):
     return (a, b, c), ok
 
 
-def region(pos, gal: Galaxy, centre) -> np.ndarray:
+def region(pos, gal: Galaxy, centre, split: bool = False) -> np.ndarray:
     """Region of each position relative to one galaxy (Sec. 2.1 list of grids
     and potential combination rule): 0 core, 1 shell, 2 outer."""
-    d = [offset_f32(pos[k], centre[k]) for k in range(3)]
+    d = [offset_f32(pos[k], centre[k], split) for k in range(3)]
     r2 = r2_f32(*d)
     n = len(pos[0])
     reg = np.full(n, REGION_OUTER, dtype=np.int64)
     in_g2 = np.zeros(n, dtype=bool)
     if gal.medium is not None:
-        _, in_g2 = grid_cells(pos, centre, gal.medium)
+        _, in_g2 = grid_cells(pos, centre, gal.medium, split)
     core = np.zeros(n, dtype=bool)
     if gal.fine is not None and gal.medium is not None:
-        _, in_g1 = grid_cells(pos, centre, gal.fine)
+        _, in_g1 = grid_cells(pos, centre, gal.fine, split)
         core = (r2 < np.float32(gal.r_core * gal.r_core)) & in_g1 & in_g2
     shell = (~core) & (r2 < np.float32(gal.r_out * gal.r_out)) & in_g2
     reg[core] = REGION_CORE
@@ -205,10 +220,10 @@ def region(pos, gal: Galaxy, centre) -> np.ndarray:
 def lost_mask(pos, system: System) -> np.ndarray:
     """Particles outside R_sys or outside the usable box of any coarse grid are
     lost (Sec. 2.1)."""
-    d = [offset_f32(pos[k], system.sys_centre[k]) for k in range(3)]
+    d = [offset_f32(pos[k], system.sys_centre[k], system.split) for k in range(3)]
     lost = ~(r2_f32(*d) < np.float32(system.r_sys * system.r_sys))
     for gal in system.galaxies:
-        _, ok = grid_cells(pos, system.sys_centre, gal.coarse)
+        _, ok = grid_cells(pos, system.sys_centre, gal.coarse, system.split)
         lost |= ~ok
     return lost
 
@@ -236,7 +251,7 @@ def classify(state: State, system: System):
     for g, gal in enumerate(system.galaxies):
         sel = state.gal == g
         if np.any(sel):
-            own[sel] = region(state.pos[:, sel], gal, state.centres[g])
+            own[sel] = region(state.pos[:, sel], gal, state.centres[g], system.split)
     return flags, own
 
 
@@ -271,7 +286,7 @@ def deposit(state: State, system: System, flags=None, own=None):
         for k, geom, ck, regs in mass_sets(gal):
             centre = state.centres[g] if ck == "gal" else system.sys_centre
             sel = live & (state.gal == g) & np.isin(own, regs)
-            (a, b, c), ok = grid_cells(state.pos[:, sel], centre, geom)
+            (a, b, c), ok = grid_cells(state.pos[:, sel], centre, geom, system.split)
             assert ok.all(), "particle of a mass set outside its grid"
             grid = np.zeros(geom.shape, dtype=np.int64)
             np.add.at(grid, (c, b, a), q[sel])
@@ -351,8 +366,8 @@ def solve_all(rho, system: System, s: int):
 # Forces: Eq. (eqn:diff) and the potential combination rule (Sec. 2.1)
 # ---------------------------------------------------------------------------
 
-def _cell_and_delta(pos, centre, g: Geometry):
-    (a, b, c), ok = grid_cells(pos, centre, g)
+def _cell_and_delta(pos, centre, g: Geometry, split: bool = False):
+    (a, b, c), ok = grid_cells(pos, centre, g, split)
     delta = np.stack([
         (pos[0] - centre[0]) - (a - g.nx // 2) * g.l_xy,
         (pos[1] - centre[1]) - (b - g.ny // 2) * g.l_xy,
@@ -410,7 +425,7 @@ def accelerations(state: State, system: System, phi, flags, with_phi=False):
     live = (flags & FLAG_LOST) == 0
     pos = state.pos
     for h, gal in enumerate(system.galaxies):
-        reg = region(pos, gal, state.centres[h])
+        reg = region(pos, gal, state.centres[h], system.split)
         sets = {k: (geom, ck) for k, geom, ck, _ in mass_sets(gal)}
         for r in (REGION_CORE, REGION_SHELL, REGION_OUTER):
             sel = live & (reg == r)
@@ -421,7 +436,7 @@ def accelerations(state: State, system: System, phi, flags, with_phi=False):
                     continue
                 geom, ck = sets[k]
                 centre = state.centres[h] if ck == "gal" else system.sys_centre
-                (a, b, c), delta, ok = _cell_and_delta(pos[:, sel], centre, geom)
+                (a, b, c), delta, ok = _cell_and_delta(pos[:, sel], centre, geom, system.split)
                 assert ok.all(), "field point outside the grid chosen for it"
                 acc[:, sel] += accel_from_grid(phi[h][k], geom, a, b, c, delta)
                 if with_phi:
@@ -458,7 +473,7 @@ def recentre(state: State, system: System) -> np.ndarray:
         f, e = math.frexp(gal.r_core)
         sD = 24 - (e - 1 if f == 0.5 else e)
         sel = live & (state.gal == g)
-        d = [offset_f32(state.pos[k, sel], state.centres[g, k]) for k in range(3)]
+        d = [offset_f32(state.pos[k, sel], state.centres[g, k], system.split) for k in range(3)]
         inside = r2_f32(*d) < np.float32(gal.r_core * gal.r_core)
         w = q[sel][inside]
         M = int(w.sum())

@@ -60,7 +60,7 @@ def build(verbose: bool = False, force: bool = False, extra=()) -> str:
 
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         list(ex.map(run, jobs))
-    if jobs or not os.path.exists(OUT):
+    if jobs or not os.path.exists(OUT) or any(os.path.getmtime(o) > os.path.getmtime(OUT) for o in objs):
         tmp = OUT + ".tmp"
         # shared runtime: the library and PyTorch share one CUDA runtime (and
         # its current-device state) in a process

@@ -87,6 +87,19 @@ GeomK make_geomk(const pm_geometry &g) {
     return k;
 }
 
+// FP64 centres and their FP32 split c = hi + lo (hi = fl32(c), lo = fl32(c - hi)).
+CenK make_cenk(const double *c, int ngal) {
+    CenK k;
+    std::memset(&k, 0, sizeof(k));
+    for (int g = 0; g < ngal; ++g)
+        for (int a = 0; a < 3; ++a) {
+            k.c[g][a] = c[3 * g + a];
+            k.hi[g][a] = (float)c[3 * g + a];
+            k.lo[g][a] = (float)(c[3 * g + a] - (double)k.hi[g][a]);
+        }
+    return k;
+}
+
 struct GeoBuf {
     pm_geometry g;
     long long A, workN, hatN;
@@ -112,17 +125,24 @@ struct pm_ctx {
     size_t rho_bytes = 0;
     SysK hs;
     SysK *d_sys = nullptr;
-    double *d_cen = nullptr;
-    unsigned long long *d_csum = nullptr;
+    CenK *d_cen = nullptr;
+    long long *d_csum = nullptr;   // per-block partial centre-of-mass sums
     double *d_diag = nullptr;
     unsigned long long *d_cnt = nullptr;
     void *d_tw[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     cudaStream_t user = nullptr;
     cudaStream_t cap = nullptr;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t gexec = nullptr;
+    cudaGraph_t graph[2] = {nullptr, nullptr};        // [0] step, [1] sort + step
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     pm_particles gkey;
     double gdt = 0;
+    // spatial sort
+    SortK sortk;
+    int sort_interval = 0;
+    long long step_count = 0;
+    long long sort_cap = 0;
+    unsigned *s_count = nullptr, *s_key = nullptr, *s_rank = nullptr, *s_bsum = nullptr;
+    void *s_arr[9] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     size_t bytes = 0;
     std::vector<void *> allocs;
     bool any_recentre = false;
@@ -281,7 +301,7 @@ template <typename T> int enqueue_solve(pm_ctx *c, cudaStream_t st, cudaEvent_t 
 
 template <typename T> int enqueue_deposit(pm_ctx *c, const pm_particles *p, cudaStream_t st) {
     PM_CK(cudaMemsetAsync(c->rho_all, 0, c->rho_bytes, st));
-    PM_CK(pm_launch_deposit<T>(part_k<T>(p), c->d_sys, c->d_cen, st));
+    PM_CK(pm_launch_deposit<T>(part_k<T>(p), c->d_sys, c->d_cen, c->sort_interval > 0 ? 1 : 0, st));
     return PM_OK;
 }
 
@@ -305,43 +325,89 @@ template <typename T> int enqueue_step(pm_ctx *c, const pm_particles *p, double 
 }
 
 void destroy_graph(pm_ctx *c) {
-    if (c->gexec) cudaGraphExecDestroy(c->gexec);
-    if (c->graph) cudaGraphDestroy(c->graph);
-    c->gexec = nullptr;
-    c->graph = nullptr;
+    for (int k = 0; k < 2; ++k) {
+        if (c->gexec[k]) cudaGraphExecDestroy(c->gexec[k]);
+        if (c->graph[k]) cudaGraphDestroy(c->graph[k]);
+        c->gexec[k] = nullptr;
+        c->graph[k] = nullptr;
+    }
+}
+
+// Scratch of the spatial sort for n particles (allocated outside any capture).
+int ensure_sort_scratch(pm_ctx *c, long long n) {
+    if (n <= c->sort_cap) return PM_OK;
+    for (int k = 0; k < 9; ++k)
+        PM_TRY(dev_alloc(c, &c->s_arr[k], (size_t)n * (k < 7 ? c->esz : 4)));
+    PM_TRY(dev_alloc(c, (void **)&c->s_key, (size_t)n * 4));
+    PM_TRY(dev_alloc(c, (void **)&c->s_rank, (size_t)n * 4));
+    c->sort_cap = n;
+    return PM_OK;
+}
+
+template <typename T> int enqueue_sort(pm_ctx *c, const pm_particles *p, long long *perm, cudaStream_t st) {
+    PartK<T> scratch = part_k<T>(p);
+    scratch.x = (T *)c->s_arr[0]; scratch.y = (T *)c->s_arr[1]; scratch.z = (T *)c->s_arr[2];
+    scratch.vx = (T *)c->s_arr[3]; scratch.vy = (T *)c->s_arr[4]; scratch.vz = (T *)c->s_arr[5];
+    scratch.m = (const T *)c->s_arr[6];
+    scratch.gal = (const int32_t *)c->s_arr[7];
+    scratch.flags = (uint32_t *)c->s_arr[8];
+    PM_CK(pm_launch_sort<T>(part_k<T>(p), scratch, c->d_sys, c->d_cen, c->sortk, c->s_count, c->s_key, c->s_rank,
+                            c->s_bsum, perm, st));
+    return PM_OK;
+}
+
+template <typename T> int capture(pm_ctx *c, const pm_particles *p, double dt, bool with_sort, cudaGraph_t *gr,
+                                  cudaGraphExec_t *ex) {
+    PM_CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+    int rc = with_sort ? enqueue_sort<T>(c, p, nullptr, c->cap) : PM_OK;
+    if (rc == PM_OK) rc = enqueue_step<T>(c, p, dt, c->cap, nullptr);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->cap, &g);
+    if (rc != PM_OK) { if (g) cudaGraphDestroy(g); return rc; }
+    if (e != cudaSuccess) return fail(PM_E_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    *gr = g;
+    e = cudaGraphInstantiate(ex, g, 0);
+    if (e != cudaSuccess) return fail(PM_E_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+    return PM_OK;
 }
 
 template <typename T> int step_impl(pm_ctx *c, const pm_particles *p, double dt, int nsteps) {
-    const bool same = c->gexec && std::memcmp(&c->gkey, p, sizeof(pm_particles)) == 0 && c->gdt == dt;
+    const bool sorting = c->sort_interval > 0 && p->n > 0;
+    const bool same = c->gexec[0] && (!sorting || c->gexec[1]) &&
+                      std::memcmp(&c->gkey, p, sizeof(pm_particles)) == 0 && c->gdt == dt;
     if (!same) {
         destroy_graph(c);
-        PM_CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
-        int rc = enqueue_step<T>(c, p, dt, c->cap, nullptr);
-        cudaGraph_t gr = nullptr;
-        cudaError_t e = cudaStreamEndCapture(c->cap, &gr);
-        if (rc != PM_OK) { if (gr) cudaGraphDestroy(gr); return rc; }
-        if (e != cudaSuccess) return fail(PM_E_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
-        c->graph = gr;
-        e = cudaGraphInstantiate(&c->gexec, gr, 0);
-        if (e != cudaSuccess) { destroy_graph(c); return fail(PM_E_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e)); }
+        if (sorting) PM_TRY(ensure_sort_scratch(c, p->n));
+        int rc = capture<T>(c, p, dt, false, &c->graph[0], &c->gexec[0]);
+        if (rc == PM_OK && sorting) rc = capture<T>(c, p, dt, true, &c->graph[1], &c->gexec[1]);
+        if (rc != PM_OK) { destroy_graph(c); return rc; }
         c->gkey = *p;
         c->gdt = dt;
     }
-    for (int s = 0; s < nsteps; ++s) PM_CK(cudaGraphLaunch(c->gexec, c->user));
+    for (int s = 0; s < nsteps; ++s) {
+        const int g = (sorting && c->step_count % c->sort_interval == 0) ? 1 : 0;
+        PM_CK(cudaGraphLaunch(c->gexec[g], c->user));
+        ++c->step_count;
+    }
     return PM_OK;
 }
 
 template <typename T> int step_timed_impl(pm_ctx *c, const pm_particles *p, double dt, int nsteps, float *ms) {
-    const int NE = 9;
+    const int NE = 10;
+    const bool sorting = c->sort_interval > 0 && p->n > 0;
+    if (sorting) PM_TRY(ensure_sort_scratch(c, p->n));
     std::vector<cudaEvent_t> ev((size_t)nsteps * NE);
     for (auto &e : ev) PM_CK(cudaEventCreate(&e));
     int rc = PM_OK;
     for (int s = 0; s < nsteps && rc == PM_OK; ++s) {
         cudaEvent_t *e = ev.data() + (size_t)s * NE;
+        cudaEventRecord(e[9], c->user);
+        if (sorting && c->step_count % c->sort_interval == 0) rc = enqueue_sort<T>(c, p, nullptr, c->user);
+        ++c->step_count;
         cudaEventRecord(e[0], c->user);
-        rc = enqueue_step<T>(c, p, dt, c->user, e + 1);
+        if (rc == PM_OK) rc = enqueue_step<T>(c, p, dt, c->user, e + 1);
     }
-    for (int k = 0; k < 9; ++k) ms[k] = 0.f;
+    for (int k = 0; k < 10; ++k) ms[k] = 0.f;
     if (rc == PM_OK) {
         cudaError_t er = cudaStreamSynchronize(c->user);
         if (er != cudaSuccess) rc = fail(PM_E_CUDA, "step_timed sync: %s", cudaGetErrorString(er));
@@ -355,8 +421,10 @@ template <typename T> int step_timed_impl(pm_ctx *c, const pm_particles *p, doub
                 ms[k] += t;
             }
             float t = 0.f;
-            cudaEventElapsedTime(&t, e[0], e[8]);
+            cudaEventElapsedTime(&t, e[9], e[8]);
             ms[8] += t;
+            cudaEventElapsedTime(&t, e[9], e[0]);
+            ms[9] += t;
         }
     }
     for (auto &e : ev) cudaEventDestroy(e);
@@ -515,6 +583,11 @@ int pm_create_grids(const pm_system *sys, const pm_galaxy *gals, void *stream, p
     hs.rsys2 = (float)(sys->r_sys * sys->r_sys);
     for (int k = 0; k < 3; ++k) hs.sc[k] = sys->sys_centre[k];
     hs.mscale = c->mscale;
+    hs.mscale_f = (float)c->mscale;
+    for (int k = 0; k < 3; ++k) {
+        hs.sc_hi[k] = (float)sys->sys_centre[k];
+        hs.sc_lo[k] = (float)(sys->sys_centre[k] - (double)hs.sc_hi[k]);
+    }
     for (int gi = 0; gi < sys->ngal; ++gi) {
         const pm_galaxy &G = gals[gi];
         GalK &K = hs.gal[gi];
@@ -530,17 +603,37 @@ int pm_create_grids(const pm_system *sys, const pm_galaxy *gals, void *stream, p
             K.phi[k] = c->phi[gi][k];
         }
     }
+    {   // key layout of the spatial sort
+        SortK &so = c->sortk;
+        std::memset(&so, 0, sizeof(so));
+        long long base = 0;
+        for (int gi = 0; gi < sys->ngal; ++gi) {
+            const pm_geometry *gg[3] = {&gals[gi].fine, &gals[gi].medium, &gals[gi].coarse};
+            for (int r = 0; r < 3; ++r) {
+                so.base[gi][r] = base;
+                if (!geom_present(*gg[r])) continue;
+                int b = 0;
+                while ((long long)(gg[r]->nx >> b) * (gg[r]->ny >> b) * (gg[r]->nz >> b) > (1LL << 21)) ++b;
+                so.shift[gi][r] = b;
+                base += (long long)(gg[r]->nx >> b) * (gg[r]->ny >> b) * (gg[r]->nz >> b);
+            }
+        }
+        so.nkeys = base + 1;
+        const long long nb = (so.nkeys + 2047) / 2048;
+        if ((rc = dev_alloc(c, (void **)&c->s_count, (size_t)so.nkeys * 4))) return cleanup(rc);
+        if ((rc = dev_alloc(c, (void **)&c->s_bsum, (size_t)nb * 4))) return cleanup(rc);
+    }
     if ((rc = dev_alloc(c, (void **)&c->d_sys, sizeof(SysK)))) return cleanup(rc);
-    if ((rc = dev_alloc(c, (void **)&c->d_cen, sizeof(double) * 3 * PM_MAX_GALAXIES))) return cleanup(rc);
-    if ((rc = dev_alloc(c, (void **)&c->d_csum, sizeof(unsigned long long) * 4 * PM_MAX_GALAXIES))) return cleanup(rc);
+    if ((rc = dev_alloc(c, (void **)&c->d_cen, sizeof(CenK)))) return cleanup(rc);
+    if ((rc = dev_alloc(c, (void **)&c->d_csum, sizeof(long long) * 4 * PM_MAX_GALAXIES * 2048))) return cleanup(rc);
     if ((rc = dev_alloc(c, (void **)&c->d_diag, sizeof(double) * 8))) return cleanup(rc);
     if ((rc = dev_alloc(c, (void **)&c->d_cnt, sizeof(unsigned long long)))) return cleanup(rc);
     double cen[3 * PM_MAX_GALAXIES] = {0};
     for (int gi = 0; gi < sys->ngal; ++gi)
         for (int k = 0; k < 3; ++k) cen[3 * gi + k] = gals[gi].centre[k];
+    const CenK ck = make_cenk(cen, sys->ngal);
     if (cudaMemcpyAsync(c->d_sys, &hs, sizeof(SysK), cudaMemcpyHostToDevice, c->user) != cudaSuccess ||
-        cudaMemcpyAsync(c->d_cen, cen, sizeof(cen), cudaMemcpyHostToDevice, c->user) != cudaSuccess ||
-        cudaMemsetAsync(c->d_csum, 0, sizeof(unsigned long long) * 4 * PM_MAX_GALAXIES, c->user) != cudaSuccess ||
+        cudaMemcpyAsync(c->d_cen, &ck, sizeof(CenK), cudaMemcpyHostToDevice, c->user) != cudaSuccess ||
         cudaStreamSynchronize(c->user) != cudaSuccess)
         return cleanup(fail(PM_E_CUDA, "context upload failed: %s", cudaGetErrorString(cudaGetLastError())));
     *out = c;
@@ -603,6 +696,23 @@ int pm_step(pm_ctx *c, const pm_particles *p, double dt, int32_t nsteps) {
     return PM_DISPATCH(c, step_impl, c, p, dt, nsteps);
 }
 
+int pm_sort(pm_ctx *c, const pm_particles *p, int64_t *perm) {
+    if (!c) return fail(PM_E_ARG, "ctx is NULL");
+    PM_TRY(check_particles(p));
+    if (p->n == 0) return PM_OK;
+    PM_TRY(ensure_sort_scratch(c, p->n));
+    return PM_DISPATCH(c, enqueue_sort, c, p, (long long *)perm, c->user);
+}
+
+int pm_set_sort_interval(pm_ctx *c, int32_t k) {
+    if (!c) return fail(PM_E_ARG, "ctx is NULL");
+    if (k < 0) return fail(PM_E_ARG, "sort interval must be >= 0");
+    c->sort_interval = k;
+    c->step_count = 0;
+    destroy_graph(c);
+    return PM_OK;
+}
+
 int pm_step_timed(pm_ctx *c, const pm_particles *p, double dt, int32_t nsteps, float *ms_out) {
     if (!c || !ms_out) return fail(PM_E_ARG, "ctx or ms_out is NULL");
     PM_TRY(check_particles(p));
@@ -653,7 +763,8 @@ int pm_get_centres(pm_ctx *c, double *host_out) {
 
 int pm_set_centres(pm_ctx *c, const double *host_in) {
     if (!c || !host_in) return fail(PM_E_ARG, "ctx or host_in is NULL");
-    PM_CK(cudaMemcpyAsync(c->d_cen, host_in, sizeof(double) * 3 * c->sys.ngal, cudaMemcpyHostToDevice, c->user));
+    const CenK ck = make_cenk(host_in, c->sys.ngal);
+    PM_CK(cudaMemcpyAsync(c->d_cen, &ck, sizeof(CenK), cudaMemcpyHostToDevice, c->user));
     PM_CK(cudaStreamSynchronize(c->user));
     return PM_OK;
 }

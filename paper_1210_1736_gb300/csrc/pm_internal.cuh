@@ -36,8 +36,26 @@ struct SysK {
     int ngal;
     float rsys2;
     double sc[3];
+    float sc_hi[3], sc_lo[3];  // system centre split as fl32(c) + fl32(c - fl32(c))
     double mscale;             // 2^s
+    float mscale_f;            // 2^s as float (exact)
     GalK gal[PM_MAX_GALAXIES];
+};
+
+// Centres of grids 1-3: FP64 values and their FP32 split (hi, lo) per axis.
+struct CenK {
+    double c[PM_MAX_GALAXIES][3];
+    float hi[PM_MAX_GALAXIES][3];
+    float lo[PM_MAX_GALAXIES][3];
+};
+
+// Key layout of the spatial sort: per galaxy and region (core, shell, outer)
+// a base offset and the bin shift applied to the cell indices of that
+// region's grid (fine, medium, coarse); the last key collects lost particles.
+struct SortK {
+    long long base[PM_MAX_GALAXIES][3];
+    int shift[PM_MAX_GALAXIES][3];
+    long long nkeys;
 };
 
 template <typename T> struct PartK {
@@ -50,13 +68,24 @@ template <typename T> struct PartK {
 
 // ----------------------------------------------------------------------------
 // Canonical cell assignment (Eq. eqn:cell).  Every rounding is explicit and
-// no multiply-add is fused, so this function and the CPU reference agree bit
-// for bit: d = fl32(x - c) (FP64 subtract), u = fl32(fl32(d*gamma) + N/2),
-// a = floor(fl32(u + 1/2)).
+// no multiply-add is fused, so these functions and the CPU reference agree
+// bit for bit: the offset d from a centre c (pm_canon), then
+// u = fl32(fl32(d*gamma) + N/2), a = floor(fl32(u + 1/2)).
 // ----------------------------------------------------------------------------
 __device__ __forceinline__ float pm_off32(double x, double c) {
     return __double2float_rn(__dsub_rn(x, c));
 }
+// FP32 contexts: positions are floats and the offset is
+// fl32(fl32(x - c_hi) - c_lo) with c = c_hi + c_lo, no FP64 arithmetic.
+__device__ __forceinline__ float pm_off32s(float x, float chi, float clo) {
+    return __fsub_rn(__fsub_rn(x, chi), clo);
+}
+// Canonical offset for the context precision.
+__device__ __forceinline__ float pm_canon(float x, double, float chi, float clo) { return pm_off32s(x, chi, clo); }
+__device__ __forceinline__ float pm_canon(double x, double c, float, float) { return pm_off32(x, c); }
+// Fixed-point mass q = rint(m 2^s): for float m the product is exact in FP32.
+__device__ __forceinline__ long long pm_qmass(float m, double, float sf) { return __float2ll_rn(__fmul_rn(m, sf)); }
+__device__ __forceinline__ long long pm_qmass(double m, double s, float) { return __double2ll_rn(__dmul_rn(m, s)); }
 __device__ __forceinline__ int pm_cell(float d, float g, int n) {
     float u = __fadd_rn(__fmul_rn(d, g), (float)(n >> 1));
     return (int)floorf(__fadd_rn(u, 0.5f));

@@ -257,12 +257,16 @@ __global__ void __launch_bounds__(NT) k_xinv(FftArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Particle kernels.  The system description is staged in shared memory.
+// Particle kernels.  The system description and the grid centres are staged
+// in shared memory.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void stage_sys(SysK &s, const SysK *g) {
+__device__ __forceinline__ void stage_sys(SysK &s, const SysK *g, CenK &cs, const CenK *cg) {
     const int *src = reinterpret_cast<const int *>(g);
     int *dst = reinterpret_cast<int *>(&s);
     for (int i = threadIdx.x; i < (int)(sizeof(SysK) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+    const int *src2 = reinterpret_cast<const int *>(cg);
+    int *dst2 = reinterpret_cast<int *>(&cs);
+    for (int i = threadIdx.x; i < (int)(sizeof(CenK) / sizeof(int)); i += blockDim.x) dst2[i] = src2[i];
     __syncthreads();
 }
 
@@ -270,42 +274,88 @@ __device__ __forceinline__ size_t cell_off(const GeomK &g, const Cell &c) {
     return ((size_t)c.k * g.ny + c.j) * g.nx + c.i;
 }
 
-// Steps a2-a3: classification and exact fixed-point mass assignment.
+// Offset used for Delta in Eq. (eqn:diff): the canonical FP32 offset in FP32
+// contexts, the exact FP64 difference in FP64 contexts.
+__device__ __forceinline__ float rel_off(float x, double, float chi, float clo) { return pm_off32s(x, chi, clo); }
+__device__ __forceinline__ double rel_off(double x, double c, float, float) { return __dsub_rn(x, c); }
+
+// Adds q (two's complement int64) to *addr for every lane with active set;
+// lanes that target the same address are combined first (exact: the sum is
+// taken mod 2^64 from four 16-bit chunk sums), so a warp of particles in one
+// cell issues one atomic.  Every lane of the warp must call it.
+__device__ __forceinline__ void agg_add(unsigned long long *addr, unsigned long long q, bool active) {
+    const unsigned mask = __ballot_sync(0xffffffffu, active);
+    if (!active) return;
+    const unsigned peers = __match_any_sync(mask, (unsigned long long)addr);
+    if (__popc(peers) == 1) { atomicAdd(addr, q); return; }
+    const unsigned s0 = __reduce_add_sync(peers, (unsigned)(q & 0xffffu));
+    const unsigned s1 = __reduce_add_sync(peers, (unsigned)((q >> 16) & 0xffffu));
+    const unsigned s2 = __reduce_add_sync(peers, (unsigned)((q >> 32) & 0xffffu));
+    const unsigned s3 = __reduce_add_sync(peers, (unsigned)(q >> 48));
+    if ((int)(threadIdx.x & 31) == __ffs(peers) - 1)
+        atomicAdd(addr, (unsigned long long)s0 + ((unsigned long long)s1 << 16) + ((unsigned long long)s2 << 32) +
+                            ((unsigned long long)s3 << 48));
+}
+
+// Steps a2-a3: classification and exact fixed-point mass assignment.  The
+// loop is warp-uniform so the aggregation can use warp collectives.
 template <typename T>
-__global__ void __launch_bounds__(256) k_deposit(PartK<T> p, const SysK *sk, const double *__restrict__ cen) {
+__global__ void __launch_bounds__(256) k_deposit(PartK<T> p, const SysK *sk, const CenK *cen, int aggregate) {
     __shared__ SysK s;
-    stage_sys(s, sk);
+    __shared__ CenK cs;
+    stage_sys(s, sk, cs, cen);
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += stride) {
-        const uint32_t f = p.flags[i];
-        if (f & PM_FLAG_LOST) continue;
-        const double x = (double)p.x[i], y = (double)p.y[i], z = (double)p.z[i];
-        const float sx = pm_off32(x, s.sc[0]), sy = pm_off32(y, s.sc[1]), sz = pm_off32(z, s.sc[2]);
-        bool lost = !(pm_r2(sx, sy, sz) < s.rsys2);
-        const int g = p.gal[i];
-        if (g < 0 || g >= s.ngal) lost = true;
-        Cell cc;
-        cc.i = cc.j = cc.k = 0; cc.ok = false;
-        for (int h = 0; h < s.ngal; ++h) {
-            const Cell ch = pm_cells(s.gal[h].coarse, sx, sy, sz);
-            lost = lost || !ch.ok;
-            if (h == g) cc = ch;
+    for (long long b = (long long)blockIdx.x * blockDim.x; b < p.n; b += stride) {
+        const long long i = b + threadIdx.x;
+        unsigned long long *tgt[3] = {nullptr, nullptr, nullptr};
+        unsigned long long q = 0;
+        if (i < p.n) {
+            const uint32_t f = p.flags[i];
+            if (!(f & PM_FLAG_LOST)) {
+                const T x = p.x[i], y = p.y[i], z = p.z[i];
+                const float sx = pm_canon(x, s.sc[0], s.sc_hi[0], s.sc_lo[0]);
+                const float sy = pm_canon(y, s.sc[1], s.sc_hi[1], s.sc_lo[1]);
+                const float sz = pm_canon(z, s.sc[2], s.sc_hi[2], s.sc_lo[2]);
+                bool lost = !(pm_r2(sx, sy, sz) < s.rsys2);
+                const int g = p.gal[i];
+                if (g < 0 || g >= s.ngal) lost = true;
+                Cell cc;
+                cc.i = cc.j = cc.k = 0; cc.ok = false;
+                for (int h = 0; h < s.ngal; ++h) {
+                    const Cell ch = pm_cells(s.gal[h].coarse, sx, sy, sz);
+                    lost = lost || !ch.ok;
+                    if (h == g) cc = ch;
+                }
+                if (lost) {
+                    p.flags[i] = f | PM_FLAG_LOST;
+                } else {
+                    const GalK &G = s.gal[g];
+                    const float dx = pm_canon(x, cs.c[g][0], cs.hi[g][0], cs.lo[g][0]);
+                    const float dy = pm_canon(y, cs.c[g][1], cs.hi[g][1], cs.lo[g][1]);
+                    const float dz = pm_canon(z, cs.c[g][2], cs.hi[g][2], cs.lo[g][2]);
+                    Cell cf, cm;
+                    const int reg = pm_region(G, dx, dy, dz, cf, cm);
+                    q = (unsigned long long)pm_qmass(p.m[i], s.mscale, s.mscale_f);
+                    if (reg == REG_CORE) {
+                        tgt[0] = G.rho[0] + cell_off(G.fine, cf);
+                        tgt[1] = G.rho[1] + cell_off(G.med, cm);
+                        tgt[2] = G.rho[3] + cell_off(G.coarse, cc);
+                    } else if (reg == REG_SHELL) {
+                        tgt[1] = G.rho[2] + cell_off(G.med, cm);
+                        tgt[2] = G.rho[3] + cell_off(G.coarse, cc);
+                    } else {
+                        tgt[2] = G.rho[4] + cell_off(G.coarse, cc);
+                    }
+                }
+            }
         }
-        if (lost) { p.flags[i] = f | PM_FLAG_LOST; continue; }
-        const GalK &G = s.gal[g];
-        const float dx = pm_off32(x, cen[3 * g]), dy = pm_off32(y, cen[3 * g + 1]), dz = pm_off32(z, cen[3 * g + 2]);
-        Cell cf, cm;
-        const int reg = pm_region(G, dx, dy, dz, cf, cm);
-        const unsigned long long q = (unsigned long long)__double2ll_rn(__dmul_rn((double)p.m[i], s.mscale));
-        if (reg == REG_CORE) {
-            atomicAdd(G.rho[0] + cell_off(G.fine, cf), q);
-            atomicAdd(G.rho[1] + cell_off(G.med, cm), q);
-            atomicAdd(G.rho[3] + cell_off(G.coarse, cc), q);
-        } else if (reg == REG_SHELL) {
-            atomicAdd(G.rho[2] + cell_off(G.med, cm), q);
-            atomicAdd(G.rho[3] + cell_off(G.coarse, cc), q);
+        if (aggregate) {
+#pragma unroll
+            for (int t = 0; t < 3; ++t) agg_add(tgt[t], q, tgt[t] != nullptr);
         } else {
-            atomicAdd(G.rho[4] + cell_off(G.coarse, cc), q);
+#pragma unroll
+            for (int t = 0; t < 3; ++t)
+                if (tgt[t]) atomicAdd(tgt[t], q);
         }
     }
 }
@@ -351,10 +401,6 @@ __device__ __forceinline__ void cell_delta(const GeomK &g, const Cell &cl, T rx,
     dz = rz - (T)(cl.k - (g.nz >> 1)) * (T)g.lz;
 }
 
-template <typename T> __device__ __forceinline__ T rel_off(double x, double c);
-template <> __device__ __forceinline__ float rel_off<float>(double x, double c) { return pm_off32(x, c); }
-template <> __device__ __forceinline__ double rel_off<double>(double x, double c) { return __dsub_rn(x, c); }
-
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -366,10 +412,11 @@ __device__ __forceinline__ double warp_sum(double v) {
 //   MODE 0: leap-frog kick-drift   MODE 1: write acceleration
 //   MODE 2: kick only              MODE 3: energy / angular momentum sums
 template <typename T, int MODE>
-__global__ void __launch_bounds__(256) k_force(PartK<T> p, const SysK *sk, const double *__restrict__ cen,
+__global__ void __launch_bounds__(256) k_force(PartK<T> p, const SysK *sk, const CenK *cen,
                                                T dt, T *ax, T *ay, T *az, double *diag) {
     __shared__ SysK s;
-    stage_sys(s, sk);
+    __shared__ CenK cs;
+    stage_sys(s, sk, cs, cen);
     double dsum[7] = {0, 0, 0, 0, 0, 0, 0};
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += stride) {
@@ -378,16 +425,20 @@ __global__ void __launch_bounds__(256) k_force(PartK<T> p, const SysK *sk, const
             continue;
         }
         const T xT = p.x[i], yT = p.y[i], zT = p.z[i];
-        const double x = (double)xT, y = (double)yT, z = (double)zT;
-        const float sx = pm_off32(x, s.sc[0]), sy = pm_off32(y, s.sc[1]), sz = pm_off32(z, s.sc[2]);
-        const T rsx = rel_off<T>(x, s.sc[0]), rsy = rel_off<T>(y, s.sc[1]), rsz = rel_off<T>(z, s.sc[2]);
+        const float sx = pm_canon(xT, s.sc[0], s.sc_hi[0], s.sc_lo[0]);
+        const float sy = pm_canon(yT, s.sc[1], s.sc_hi[1], s.sc_lo[1]);
+        const float sz = pm_canon(zT, s.sc[2], s.sc_hi[2], s.sc_lo[2]);
+        const T rsx = rel_off(xT, s.sc[0], s.sc_hi[0], s.sc_lo[0]);
+        const T rsy = rel_off(yT, s.sc[1], s.sc_hi[1], s.sc_lo[1]);
+        const T rsz = rel_off(zT, s.sc[2], s.sc_hi[2], s.sc_lo[2]);
         T acc[3] = {0, 0, 0};
         T phiv = 0;
         T *php = (MODE == 3) ? &phiv : nullptr;
         for (int h = 0; h < s.ngal; ++h) {
             const GalK &G = s.gal[h];
-            const double cx = cen[3 * h], cy = cen[3 * h + 1], cz = cen[3 * h + 2];
-            const float fx = pm_off32(x, cx), fy = pm_off32(y, cy), fz = pm_off32(z, cz);
+            const float fx = pm_canon(xT, cs.c[h][0], cs.hi[h][0], cs.lo[h][0]);
+            const float fy = pm_canon(yT, cs.c[h][1], cs.hi[h][1], cs.lo[h][1]);
+            const float fz = pm_canon(zT, cs.c[h][2], cs.hi[h][2], cs.lo[h][2]);
             Cell cf, cm;
             const int reg = pm_region(G, fx, fy, fz, cf, cm);
             const Cell cc = pm_cells(G.coarse, sx, sy, sz);
@@ -397,7 +448,9 @@ __global__ void __launch_bounds__(256) k_force(PartK<T> p, const SysK *sk, const
             stencil<T>(G.coarse, static_cast<const T *>(G.phi[4]),
                        reg == REG_OUTER ? static_cast<const T *>(G.phi[3]) : nullptr, cc, dx, dy, dz, acc, php);
             if (reg != REG_OUTER) {
-                const T rx = rel_off<T>(x, cx), ry = rel_off<T>(y, cy), rz = rel_off<T>(z, cz);
+                const T rx = rel_off(xT, cs.c[h][0], cs.hi[h][0], cs.lo[h][0]);
+                const T ry = rel_off(yT, cs.c[h][1], cs.hi[h][1], cs.lo[h][1]);
+                const T rz = rel_off(zT, cs.c[h][2], cs.hi[h][2], cs.lo[h][2]);
                 cell_delta(G.med, cm, rx, ry, rz, dx, dy, dz);
                 stencil<T>(G.med, static_cast<const T *>(G.phi[2]),
                            reg == REG_SHELL ? static_cast<const T *>(G.phi[1]) : nullptr, cm, dx, dy, dz, acc, php);
@@ -416,6 +469,7 @@ __global__ void __launch_bounds__(256) k_force(PartK<T> p, const SysK *sk, const
         } else if (MODE == 2) {
             p.vx[i] += dt * acc[0]; p.vy[i] += dt * acc[1]; p.vz[i] += dt * acc[2];
         } else {
+            const double x = (double)xT, y = (double)yT, z = (double)zT;
             const double hdt = 0.5 * (double)dt;
             const double vx = (double)p.vx[i] + hdt * (double)acc[0];
             const double vy = (double)p.vy[i] + hdt * (double)acc[1];
@@ -454,59 +508,228 @@ __device__ __forceinline__ long long warp_sum_ll(long long v) {
 }
 
 // Step a1: exact integer centre-of-mass sums within R_core of each galaxy's
-// current centre: sum M, sum M*D (M = q >> 26, D = rint(d * 2^sD)).
+// current centre: sum M, sum M*D (M = q >> 26, D = rint(d * 2^sD)).  Warp
+// sums go to shared memory; each block writes its partial sums to
+// part[block][galaxy][4] (no contended global atomics); the apply kernel adds
+// the partials (integer sums: the order does not matter).
+constexpr int RECENTRE_MAX_BLOCKS = 2048;
+
 template <typename T>
-__global__ void __launch_bounds__(256) k_recentre_sum(PartK<T> p, const SysK *sk, const double *__restrict__ cen,
-                                                      unsigned long long *sums) {
+__global__ void __launch_bounds__(256) k_recentre_sum(PartK<T> p, const SysK *sk, const CenK *cen,
+                                                      long long *part) {
     __shared__ SysK s;
-    stage_sys(s, sk);
-    long long acc[PM_MAX_GALAXIES][4];
-#pragma unroll
-    for (int h = 0; h < PM_MAX_GALAXIES; ++h)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) acc[h][k] = 0;
+    __shared__ CenK cs;
+    __shared__ unsigned long long red[PM_MAX_GALAXIES][4];
+    if (threadIdx.x < PM_MAX_GALAXIES * 4) (&red[0][0])[threadIdx.x] = 0;
+    stage_sys(s, sk, cs, cen);
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += stride) {
-        if (p.flags[i] & PM_FLAG_LOST) continue;
-        const int g = p.gal[i];
-        if (g < 0 || g >= s.ngal || !s.gal[g].recentre) continue;
-        const float dx = pm_off32((double)p.x[i], cen[3 * g]);
-        const float dy = pm_off32((double)p.y[i], cen[3 * g + 1]);
-        const float dz = pm_off32((double)p.z[i], cen[3 * g + 2]);
-        if (!(pm_r2(dx, dy, dz) < s.gal[g].rc2)) continue;
-        const long long M = __double2ll_rn(__dmul_rn((double)p.m[i], s.mscale)) >> 26;
-        const int sD = s.gal[g].sD;
-        const long long Dx = __float2ll_rn(ldexpf(dx, sD));
-        const long long Dy = __float2ll_rn(ldexpf(dy, sD));
-        const long long Dz = __float2ll_rn(ldexpf(dz, sD));
-#pragma unroll
-        for (int h = 0; h < PM_MAX_GALAXIES; ++h)
-            if (h == g) { acc[h][0] += M; acc[h][1] += M * Dx; acc[h][2] += M * Dy; acc[h][3] += M * Dz; }
+    for (long long b = (long long)blockIdx.x * blockDim.x; b < p.n; b += stride) {
+        const long long i = b + threadIdx.x;
+        int g = -1;
+        long long M = 0, Dx = 0, Dy = 0, Dz = 0;
+        if (i < p.n && !(p.flags[i] & PM_FLAG_LOST)) {
+            g = p.gal[i];
+            if (g < 0 || g >= s.ngal || !s.gal[g].recentre) {
+                g = -1;
+            } else {
+                const float dx = pm_canon(p.x[i], cs.c[g][0], cs.hi[g][0], cs.lo[g][0]);
+                const float dy = pm_canon(p.y[i], cs.c[g][1], cs.hi[g][1], cs.lo[g][1]);
+                const float dz = pm_canon(p.z[i], cs.c[g][2], cs.hi[g][2], cs.lo[g][2]);
+                if (pm_r2(dx, dy, dz) < s.gal[g].rc2) {
+                    M = pm_qmass(p.m[i], s.mscale, s.mscale_f) >> 26;
+                    const float sc = __int_as_float((127 + s.gal[g].sD) << 23);  // 2^sD
+                    Dx = __float2ll_rn(__fmul_rn(dx, sc));
+                    Dy = __float2ll_rn(__fmul_rn(dy, sc));
+                    Dz = __float2ll_rn(__fmul_rn(dz, sc));
+                } else {
+                    g = -1;
+                }
+            }
+        }
+        for (int h = 0; h < s.ngal; ++h) {
+            if (!__any_sync(0xffffffffu, g == h)) continue;
+            const bool mine = (g == h);
+            const long long v0 = warp_sum_ll(mine ? M : 0);
+            const long long v1 = warp_sum_ll(mine ? M * Dx : 0);
+            const long long v2 = warp_sum_ll(mine ? M * Dy : 0);
+            const long long v3 = warp_sum_ll(mine ? M * Dz : 0);
+            if ((threadIdx.x & 31) == 0) {
+                atomicAdd(&red[h][0], (unsigned long long)v0);
+                atomicAdd(&red[h][1], (unsigned long long)v1);
+                atomicAdd(&red[h][2], (unsigned long long)v2);
+                atomicAdd(&red[h][3], (unsigned long long)v3);
+            }
+        }
     }
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int h = 0; h < PM_MAX_GALAXIES; ++h) {
-        if (h >= s.ngal) break;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const long long v = warp_sum_ll(acc[h][k]);
-            if (lane == 0 && v != 0) atomicAdd(sums + 4 * h + k, (unsigned long long)v);
+    __syncthreads();
+    if (threadIdx.x < PM_MAX_GALAXIES * 4)
+        part[(long long)blockIdx.x * PM_MAX_GALAXIES * 4 + threadIdx.x] = (long long)(&red[0][0])[threadIdx.x];
+}
+
+static __global__ void __launch_bounds__(256) k_recentre_apply(const SysK *sk, CenK *cen, const long long *part,
+                                                               int nblocks, int ngal) {
+    __shared__ long long red[8][PM_MAX_GALAXIES * 4];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int v = 0; v < ngal * 4; ++v) {
+        long long acc = 0;
+        for (int b = threadIdx.x; b < nblocks; b += blockDim.x) acc += part[(long long)b * PM_MAX_GALAXIES * 4 + v];
+        acc = warp_sum_ll(acc);
+        if (lane == 0) red[w][v] = acc;
+    }
+    __syncthreads();
+    const int g = threadIdx.x;
+    if (g >= ngal) return;
+    long long S[4];
+    for (int k = 0; k < 4; ++k) {
+        S[k] = 0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) S[k] += red[q][4 * g + k];
+    }
+    if (sk->gal[g].recentre && S[0] > 0) {
+        const double sc = ldexp(1.0, -sk->gal[g].sD);
+        for (int k = 0; k < 3; ++k) {
+            const double c = __dadd_rn(cen->c[g][k], __dmul_rn(__ddiv_rn(__ll2double_rn(S[1 + k]), __ll2double_rn(S[0])), sc));
+            const float hi = __double2float_rn(c);
+            cen->c[g][k] = c;
+            cen->hi[g][k] = hi;
+            cen->lo[g][k] = __double2float_rn(__dsub_rn(c, (double)hi));
         }
     }
 }
 
-static __global__ void k_recentre_apply(const SysK *sk, double *cen, unsigned long long *sums, int ngal) {
-    const int g = threadIdx.x;
-    if (g >= ngal) return;
-    const long long M = (long long)sums[4 * g];
-    if (sk->gal[g].recentre && M > 0) {
-        const double sc = ldexp(1.0, -sk->gal[g].sD);
-        for (int k = 0; k < 3; ++k) {
-            const long long MD = (long long)sums[4 * g + 1 + k];
-            cen[3 * g + k] = __dadd_rn(cen[3 * g + k], __dmul_rn(__ddiv_rn(__ll2double_rn(MD), __ll2double_rn(M)), sc));
+// ---------------------------------------------------------------------------
+// Spatial counting sort of the particles: key = (galaxy, region, bin of the
+// finest grid of that region); a warp then works on particles of the same or
+// neighbouring cells, so the deposit atomics and stencil gathers of its lanes
+// share addresses.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_sort_key(PartK<T> p, const SysK *sk, const CenK *cen, SortK so,
+                                                  unsigned *count, unsigned *key, unsigned *rank) {
+    __shared__ SysK s;
+    __shared__ CenK cs;
+    stage_sys(s, sk, cs, cen);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += stride) {
+        unsigned k = (unsigned)(so.nkeys - 1);  // lost
+        const int g = p.gal[i];
+        if (!(p.flags[i] & PM_FLAG_LOST) && g >= 0 && g < s.ngal) {
+            const T x = p.x[i], y = p.y[i], z = p.z[i];
+            const GalK &G = s.gal[g];
+            const float fx = pm_canon(x, cs.c[g][0], cs.hi[g][0], cs.lo[g][0]);
+            const float fy = pm_canon(y, cs.c[g][1], cs.hi[g][1], cs.lo[g][1]);
+            const float fz = pm_canon(z, cs.c[g][2], cs.hi[g][2], cs.lo[g][2]);
+            Cell cf, cm;
+            const int reg = pm_region(G, fx, fy, fz, cf, cm);
+            const GeomK *gm;
+            Cell c;
+            if (reg == REG_CORE) { gm = &G.fine; c = cf; }
+            else if (reg == REG_SHELL) { gm = &G.med; c = cm; }
+            else {
+                gm = &G.coarse;
+                c = pm_cells(G.coarse, pm_canon(x, s.sc[0], s.sc_hi[0], s.sc_lo[0]),
+                             pm_canon(y, s.sc[1], s.sc_hi[1], s.sc_lo[1]), pm_canon(z, s.sc[2], s.sc_hi[2], s.sc_lo[2]));
+            }
+            if (c.ok) {
+                const int b = so.shift[g][reg];
+                const long long bin = ((long long)(c.k >> b) * (gm->ny >> b) + (c.j >> b)) * (gm->nx >> b) + (c.i >> b);
+                k = (unsigned)(so.base[g][reg] + bin);
+            }
         }
+        key[i] = k;
+        rank[i] = atomicAdd(count + k, 1u);
     }
-    for (int k = 0; k < 4; ++k) sums[4 * g + k] = 0;
+}
+
+constexpr int SCAN_TILE = 2048;  // 256 threads x 8
+
+__device__ __forceinline__ unsigned block_excl_scan(unsigned v, unsigned *tmp, unsigned &total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    unsigned x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) tmp[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        unsigned t = lane < nw ? tmp[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < nw) tmp[lane] = t;
+    }
+    __syncthreads();
+    total = tmp[nw - 1];
+    const unsigned before = w > 0 ? tmp[w - 1] : 0u;
+    __syncthreads();
+    return before + x - v;
+}
+
+static __global__ void __launch_bounds__(256) k_scan_reduce(const unsigned *a, long long n, unsigned *bsum) {
+    __shared__ unsigned tmp[32];
+    const long long t0 = (long long)blockIdx.x * SCAN_TILE;
+    unsigned v = 0;
+    for (int k = 0; k < SCAN_TILE / 256; ++k) {
+        const long long i = t0 + k * 256 + threadIdx.x;
+        if (i < n) v += a[i];
+    }
+    unsigned total;
+    block_excl_scan(v, tmp, total);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+}
+
+static __global__ void __launch_bounds__(1024) k_scan_top(unsigned *bsum, int nb) {
+    __shared__ unsigned tmp[32];
+    const int per = (nb + blockDim.x - 1) / blockDim.x;
+    const int b0 = threadIdx.x * per;
+    unsigned v = 0;
+    for (int k = 0; k < per; ++k)
+        if (b0 + k < nb) v += bsum[b0 + k];
+    unsigned total;
+    unsigned run = block_excl_scan(v, tmp, total);
+    for (int k = 0; k < per; ++k)
+        if (b0 + k < nb) {
+            const unsigned t = bsum[b0 + k];
+            bsum[b0 + k] = run;
+            run += t;
+        }
+}
+
+static __global__ void __launch_bounds__(256) k_scan_down(unsigned *a, long long n, const unsigned *bsum) {
+    __shared__ unsigned tmp[32];
+    const long long t0 = (long long)blockIdx.x * SCAN_TILE + (long long)threadIdx.x * (SCAN_TILE / 256);
+    unsigned v[SCAN_TILE / 256];
+    unsigned sum = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_TILE / 256; ++k) {
+        v[k] = (t0 + k < n) ? a[t0 + k] : 0u;
+        sum += v[k];
+    }
+    unsigned total;
+    unsigned run = block_excl_scan(sum, tmp, total) + bsum[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < SCAN_TILE / 256; ++k) {
+        if (t0 + k < n) a[t0 + k] = run;
+        run += v[k];
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_sort_scatter(PartK<T> p, PartK<T> d, const unsigned *key, const unsigned *rank,
+                                                      const unsigned *off, long long *perm) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += stride) {
+        const long long j = (long long)off[key[i]] + rank[i];
+        d.x[j] = p.x[i]; d.y[j] = p.y[i]; d.z[j] = p.z[i];
+        d.vx[j] = p.vx[i]; d.vy[j] = p.vy[i]; d.vz[j] = p.vz[i];
+        const_cast<T *>(d.m)[j] = p.m[i];
+        const_cast<int32_t *>(d.gal)[j] = p.gal[i];
+        d.flags[j] = p.flags[i];
+        if (perm) perm[j] = i;
+    }
 }
 
 template <typename T>
@@ -612,14 +835,14 @@ template <typename T> cudaError_t pm_launch_col(const FftArgs &a, int mode, int 
 }
 
 template <typename T>
-cudaError_t pm_launch_deposit(const PartK<T> &p, const SysK *sk, const double *cen, cudaStream_t st) {
+cudaError_t pm_launch_deposit(const PartK<T> &p, const SysK *sk, const CenK *cen, int aggregate, cudaStream_t st) {
     if (p.n <= 0) return cudaSuccess;
-    pmk::k_deposit<T><<<pmk_host::particle_grid(p.n), 256, 0, st>>>(p, sk, cen);
+    pmk::k_deposit<T><<<pmk_host::particle_grid(p.n), 256, 0, st>>>(p, sk, cen, aggregate);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t pm_launch_force(int mode, const PartK<T> &p, const SysK *sk, const double *cen, double dt,
+cudaError_t pm_launch_force(int mode, const PartK<T> &p, const SysK *sk, const CenK *cen, double dt,
                             T *ax, T *ay, T *az, double *diag, cudaStream_t st) {
     if (p.n <= 0) return cudaSuccess;
     const int g = pmk_host::particle_grid(p.n);
@@ -634,11 +857,40 @@ cudaError_t pm_launch_force(int mode, const PartK<T> &p, const SysK *sk, const d
 }
 
 template <typename T>
-cudaError_t pm_launch_recentre(const PartK<T> &p, const SysK *sk, double *cen, unsigned long long *sums,
+cudaError_t pm_launch_recentre(const PartK<T> &p, const SysK *sk, CenK *cen, long long *part,
                                int ngal, cudaStream_t st) {
-    if (p.n > 0) pmk::k_recentre_sum<T><<<pmk_host::particle_grid(p.n), 256, 0, st>>>(p, sk, cen, sums);
-    pmk::k_recentre_apply<<<1, 32, 0, st>>>(sk, cen, sums, ngal);
+    if (p.n <= 0) return cudaSuccess;
+    long long nb = (p.n + 255) / 256;
+    if (nb > pmk::RECENTRE_MAX_BLOCKS) nb = pmk::RECENTRE_MAX_BLOCKS;
+    pmk::k_recentre_sum<T><<<(int)nb, 256, 0, st>>>(p, sk, cen, part);
+    pmk::k_recentre_apply<<<1, 256, 0, st>>>(sk, cen, part, (int)nb, ngal);
     return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t pm_launch_sort(const PartK<T> &p, const PartK<T> &scratch, const SysK *sk, const CenK *cen,
+                           const SortK &so, unsigned *count, unsigned *key, unsigned *rank, unsigned *bsum,
+                           long long *perm, cudaStream_t st) {
+    if (p.n <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(count, 0, (size_t)so.nkeys * sizeof(unsigned), st);
+    if (e) return e;
+    const int g = pmk_host::particle_grid(p.n);
+    pmk::k_sort_key<T><<<g, 256, 0, st>>>(p, sk, cen, so, count, key, rank);
+    const int nb = (int)((so.nkeys + pmk::SCAN_TILE - 1) / pmk::SCAN_TILE);
+    pmk::k_scan_reduce<<<nb, 256, 0, st>>>(count, so.nkeys, bsum);
+    pmk::k_scan_top<<<1, 1024, 0, st>>>(bsum, nb);
+    pmk::k_scan_down<<<nb, 256, 0, st>>>(count, so.nkeys, bsum);
+    pmk::k_sort_scatter<T><<<g, 256, 0, st>>>(p, scratch, key, rank, count, perm);
+    if ((e = cudaGetLastError())) return e;
+    const size_t b = (size_t)p.n * sizeof(T);
+    void *const src[9] = {scratch.x, scratch.y, scratch.z, scratch.vx, scratch.vy, scratch.vz,
+                          (void *)scratch.m, (void *)scratch.gal, scratch.flags};
+    void *const dst[9] = {p.x, p.y, p.z, p.vx, p.vy, p.vz, (void *)p.m, (void *)p.gal, p.flags};
+    for (int k = 0; k < 9; ++k) {
+        const size_t bytes = k < 7 ? b : (size_t)p.n * 4;
+        if ((e = cudaMemcpyAsync(dst[k], src[k], bytes, cudaMemcpyDeviceToDevice, st))) return e;
+    }
+    return cudaSuccess;
 }
 
 template <typename T>
@@ -659,10 +911,13 @@ cudaError_t pm_store_hhat(const double *in, T *out, long long n, double scale, c
     template cudaError_t pm_launch_xfwd<T>(const FftArgs &, int, cudaStream_t);                               \
     template cudaError_t pm_launch_xinv<T>(const FftArgs &, int, cudaStream_t);                               \
     template cudaError_t pm_launch_col<T>(const FftArgs &, int, int, cudaStream_t);                           \
-    template cudaError_t pm_launch_deposit<T>(const PartK<T> &, const SysK *, const double *, cudaStream_t);   \
-    template cudaError_t pm_launch_force<T>(int, const PartK<T> &, const SysK *, const double *, double, T *, \
+    template cudaError_t pm_launch_deposit<T>(const PartK<T> &, const SysK *, const CenK *, int, cudaStream_t); \
+    template cudaError_t pm_launch_force<T>(int, const PartK<T> &, const SysK *, const CenK *, double, T *,   \
                                             T *, T *, double *, cudaStream_t);                                 \
-    template cudaError_t pm_launch_recentre<T>(const PartK<T> &, const SysK *, double *, unsigned long long *, \
+    template cudaError_t pm_launch_recentre<T>(const PartK<T> &, const SysK *, CenK *, long long *,            \
                                                int, cudaStream_t);                                             \
     template cudaError_t pm_launch_count_lost<T>(const PartK<T> &, unsigned long long *, cudaStream_t);       \
+    template cudaError_t pm_launch_sort<T>(const PartK<T> &, const PartK<T> &, const SysK *, const CenK *,     \
+                                           const SortK &, unsigned *, unsigned *, unsigned *, unsigned *,       \
+                                           long long *, cudaStream_t);                                          \
     template cudaError_t pm_store_hhat<T>(const double *, T *, long long, double, cudaStream_t);

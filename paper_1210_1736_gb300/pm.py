@@ -70,6 +70,8 @@ _SIGS.update({
     "pm_count_lost": (C.c_int, [_vp, _P(pm_particles), _P(C.c_int64)]),
     "pm_info": (C.c_int, [_vp, _P(C.c_int64)]),
     "pm_step_timed": (C.c_int, [_vp, _P(pm_particles), C.c_double, C.c_int32, _P(C.c_float)]),
+    "pm_sort": (C.c_int, [_vp, _P(pm_particles), _vp]),
+    "pm_set_sort_interval": (C.c_int, [_vp, C.c_int32]),
     "pm_potential_static": (C.c_int, [_vp, _vp, C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_double,
                                       C.c_double, C.c_double, C.c_int32, C.c_int32, _vp]),
 })
@@ -242,8 +244,16 @@ class Context:
     def step(self, p, dt, nsteps=1):
         _check(lib().pm_step(self.h, C.byref(p.struct()), float(dt), int(nsteps)))
 
+    def sort(self, p, perm=None):
+        """Spatially sort p's arrays in place; perm (int64 device tensor of
+        length n, optional) receives perm[new] = old."""
+        _check(lib().pm_sort(self.h, C.byref(p.struct()), None if perm is None else perm.data_ptr()))
+
+    def set_sort_interval(self, k):
+        _check(lib().pm_set_sort_interval(self.h, int(k)))
+
     def step_timed(self, p, dt, nsteps=1):
-        out = (C.c_float * 9)()
+        out = (C.c_float * 10)()
         _check(lib().pm_step_timed(self.h, C.byref(p.struct()), float(dt), int(nsteps), out))
         return list(out)
 
