@@ -127,11 +127,15 @@ struct pm_ctx {
     SysK *d_sys = nullptr;
     CenK *d_cen = nullptr;
     long long *d_csum = nullptr;   // per-block partial centre-of-mass sums
+    unsigned *d_ticket = nullptr;  // blocks done (reset by the last one)
     double *d_diag = nullptr;
     unsigned long long *d_cnt = nullptr;
     void *d_tw[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     cudaStream_t user = nullptr;
     cudaStream_t cap = nullptr;
+    std::vector<cudaStream_t> branch;   // one per geometry (solve branches)
+    std::vector<cudaEvent_t> ev_join;
+    cudaEvent_t ev_fork = nullptr;
     cudaGraph_t graph[2] = {nullptr, nullptr};        // [0] step, [1] sort + step
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     pm_particles gkey;
@@ -245,8 +249,10 @@ template <typename T> int upload_twiddles(pm_ctx *c) {
 // ---- the passes of pm_solve, one launch per geometry -----------------------
 enum { PASS_XFWD = 0, PASS_YFWD, PASS_ZCONV, PASS_YINV, PASS_XINV, NPASS };
 
-template <typename T> int launch_pass(pm_ctx *c, int pass, cudaStream_t st) {
-    for (const GeoBuf &gb : c->geos) {
+template <typename T> int launch_pass(pm_ctx *c, int pass, cudaStream_t st, int only = -1) {
+    for (int gi = 0; gi < (int)c->geos.size(); ++gi) {
+        if (only >= 0 && gi != only) continue;
+        const GeoBuf &gb = c->geos[gi];
         const pm_geometry &g = gb.g;
         for (size_t b0 = 0; b0 < gb.sets.size(); b0 += PM_MAX_BATCH) {
             const int nb = (int)std::min<size_t>(PM_MAX_BATCH, gb.sets.size() - b0);
@@ -291,10 +297,24 @@ template <typename T> int launch_pass(pm_ctx *c, int pass, cudaStream_t st) {
     return PM_OK;
 }
 
+// With ev (phase timing) the passes run pass by pass on st; otherwise each
+// geometry's chain of five passes runs on its own branch stream (forked from
+// and joined back to st), so independent geometries overlap on the GPU.
 template <typename T> int enqueue_solve(pm_ctx *c, cudaStream_t st, cudaEvent_t *ev) {
-    for (int pass = 0; pass < NPASS; ++pass) {
-        PM_TRY(launch_pass<T>(c, pass, st));
-        if (ev) PM_CK(cudaEventRecord(ev[pass], st));
+    if (ev || c->geos.size() < 2) {
+        for (int pass = 0; pass < NPASS; ++pass) {
+            PM_TRY(launch_pass<T>(c, pass, st));
+            if (ev) PM_CK(cudaEventRecord(ev[pass], st));
+        }
+        return PM_OK;
+    }
+    PM_CK(cudaEventRecord(c->ev_fork, st));
+    for (int gi = 0; gi < (int)c->geos.size(); ++gi) {
+        cudaStream_t b = c->branch[gi];
+        PM_CK(cudaStreamWaitEvent(b, c->ev_fork, 0));
+        for (int pass = 0; pass < NPASS; ++pass) PM_TRY(launch_pass<T>(c, pass, b, gi));
+        PM_CK(cudaEventRecord(c->ev_join[gi], b));
+        PM_CK(cudaStreamWaitEvent(st, c->ev_join[gi], 0));
     }
     return PM_OK;
 }
@@ -307,7 +327,7 @@ template <typename T> int enqueue_deposit(pm_ctx *c, const pm_particles *p, cuda
 
 template <typename T> int enqueue_recentre(pm_ctx *c, const pm_particles *p, cudaStream_t st) {
     if (!c->any_recentre) return PM_OK;
-    PM_CK(pm_launch_recentre<T>(part_k<T>(p), c->d_sys, c->d_cen, c->d_csum, c->sys.ngal, st));
+    PM_CK(pm_launch_recentre<T>(part_k<T>(p), c->d_sys, c->d_cen, c->d_csum, c->d_ticket, st));
     return PM_OK;
 }
 
@@ -570,6 +590,18 @@ int pm_create_grids(const pm_system *sys, const pm_galaxy *gals, void *stream, p
             if (cudaMemsetAsync(c->work[gi][k], 0, gb.workN * 2 * c->esz, c->user) != cudaSuccess)
                 return cleanup(fail(PM_E_CUDA, "memset failed"));
         }
+    if (cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess)
+        return cleanup(fail(PM_E_CUDA, "cudaEventCreate failed"));
+    for (size_t gi = 0; gi < c->geos.size(); ++gi) {
+        cudaStream_t b;
+        cudaEvent_t e;
+        if (cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking) != cudaSuccess)
+            return cleanup(fail(PM_E_CUDA, "cudaStreamCreate failed"));
+        c->branch.push_back(b);
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+            return cleanup(fail(PM_E_CUDA, "cudaEventCreate failed"));
+        c->ev_join.push_back(e);
+    }
     for (GeoBuf &gb : c->geos) {
         if ((rc = dev_alloc(c, &gb.hhat, gb.hatN * c->esz))) return cleanup(rc);
         if ((rc = build_hhat(c, gb))) return cleanup(rc);
@@ -626,6 +658,7 @@ int pm_create_grids(const pm_system *sys, const pm_galaxy *gals, void *stream, p
     if ((rc = dev_alloc(c, (void **)&c->d_sys, sizeof(SysK)))) return cleanup(rc);
     if ((rc = dev_alloc(c, (void **)&c->d_cen, sizeof(CenK)))) return cleanup(rc);
     if ((rc = dev_alloc(c, (void **)&c->d_csum, sizeof(long long) * 4 * PM_MAX_GALAXIES * 2048))) return cleanup(rc);
+    if ((rc = dev_alloc(c, (void **)&c->d_ticket, sizeof(unsigned)))) return cleanup(rc);
     if ((rc = dev_alloc(c, (void **)&c->d_diag, sizeof(double) * 8))) return cleanup(rc);
     if ((rc = dev_alloc(c, (void **)&c->d_cnt, sizeof(unsigned long long)))) return cleanup(rc);
     double cen[3 * PM_MAX_GALAXIES] = {0};
@@ -634,6 +667,7 @@ int pm_create_grids(const pm_system *sys, const pm_galaxy *gals, void *stream, p
     const CenK ck = make_cenk(cen, sys->ngal);
     if (cudaMemcpyAsync(c->d_sys, &hs, sizeof(SysK), cudaMemcpyHostToDevice, c->user) != cudaSuccess ||
         cudaMemcpyAsync(c->d_cen, &ck, sizeof(CenK), cudaMemcpyHostToDevice, c->user) != cudaSuccess ||
+        cudaMemsetAsync(c->d_ticket, 0, sizeof(unsigned), c->user) != cudaSuccess ||
         cudaStreamSynchronize(c->user) != cudaSuccess)
         return cleanup(fail(PM_E_CUDA, "context upload failed: %s", cudaGetErrorString(cudaGetLastError())));
     *out = c;
@@ -644,8 +678,12 @@ void pm_destroy(pm_ctx *c) {
     if (!c) return;
     if (c->user) cudaStreamSynchronize(c->user);
     destroy_graph(c);
+    for (cudaStream_t b : c->branch) cudaStreamSynchronize(b);
     for (void *p : c->allocs) cudaFree(p);
     if (c->cap) cudaStreamDestroy(c->cap);
+    for (cudaStream_t b : c->branch) cudaStreamDestroy(b);
+    for (cudaEvent_t e : c->ev_join) cudaEventDestroy(e);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     delete c;
 }
 

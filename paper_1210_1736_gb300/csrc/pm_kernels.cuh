@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(NT) k_xfwd(FftArgs a) {
 //   COL_YINV : inverse along y, keep y < ny
 // ---------------------------------------------------------------------------
 template <typename T, int L, int MODE>
-__global__ void __launch_bounds__(NT) k_col(FftArgs a) {
+__global__ void __launch_bounds__(NT, 4) k_col(FftArgs a) {
     typedef typename cplx_t<T>::type C;
     typedef CShape<L> S;
     constexpr int NS = nstages(L);
@@ -509,41 +509,47 @@ __device__ __forceinline__ long long warp_sum_ll(long long v) {
 
 // Step a1: exact integer centre-of-mass sums within R_core of each galaxy's
 // current centre: sum M, sum M*D (M = q >> 26, D = rint(d * 2^sD)).  Warp
-// sums go to shared memory; each block writes its partial sums to
-// part[block][galaxy][4] (no contended global atomics); the apply kernel adds
-// the partials (integer sums: the order does not matter).
-constexpr int RECENTRE_MAX_BLOCKS = 2048;
+// sums go to shared memory, each block writes its partials to
+// part[block][galaxy][4]; the last block to finish (ticket counter after a
+// memory fence, no waiting) adds all partials -- integer sums, so the order
+// does not matter -- and moves the centres: c += (sum M D / sum M) 2^-sD.
+constexpr int RECENTRE_MAX_BLOCKS = 608;
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_recentre_sum(PartK<T> p, const SysK *sk, const CenK *cen,
-                                                      long long *part) {
+__global__ void __launch_bounds__(256) k_recentre(PartK<T> p, const SysK *sk, CenK *cen, long long *part,
+                                                  unsigned *ticket) {
     __shared__ SysK s;
     __shared__ CenK cs;
     __shared__ unsigned long long red[PM_MAX_GALAXIES][4];
+    __shared__ long long red2[8][PM_MAX_GALAXIES * 4];
+    __shared__ bool last;
     if (threadIdx.x < PM_MAX_GALAXIES * 4) (&red[0][0])[threadIdx.x] = 0;
     stage_sys(s, sk, cs, cen);
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long b = (long long)blockIdx.x * blockDim.x; b < p.n; b += stride) {
         const long long i = b + threadIdx.x;
+        uint32_t f = PM_FLAG_LOST;
         int g = -1;
+        T x = 0, y = 0, z = 0, m = 0;
+        if (i < p.n) {  // all loads issued together
+            f = p.flags[i]; g = p.gal[i];
+            x = p.x[i]; y = p.y[i]; z = p.z[i]; m = p.m[i];
+        }
         long long M = 0, Dx = 0, Dy = 0, Dz = 0;
-        if (i < p.n && !(p.flags[i] & PM_FLAG_LOST)) {
-            g = p.gal[i];
-            if (g < 0 || g >= s.ngal || !s.gal[g].recentre) {
-                g = -1;
+        if ((f & PM_FLAG_LOST) || g < 0 || g >= s.ngal || !s.gal[g].recentre) {
+            g = -1;
+        } else {
+            const float dx = pm_canon(x, cs.c[g][0], cs.hi[g][0], cs.lo[g][0]);
+            const float dy = pm_canon(y, cs.c[g][1], cs.hi[g][1], cs.lo[g][1]);
+            const float dz = pm_canon(z, cs.c[g][2], cs.hi[g][2], cs.lo[g][2]);
+            if (pm_r2(dx, dy, dz) < s.gal[g].rc2) {
+                M = pm_qmass(m, s.mscale, s.mscale_f) >> 26;
+                const float sc = __int_as_float((127 + s.gal[g].sD) << 23);  // 2^sD
+                Dx = __float2ll_rn(__fmul_rn(dx, sc));
+                Dy = __float2ll_rn(__fmul_rn(dy, sc));
+                Dz = __float2ll_rn(__fmul_rn(dz, sc));
             } else {
-                const float dx = pm_canon(p.x[i], cs.c[g][0], cs.hi[g][0], cs.lo[g][0]);
-                const float dy = pm_canon(p.y[i], cs.c[g][1], cs.hi[g][1], cs.lo[g][1]);
-                const float dz = pm_canon(p.z[i], cs.c[g][2], cs.hi[g][2], cs.lo[g][2]);
-                if (pm_r2(dx, dy, dz) < s.gal[g].rc2) {
-                    M = pm_qmass(p.m[i], s.mscale, s.mscale_f) >> 26;
-                    const float sc = __int_as_float((127 + s.gal[g].sD) << 23);  // 2^sD
-                    Dx = __float2ll_rn(__fmul_rn(dx, sc));
-                    Dy = __float2ll_rn(__fmul_rn(dy, sc));
-                    Dz = __float2ll_rn(__fmul_rn(dz, sc));
-                } else {
-                    g = -1;
-                }
+                g = -1;
             }
         }
         for (int h = 0; h < s.ngal; ++h) {
@@ -564,30 +570,33 @@ __global__ void __launch_bounds__(256) k_recentre_sum(PartK<T> p, const SysK *sk
     __syncthreads();
     if (threadIdx.x < PM_MAX_GALAXIES * 4)
         part[(long long)blockIdx.x * PM_MAX_GALAXIES * 4 + threadIdx.x] = (long long)(&red[0][0])[threadIdx.x];
-}
-
-static __global__ void __launch_bounds__(256) k_recentre_apply(const SysK *sk, CenK *cen, const long long *part,
-                                                               int nblocks, int ngal) {
-    __shared__ long long red[8][PM_MAX_GALAXIES * 4];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int v = 0; v < ngal * 4; ++v) {
+    for (int v = 0; v < s.ngal * 4; ++v) {
         long long acc = 0;
-        for (int b = threadIdx.x; b < nblocks; b += blockDim.x) acc += part[(long long)b * PM_MAX_GALAXIES * 4 + v];
+        for (int q = threadIdx.x; q < (int)gridDim.x; q += blockDim.x)
+            acc += __ldcg(part + (long long)q * PM_MAX_GALAXIES * 4 + v);
         acc = warp_sum_ll(acc);
-        if (lane == 0) red[w][v] = acc;
+        if (lane == 0) red2[w][v] = acc;
     }
     __syncthreads();
     const int g = threadIdx.x;
-    if (g >= ngal) return;
+    if (g == 0) *ticket = 0;
+    if (g >= s.ngal) return;
     long long S[4];
     for (int k = 0; k < 4; ++k) {
         S[k] = 0;
-        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) S[k] += red[q][4 * g + k];
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) S[k] += red2[q][4 * g + k];
     }
-    if (sk->gal[g].recentre && S[0] > 0) {
-        const double sc = ldexp(1.0, -sk->gal[g].sD);
+    if (s.gal[g].recentre && S[0] > 0) {
+        const double sc = ldexp(1.0, -s.gal[g].sD);
         for (int k = 0; k < 3; ++k) {
-            const double c = __dadd_rn(cen->c[g][k], __dmul_rn(__ddiv_rn(__ll2double_rn(S[1 + k]), __ll2double_rn(S[0])), sc));
+            const double c = __dadd_rn(cs.c[g][k], __dmul_rn(__ddiv_rn(__ll2double_rn(S[1 + k]), __ll2double_rn(S[0])), sc));
             const float hi = __double2float_rn(c);
             cen->c[g][k] = c;
             cen->hi[g][k] = hi;
@@ -636,7 +645,17 @@ __global__ void __launch_bounds__(256) k_sort_key(PartK<T> p, const SysK *sk, co
             }
         }
         key[i] = k;
-        rank[i] = atomicAdd(count + k, 1u);
+        // warp-aggregated ranking: lanes with the same key take consecutive
+        // ranks from one atomic (the lanes of a warp run this loop together
+        // only while i < n, so use the lanes that are here)
+        const unsigned act = __activemask();
+        const unsigned peers = __match_any_sync(act, k);
+        const int lane = threadIdx.x & 31;
+        const int leader = __ffs(peers) - 1;
+        unsigned base = 0;
+        if (lane == leader) base = atomicAdd(count + k, (unsigned)__popc(peers));
+        base = __shfl_sync(peers, base, leader);
+        rank[i] = base + __popc(peers & ((1u << lane) - 1u));
     }
 }
 
@@ -717,19 +736,24 @@ static __global__ void __launch_bounds__(256) k_scan_down(unsigned *a, long long
     }
 }
 
+// One particle per thread (full grid): every load is issued before the
+// destination is known, so a warp keeps all its reads in flight.
 template <typename T>
 __global__ void __launch_bounds__(256) k_sort_scatter(PartK<T> p, PartK<T> d, const unsigned *key, const unsigned *rank,
                                                       const unsigned *off, long long *perm) {
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += stride) {
-        const long long j = (long long)off[key[i]] + rank[i];
-        d.x[j] = p.x[i]; d.y[j] = p.y[i]; d.z[j] = p.z[i];
-        d.vx[j] = p.vx[i]; d.vy[j] = p.vy[i]; d.vz[j] = p.vz[i];
-        const_cast<T *>(d.m)[j] = p.m[i];
-        const_cast<int32_t *>(d.gal)[j] = p.gal[i];
-        d.flags[j] = p.flags[i];
-        if (perm) perm[j] = i;
-    }
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= p.n) return;
+    const unsigned k = key[i], r = rank[i];
+    const T x = p.x[i], y = p.y[i], z = p.z[i], vx = p.vx[i], vy = p.vy[i], vz = p.vz[i], m = p.m[i];
+    const int32_t g = p.gal[i];
+    const uint32_t f = p.flags[i];
+    const long long j = (long long)off[k] + r;
+    d.x[j] = x; d.y[j] = y; d.z[j] = z;
+    d.vx[j] = vx; d.vy[j] = vy; d.vz[j] = vz;
+    const_cast<T *>(d.m)[j] = m;
+    const_cast<int32_t *>(d.gal)[j] = g;
+    d.flags[j] = f;
+    if (perm) perm[j] = i;
 }
 
 template <typename T>
@@ -858,12 +882,11 @@ cudaError_t pm_launch_force(int mode, const PartK<T> &p, const SysK *sk, const C
 
 template <typename T>
 cudaError_t pm_launch_recentre(const PartK<T> &p, const SysK *sk, CenK *cen, long long *part,
-                               int ngal, cudaStream_t st) {
+                               unsigned *ticket, cudaStream_t st) {
     if (p.n <= 0) return cudaSuccess;
     long long nb = (p.n + 255) / 256;
     if (nb > pmk::RECENTRE_MAX_BLOCKS) nb = pmk::RECENTRE_MAX_BLOCKS;
-    pmk::k_recentre_sum<T><<<(int)nb, 256, 0, st>>>(p, sk, cen, part);
-    pmk::k_recentre_apply<<<1, 256, 0, st>>>(sk, cen, part, (int)nb, ngal);
+    pmk::k_recentre<T><<<(int)nb, 256, 0, st>>>(p, sk, cen, part, ticket);
     return cudaGetLastError();
 }
 
@@ -880,7 +903,7 @@ cudaError_t pm_launch_sort(const PartK<T> &p, const PartK<T> &scratch, const Sys
     pmk::k_scan_reduce<<<nb, 256, 0, st>>>(count, so.nkeys, bsum);
     pmk::k_scan_top<<<1, 1024, 0, st>>>(bsum, nb);
     pmk::k_scan_down<<<nb, 256, 0, st>>>(count, so.nkeys, bsum);
-    pmk::k_sort_scatter<T><<<g, 256, 0, st>>>(p, scratch, key, rank, count, perm);
+    pmk::k_sort_scatter<T><<<(unsigned)((p.n + 255) / 256), 256, 0, st>>>(p, scratch, key, rank, count, perm);
     if ((e = cudaGetLastError())) return e;
     const size_t b = (size_t)p.n * sizeof(T);
     void *const src[9] = {scratch.x, scratch.y, scratch.z, scratch.vx, scratch.vy, scratch.vz,
@@ -915,7 +938,7 @@ cudaError_t pm_store_hhat(const double *in, T *out, long long n, double scale, c
     template cudaError_t pm_launch_force<T>(int, const PartK<T> &, const SysK *, const CenK *, double, T *,   \
                                             T *, T *, double *, cudaStream_t);                                 \
     template cudaError_t pm_launch_recentre<T>(const PartK<T> &, const SysK *, CenK *, long long *,            \
-                                               int, cudaStream_t);                                             \
+                                               unsigned *, cudaStream_t);                                      \
     template cudaError_t pm_launch_count_lost<T>(const PartK<T> &, unsigned long long *, cudaStream_t);       \
     template cudaError_t pm_launch_sort<T>(const PartK<T> &, const PartK<T> &, const SysK *, const CenK *,     \
                                            const SortK &, unsigned *, unsigned *, unsigned *, unsigned *,       \

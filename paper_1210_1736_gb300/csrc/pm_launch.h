@@ -33,8 +33,8 @@ template <typename T>
 cudaError_t pm_launch_force(int mode, const PartK<T> &p, const SysK *sk, const CenK *cen, double dt,
                             T *ax, T *ay, T *az, double *diag, cudaStream_t st);
 template <typename T>
-cudaError_t pm_launch_recentre(const PartK<T> &p, const SysK *sk, CenK *cen,
-                               long long *part, int ngal, cudaStream_t st);
+cudaError_t pm_launch_recentre(const PartK<T> &p, const SysK *sk, CenK *cen, long long *part,
+                               unsigned *ticket, cudaStream_t st);
 template <typename T>
 cudaError_t pm_launch_count_lost(const PartK<T> &p, unsigned long long *out, cudaStream_t st);
 // Counting sort by spatial key; permutes p's arrays in place through scratch.
