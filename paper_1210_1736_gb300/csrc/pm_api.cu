@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -126,8 +127,7 @@ struct pm_ctx {
     SysK hs;
     SysK *d_sys = nullptr;
     CenK *d_cen = nullptr;
-    long long *d_csum = nullptr;   // per-block partial centre-of-mass sums
-    unsigned *d_ticket = nullptr;  // blocks done (reset by the last one)
+    long long *d_csum = nullptr;   // centre-of-mass accumulators (zero between uses)
     double *d_diag = nullptr;
     unsigned long long *d_cnt = nullptr;
     void *d_tw[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -136,7 +136,8 @@ struct pm_ctx {
     std::vector<cudaStream_t> branch;   // one per geometry (solve branches)
     std::vector<cudaEvent_t> ev_join;
     cudaEvent_t ev_fork = nullptr;
-    cudaGraph_t graph[2] = {nullptr, nullptr};        // [0] step, [1] sort + step
+    // captured steps: [0] step, [1] sort + step
+    cudaGraph_t graph[2] = {nullptr, nullptr};
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     pm_particles gkey;
     double gdt = 0;
@@ -321,13 +322,13 @@ template <typename T> int enqueue_solve(pm_ctx *c, cudaStream_t st, cudaEvent_t 
 
 template <typename T> int enqueue_deposit(pm_ctx *c, const pm_particles *p, cudaStream_t st) {
     PM_CK(cudaMemsetAsync(c->rho_all, 0, c->rho_bytes, st));
-    PM_CK(pm_launch_deposit<T>(part_k<T>(p), c->d_sys, c->d_cen, c->sort_interval > 0 ? 1 : 0, st));
+    PM_CK(pm_launch_deposit<T>(part_k<T>(p), c->hs, c->d_cen, c->sort_interval > 0 ? 1 : 0, st));
     return PM_OK;
 }
 
 template <typename T> int enqueue_recentre(pm_ctx *c, const pm_particles *p, cudaStream_t st) {
     if (!c->any_recentre) return PM_OK;
-    PM_CK(pm_launch_recentre<T>(part_k<T>(p), c->d_sys, c->d_cen, c->d_csum, c->d_ticket, st));
+    PM_CK(pm_launch_recentre<T>(part_k<T>(p), c->hs, c->d_cen, c->d_csum, st));
     return PM_OK;
 }
 
@@ -339,7 +340,7 @@ template <typename T> int enqueue_step(pm_ctx *c, const pm_particles *p, double 
     PM_TRY(enqueue_deposit<T>(c, p, st));
     if (ev) PM_CK(cudaEventRecord(ev[1], st));
     PM_TRY(enqueue_solve<T>(c, st, ev ? ev + 2 : nullptr));
-    PM_CK(pm_launch_force<T>(0, part_k<T>(p), c->d_sys, c->d_cen, dt, nullptr, nullptr, nullptr, nullptr, st));
+    PM_CK(pm_launch_force<T>(0, part_k<T>(p), c->hs, c->d_cen, dt, nullptr, nullptr, nullptr, nullptr, st));
     if (ev) PM_CK(cudaEventRecord(ev[7], st));
     return PM_OK;
 }
@@ -371,13 +372,13 @@ template <typename T> int enqueue_sort(pm_ctx *c, const pm_particles *p, long lo
     scratch.m = (const T *)c->s_arr[6];
     scratch.gal = (const int32_t *)c->s_arr[7];
     scratch.flags = (uint32_t *)c->s_arr[8];
-    PM_CK(pm_launch_sort<T>(part_k<T>(p), scratch, c->d_sys, c->d_cen, c->sortk, c->s_count, c->s_key, c->s_rank,
-                            c->s_bsum, perm, st));
+    PM_CK(pm_launch_sort<T>(part_k<T>(p), scratch, c->hs, c->d_cen, c->sortk, c->s_count, c->s_key,
+                            c->s_rank, c->s_bsum, perm, st));
     return PM_OK;
 }
 
-template <typename T> int capture(pm_ctx *c, const pm_particles *p, double dt, bool with_sort, cudaGraph_t *gr,
-                                  cudaGraphExec_t *ex) {
+template <typename T> int capture(pm_ctx *c, const pm_particles *p, double dt, bool with_sort,
+                                  cudaGraph_t *gr, cudaGraphExec_t *ex) {
     PM_CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
     int rc = with_sort ? enqueue_sort<T>(c, p, nullptr, c->cap) : PM_OK;
     if (rc == PM_OK) rc = enqueue_step<T>(c, p, dt, c->cap, nullptr);
@@ -393,19 +394,20 @@ template <typename T> int capture(pm_ctx *c, const pm_particles *p, double dt, b
 
 template <typename T> int step_impl(pm_ctx *c, const pm_particles *p, double dt, int nsteps) {
     const bool sorting = c->sort_interval > 0 && p->n > 0;
-    const bool same = c->gexec[0] && (!sorting || c->gexec[1]) &&
-                      std::memcmp(&c->gkey, p, sizeof(pm_particles)) == 0 && c->gdt == dt;
+    const bool same = c->gexec[0] && std::memcmp(&c->gkey, p, sizeof(pm_particles)) == 0 && c->gdt == dt;
     if (!same) {
         destroy_graph(c);
         if (sorting) PM_TRY(ensure_sort_scratch(c, p->n));
-        int rc = capture<T>(c, p, dt, false, &c->graph[0], &c->gexec[0]);
-        if (rc == PM_OK && sorting) rc = capture<T>(c, p, dt, true, &c->graph[1], &c->gexec[1]);
-        if (rc != PM_OK) { destroy_graph(c); return rc; }
         c->gkey = *p;
         c->gdt = dt;
     }
     for (int s = 0; s < nsteps; ++s) {
-        const int g = (sorting && c->step_count % c->sort_interval == 0) ? 1 : 0;
+        const bool sort_now = sorting && c->step_count % c->sort_interval == 0;
+        const int g = sort_now ? 1 : 0;
+        if (!c->gexec[g]) {
+            const int rc = capture<T>(c, p, dt, sort_now, &c->graph[g], &c->gexec[g]);
+            if (rc != PM_OK) { destroy_graph(c); return rc; }
+        }
         PM_CK(cudaGraphLaunch(c->gexec[g], c->user));
         ++c->step_count;
     }
@@ -453,7 +455,7 @@ template <typename T> int step_timed_impl(pm_ctx *c, const pm_particles *p, doub
 
 template <typename T> int force_impl(pm_ctx *c, int mode, const pm_particles *p, double dt, void *ax, void *ay,
                                      void *az, double *diag) {
-    PM_CK(pm_launch_force<T>(mode, part_k<T>(p), c->d_sys, c->d_cen, dt, (T *)ax, (T *)ay, (T *)az, diag, c->user));
+    PM_CK(pm_launch_force<T>(mode, part_k<T>(p), c->hs, c->d_cen, dt, (T *)ax, (T *)ay, (T *)az, diag, c->user));
     return PM_OK;
 }
 
@@ -652,13 +654,14 @@ int pm_create_grids(const pm_system *sys, const pm_galaxy *gals, void *stream, p
         }
         so.nkeys = base + 1;
         const long long nb = (so.nkeys + 2047) / 2048;
-        if ((rc = dev_alloc(c, (void **)&c->s_count, (size_t)so.nkeys * 4))) return cleanup(rc);
+        if ((rc = dev_alloc(c, (void **)&c->s_count, (size_t)nb * 2048 * 4))) return cleanup(rc);
         if ((rc = dev_alloc(c, (void **)&c->s_bsum, (size_t)nb * 4))) return cleanup(rc);
     }
     if ((rc = dev_alloc(c, (void **)&c->d_sys, sizeof(SysK)))) return cleanup(rc);
     if ((rc = dev_alloc(c, (void **)&c->d_cen, sizeof(CenK)))) return cleanup(rc);
-    if ((rc = dev_alloc(c, (void **)&c->d_csum, sizeof(long long) * 4 * PM_MAX_GALAXIES * 2048))) return cleanup(rc);
-    if ((rc = dev_alloc(c, (void **)&c->d_ticket, sizeof(unsigned)))) return cleanup(rc);
+    // centre-of-mass accumulators: 64 rows x 8 galaxies x 4 sums, kept zero
+    // between uses by the kernel that consumes them
+    if ((rc = dev_alloc(c, (void **)&c->d_csum, sizeof(long long) * 4 * PM_MAX_GALAXIES * 64))) return cleanup(rc);
     if ((rc = dev_alloc(c, (void **)&c->d_diag, sizeof(double) * 8))) return cleanup(rc);
     if ((rc = dev_alloc(c, (void **)&c->d_cnt, sizeof(unsigned long long)))) return cleanup(rc);
     double cen[3 * PM_MAX_GALAXIES] = {0};
@@ -667,7 +670,7 @@ int pm_create_grids(const pm_system *sys, const pm_galaxy *gals, void *stream, p
     const CenK ck = make_cenk(cen, sys->ngal);
     if (cudaMemcpyAsync(c->d_sys, &hs, sizeof(SysK), cudaMemcpyHostToDevice, c->user) != cudaSuccess ||
         cudaMemcpyAsync(c->d_cen, &ck, sizeof(CenK), cudaMemcpyHostToDevice, c->user) != cudaSuccess ||
-        cudaMemsetAsync(c->d_ticket, 0, sizeof(unsigned), c->user) != cudaSuccess ||
+        cudaMemsetAsync(c->d_csum, 0, sizeof(long long) * 4 * PM_MAX_GALAXIES * 64, c->user) != cudaSuccess ||
         cudaStreamSynchronize(c->user) != cudaSuccess)
         return cleanup(fail(PM_E_CUDA, "context upload failed: %s", cudaGetErrorString(cudaGetLastError())));
     *out = c;

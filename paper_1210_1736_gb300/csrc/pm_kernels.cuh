@@ -257,21 +257,28 @@ __global__ void __launch_bounds__(NT) k_xinv(FftArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Particle kernels.  The system description and the grid centres are staged
-// in shared memory.
+// Particle kernels.  The system description is a __grid_constant__ kernel
+// parameter (read through the constant cache, no staging); the centres of
+// grids 1-3 are read from device memory.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void stage_sys(SysK &s, const SysK *g, CenK &cs, const CenK *cg) {
-    const int *src = reinterpret_cast<const int *>(g);
-    int *dst = reinterpret_cast<int *>(&s);
-    for (int i = threadIdx.x; i < (int)(sizeof(SysK) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
-    const int *src2 = reinterpret_cast<const int *>(cg);
-    int *dst2 = reinterpret_cast<int *>(&cs);
-    for (int i = threadIdx.x; i < (int)(sizeof(CenK) / sizeof(int)); i += blockDim.x) dst2[i] = src2[i];
-    __syncthreads();
-}
-
 __device__ __forceinline__ size_t cell_off(const GeomK &g, const Cell &c) {
     return ((size_t)c.k * g.ny + c.j) * g.nx + c.i;
+}
+
+struct Cen1 {
+    double c[3];
+    float hi[3], lo[3];
+};
+__device__ __forceinline__ Cen1 load_cen(const CenK *cen, int g) {
+    Cen1 r;
+    const CenK *cs = cen;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        r.c[k] = __ldg(&cs->c[g][k]);
+        r.hi[k] = __ldg(&cs->hi[g][k]);
+        r.lo[k] = __ldg(&cs->lo[g][k]);
+    }
+    return r;
 }
 
 // Offset used for Delta in Eq. (eqn:diff): the canonical FP32 offset in FP32
@@ -300,10 +307,8 @@ __device__ __forceinline__ void agg_add(unsigned long long *addr, unsigned long 
 // Steps a2-a3: classification and exact fixed-point mass assignment.  The
 // loop is warp-uniform so the aggregation can use warp collectives.
 template <typename T>
-__global__ void __launch_bounds__(256) k_deposit(PartK<T> p, const SysK *sk, const CenK *cen, int aggregate) {
-    __shared__ SysK s;
-    __shared__ CenK cs;
-    stage_sys(s, sk, cs, cen);
+__global__ void __launch_bounds__(256) k_deposit(PartK<T> p, const __grid_constant__ SysK s, const CenK *cen,
+                                                 int aggregate) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long b = (long long)blockIdx.x * blockDim.x; b < p.n; b += stride) {
         const long long i = b + threadIdx.x;
@@ -313,11 +318,11 @@ __global__ void __launch_bounds__(256) k_deposit(PartK<T> p, const SysK *sk, con
             const uint32_t f = p.flags[i];
             if (!(f & PM_FLAG_LOST)) {
                 const T x = p.x[i], y = p.y[i], z = p.z[i];
+                const int g = p.gal[i];
                 const float sx = pm_canon(x, s.sc[0], s.sc_hi[0], s.sc_lo[0]);
                 const float sy = pm_canon(y, s.sc[1], s.sc_hi[1], s.sc_lo[1]);
                 const float sz = pm_canon(z, s.sc[2], s.sc_hi[2], s.sc_lo[2]);
                 bool lost = !(pm_r2(sx, sy, sz) < s.rsys2);
-                const int g = p.gal[i];
                 if (g < 0 || g >= s.ngal) lost = true;
                 Cell cc;
                 cc.i = cc.j = cc.k = 0; cc.ok = false;
@@ -330,9 +335,10 @@ __global__ void __launch_bounds__(256) k_deposit(PartK<T> p, const SysK *sk, con
                     p.flags[i] = f | PM_FLAG_LOST;
                 } else {
                     const GalK &G = s.gal[g];
-                    const float dx = pm_canon(x, cs.c[g][0], cs.hi[g][0], cs.lo[g][0]);
-                    const float dy = pm_canon(y, cs.c[g][1], cs.hi[g][1], cs.lo[g][1]);
-                    const float dz = pm_canon(z, cs.c[g][2], cs.hi[g][2], cs.lo[g][2]);
+                    const Cen1 ce = load_cen(cen, g);
+                    const float dx = pm_canon(x, ce.c[0], ce.hi[0], ce.lo[0]);
+                    const float dy = pm_canon(y, ce.c[1], ce.hi[1], ce.lo[1]);
+                    const float dz = pm_canon(z, ce.c[2], ce.hi[2], ce.lo[2]);
                     Cell cf, cm;
                     const int reg = pm_region(G, dx, dy, dz, cf, cm);
                     q = (unsigned long long)pm_qmass(p.m[i], s.mscale, s.mscale_f);
@@ -407,200 +413,218 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// Step a8 (+a9): acceleration by Eq. (eqn:diff) on the grids the combination
-// rule selects for each galaxy (Sec. 2.1), then
-//   MODE 0: leap-frog kick-drift   MODE 1: write acceleration
-//   MODE 2: kick only              MODE 3: energy / angular momentum sums
-template <typename T, int MODE>
-__global__ void __launch_bounds__(256) k_force(PartK<T> p, const SysK *sk, const CenK *cen,
-                                               T dt, T *ax, T *ay, T *az, double *diag) {
-    __shared__ SysK s;
-    __shared__ CenK cs;
-    stage_sys(s, sk, cs, cen);
-    double dsum[7] = {0, 0, 0, 0, 0, 0, 0};
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += stride) {
-        if (p.flags[i] & PM_FLAG_LOST) {
-            if (MODE == 1) { ax[i] = 0; ay[i] = 0; az[i] = 0; }
-            continue;
-        }
-        const T xT = p.x[i], yT = p.y[i], zT = p.z[i];
-        const float sx = pm_canon(xT, s.sc[0], s.sc_hi[0], s.sc_lo[0]);
-        const float sy = pm_canon(yT, s.sc[1], s.sc_hi[1], s.sc_lo[1]);
-        const float sz = pm_canon(zT, s.sc[2], s.sc_hi[2], s.sc_lo[2]);
-        const T rsx = rel_off(xT, s.sc[0], s.sc_hi[0], s.sc_lo[0]);
-        const T rsy = rel_off(yT, s.sc[1], s.sc_hi[1], s.sc_lo[1]);
-        const T rsz = rel_off(zT, s.sc[2], s.sc_hi[2], s.sc_lo[2]);
-        T acc[3] = {0, 0, 0};
-        T phiv = 0;
-        T *php = (MODE == 3) ? &phiv : nullptr;
-        for (int h = 0; h < s.ngal; ++h) {
-            const GalK &G = s.gal[h];
-            const float fx = pm_canon(xT, cs.c[h][0], cs.hi[h][0], cs.lo[h][0]);
-            const float fy = pm_canon(yT, cs.c[h][1], cs.hi[h][1], cs.lo[h][1]);
-            const float fz = pm_canon(zT, cs.c[h][2], cs.hi[h][2], cs.lo[h][2]);
-            Cell cf, cm;
-            const int reg = pm_region(G, fx, fy, fz, cf, cm);
-            const Cell cc = pm_cells(G.coarse, sx, sy, sz);
-            if (!cc.ok) continue;  // only after positions changed without a deposit
-            T dx, dy, dz;
-            cell_delta(G.coarse, cc, rsx, rsy, rsz, dx, dy, dz);
-            stencil<T>(G.coarse, static_cast<const T *>(G.phi[4]),
-                       reg == REG_OUTER ? static_cast<const T *>(G.phi[3]) : nullptr, cc, dx, dy, dz, acc, php);
-            if (reg != REG_OUTER) {
-                const T rx = rel_off(xT, cs.c[h][0], cs.hi[h][0], cs.lo[h][0]);
-                const T ry = rel_off(yT, cs.c[h][1], cs.hi[h][1], cs.lo[h][1]);
-                const T rz = rel_off(zT, cs.c[h][2], cs.hi[h][2], cs.lo[h][2]);
-                cell_delta(G.med, cm, rx, ry, rz, dx, dy, dz);
-                stencil<T>(G.med, static_cast<const T *>(G.phi[2]),
-                           reg == REG_SHELL ? static_cast<const T *>(G.phi[1]) : nullptr, cm, dx, dy, dz, acc, php);
-                if (reg == REG_CORE) {
-                    cell_delta(G.fine, cf, rx, ry, rz, dx, dy, dz);
-                    stencil<T>(G.fine, static_cast<const T *>(G.phi[0]), nullptr, cf, dx, dy, dz, acc, php);
-                }
-            }
-        }
-        if (MODE == 0) {
-            const T vx = p.vx[i] + dt * acc[0], vy = p.vy[i] + dt * acc[1], vz = p.vz[i] + dt * acc[2];
-            p.vx[i] = vx; p.vy[i] = vy; p.vz[i] = vz;
-            p.x[i] = xT + dt * vx; p.y[i] = yT + dt * vy; p.z[i] = zT + dt * vz;
-        } else if (MODE == 1) {
-            ax[i] = acc[0]; ay[i] = acc[1]; az[i] = acc[2];
-        } else if (MODE == 2) {
-            p.vx[i] += dt * acc[0]; p.vy[i] += dt * acc[1]; p.vz[i] += dt * acc[2];
-        } else {
-            const double x = (double)xT, y = (double)yT, z = (double)zT;
-            const double hdt = 0.5 * (double)dt;
-            const double vx = (double)p.vx[i] + hdt * (double)acc[0];
-            const double vy = (double)p.vy[i] + hdt * (double)acc[1];
-            const double vz = (double)p.vz[i] + hdt * (double)acc[2];
-            const double m = (double)p.m[i];
-            dsum[0] += 0.5 * m * (vx * vx + vy * vy + vz * vz);
-            dsum[1] += -0.5 * m * (double)phiv;
-            dsum[3] += m * (y * vz - z * vy);
-            dsum[4] += m * (z * vx - x * vz);
-            dsum[5] += m * (x * vy - y * vx);
-            dsum[6] += 1.0;
-        }
-    }
-    if (MODE == 3) {
-        dsum[2] = dsum[0] + dsum[1];
-        __shared__ double red[8][7];
-        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-        for (int k = 0; k < 7; ++k) {
-            const double v = warp_sum(dsum[k]);
-            if (lane == 0) red[w][k] = v;
-        }
-        __syncthreads();
-        if (threadIdx.x < 7) {
-            double v = 0;
-            for (int k = 0; k < (int)(blockDim.x >> 5); ++k) v += red[k][threadIdx.x];
-            atomicAdd(diag + threadIdx.x, v);
-        }
-    }
-}
-
 __device__ __forceinline__ long long warp_sum_ll(long long v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     return v;
 }
 
-// Step a1: exact integer centre-of-mass sums within R_core of each galaxy's
-// current centre: sum M, sum M*D (M = q >> 26, D = rint(d * 2^sD)).  Warp
-// sums go to shared memory, each block writes its partials to
-// part[block][galaxy][4]; the last block to finish (ticket counter after a
-// memory fence, no waiting) adds all partials -- integer sums, so the order
-// does not matter -- and moves the centres: c += (sum M D / sum M) 2^-sD.
-constexpr int RECENTRE_MAX_BLOCKS = 608;
-
+// ---------------------------------------------------------------------------
+// Step a1 (recentring).  The centre of mass of each recentring galaxy's live
+// particles within R_core of its centre c is accumulated exactly in integers:
+// sum M and sum M*D with M = q >> 26 and D = rint(d 2^sD) (|D| < 2^24); then
+// c' = c + (sum M D / sum M) 2^-sD.  Warp sums go to shared memory, each
+// block adds its sums into one of COM_SLOTS accumulator rows, and a one-block
+// kernel adds the rows and moves the centres.
+// ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256) k_recentre(PartK<T> p, const SysK *sk, CenK *cen, long long *part,
-                                                  unsigned *ticket) {
-    __shared__ SysK s;
-    __shared__ CenK cs;
-    __shared__ unsigned long long red[PM_MAX_GALAXIES][4];
-    __shared__ long long red2[8][PM_MAX_GALAXIES * 4];
-    __shared__ bool last;
-    if (threadIdx.x < PM_MAX_GALAXIES * 4) (&red[0][0])[threadIdx.x] = 0;
-    stage_sys(s, sk, cs, cen);
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long b = (long long)blockIdx.x * blockDim.x; b < p.n; b += stride) {
-        const long long i = b + threadIdx.x;
-        uint32_t f = PM_FLAG_LOST;
-        int g = -1;
-        T x = 0, y = 0, z = 0, m = 0;
-        if (i < p.n) {  // all loads issued together
-            f = p.flags[i]; g = p.gal[i];
-            x = p.x[i]; y = p.y[i]; z = p.z[i]; m = p.m[i];
-        }
-        long long M = 0, Dx = 0, Dy = 0, Dz = 0;
-        if ((f & PM_FLAG_LOST) || g < 0 || g >= s.ngal || !s.gal[g].recentre) {
-            g = -1;
-        } else {
-            const float dx = pm_canon(x, cs.c[g][0], cs.hi[g][0], cs.lo[g][0]);
-            const float dy = pm_canon(y, cs.c[g][1], cs.hi[g][1], cs.lo[g][1]);
-            const float dz = pm_canon(z, cs.c[g][2], cs.hi[g][2], cs.lo[g][2]);
-            if (pm_r2(dx, dy, dz) < s.gal[g].rc2) {
-                M = pm_qmass(m, s.mscale, s.mscale_f) >> 26;
-                const float sc = __int_as_float((127 + s.gal[g].sD) << 23);  // 2^sD
-                Dx = __float2ll_rn(__fmul_rn(dx, sc));
-                Dy = __float2ll_rn(__fmul_rn(dy, sc));
-                Dz = __float2ll_rn(__fmul_rn(dz, sc));
-            } else {
-                g = -1;
-            }
-        }
-        for (int h = 0; h < s.ngal; ++h) {
-            if (!__any_sync(0xffffffffu, g == h)) continue;
-            const bool mine = (g == h);
-            const long long v0 = warp_sum_ll(mine ? M : 0);
-            const long long v1 = warp_sum_ll(mine ? M * Dx : 0);
-            const long long v2 = warp_sum_ll(mine ? M * Dy : 0);
-            const long long v3 = warp_sum_ll(mine ? M * Dz : 0);
-            if ((threadIdx.x & 31) == 0) {
-                atomicAdd(&red[h][0], (unsigned long long)v0);
-                atomicAdd(&red[h][1], (unsigned long long)v1);
-                atomicAdd(&red[h][2], (unsigned long long)v2);
-                atomicAdd(&red[h][3], (unsigned long long)v3);
-            }
+__device__ __forceinline__ int com_contrib(const SysK &s, const CenK *cen, int g, T x, T y, T z, T m,
+                                           long long &M, int &Dx, int &Dy, int &Dz) {
+    if (g < 0 || g >= s.ngal || !s.gal[g].recentre) return -1;
+    const Cen1 ce = load_cen(cen, g);
+    const float dx = pm_canon(x, ce.c[0], ce.hi[0], ce.lo[0]);
+    const float dy = pm_canon(y, ce.c[1], ce.hi[1], ce.lo[1]);
+    const float dz = pm_canon(z, ce.c[2], ce.hi[2], ce.lo[2]);
+    if (!(pm_r2(dx, dy, dz) < s.gal[g].rc2)) return -1;
+    M = pm_qmass(m, s.mscale, s.mscale_f) >> 26;
+    const float sc = __int_as_float((127 + s.gal[g].sD) << 23);  // 2^sD
+    Dx = __float2int_rn(__fmul_rn(dx, sc));
+    Dy = __float2int_rn(__fmul_rn(dy, sc));
+    Dz = __float2int_rn(__fmul_rn(dz, sc));
+    return g;
+}
+
+// Warp-collective: every lane of the warp calls it (g = -1: no contribution).
+__device__ __forceinline__ void com_warp_add(const SysK &s, unsigned long long (*red)[4], int g, long long M,
+                                             int Dx, int Dy, int Dz) {
+    for (int h = 0; h < s.ngal; ++h) {
+        if (!__any_sync(0xffffffffu, g == h)) continue;
+        const bool mine = (g == h);
+        const long long v0 = warp_sum_ll(mine ? M : 0);
+        const long long v1 = warp_sum_ll(mine ? M * Dx : 0);
+        const long long v2 = warp_sum_ll(mine ? M * Dy : 0);
+        const long long v3 = warp_sum_ll(mine ? M * Dz : 0);
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(&red[h][0], (unsigned long long)v0);
+            atomicAdd(&red[h][1], (unsigned long long)v1);
+            atomicAdd(&red[h][2], (unsigned long long)v2);
+            atomicAdd(&red[h][3], (unsigned long long)v3);
         }
     }
+}
+
+// Block epilogue: the block's sums are added (integer atomics, any order)
+// into one of COM_SLOTS accumulator rows, part[blockIdx % COM_SLOTS][galaxy][4],
+// so no address sees more than a few dozen atomics.
+constexpr int COM_SLOTS = 64;
+__device__ __forceinline__ void com_write_partials(const SysK &s, unsigned long long (*red)[4], long long *part) {
     __syncthreads();
-    if (threadIdx.x < PM_MAX_GALAXIES * 4)
-        part[(long long)blockIdx.x * PM_MAX_GALAXIES * 4 + threadIdx.x] = (long long)(&red[0][0])[threadIdx.x];
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
+    if (threadIdx.x < s.ngal * 4) {
+        const unsigned long long v = (&red[0][0])[threadIdx.x];
+        if (v) atomicAdd(reinterpret_cast<unsigned long long *>(part) + (blockIdx.x % COM_SLOTS) * PM_MAX_GALAXIES * 4 +
+                             threadIdx.x, v);
+    }
+}
+
+// One block of 256 threads: adds the COM_SLOTS accumulator rows, clears them
+// for the next use, and moves the centres: c += (sum M D / sum M) 2^-sD.
+static __global__ void __launch_bounds__(256) k_com_apply(const __grid_constant__ SysK s, long long *part,
+                                                          CenK *cen) {
+    constexpr int NV = COM_SLOTS * PM_MAX_GALAXIES * 4;  // 2048 values, value index = slot * 32 + v
+    __shared__ long long red2[8][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int v = 0; v < s.ngal * 4; ++v) {
-        long long acc = 0;
-        for (int q = threadIdx.x; q < (int)gridDim.x; q += blockDim.x)
-            acc += __ldcg(part + (long long)q * PM_MAX_GALAXIES * 4 + v);
-        acc = warp_sum_ll(acc);
-        if (lane == 0) red2[w][v] = acc;
+    long long acc = 0;
+#pragma unroll
+    for (int k = 0; k < NV / 256; ++k) {
+        long long *q = part + threadIdx.x + 256 * k;   // v = threadIdx.x % 32 for every k
+        acc += *q;
+        *q = 0;
     }
+    red2[w][lane] = acc;
     __syncthreads();
     const int g = threadIdx.x;
-    if (g == 0) *ticket = 0;
-    if (g >= s.ngal) return;
+    if (g >= s.ngal || !s.gal[g].recentre) return;
     long long S[4];
     for (int k = 0; k < 4; ++k) {
         S[k] = 0;
-        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) S[k] += red2[q][4 * g + k];
+        for (int q = 0; q < 8; ++q) S[k] += red2[q][4 * g + k];
     }
-    if (s.gal[g].recentre && S[0] > 0) {
-        const double sc = ldexp(1.0, -s.gal[g].sD);
-        for (int k = 0; k < 3; ++k) {
-            const double c = __dadd_rn(cs.c[g][k], __dmul_rn(__ddiv_rn(__ll2double_rn(S[1 + k]), __ll2double_rn(S[0])), sc));
-            const float hi = __double2float_rn(c);
-            cen->c[g][k] = c;
-            cen->hi[g][k] = hi;
-            cen->lo[g][k] = __double2float_rn(__dsub_rn(c, (double)hi));
+    if (S[0] <= 0) return;
+    const double sc = ldexp(1.0, -s.gal[g].sD);
+    for (int k = 0; k < 3; ++k) {
+        const double c =
+            __dadd_rn(cen->c[g][k], __dmul_rn(__ddiv_rn(__ll2double_rn(S[1 + k]), __ll2double_rn(S[0])), sc));
+        const float hi = __double2float_rn(c);
+        cen->c[g][k] = c;
+        cen->hi[g][k] = hi;
+        cen->lo[g][k] = __double2float_rn(__dsub_rn(c, (double)hi));
+    }
+}
+
+// Step a1: centre-of-mass sums of the current positions, then k_com_apply.
+template <typename T>
+__global__ void __launch_bounds__(256) k_recentre(PartK<T> p, const __grid_constant__ SysK s, CenK *cen,
+                                                  long long *part) {
+    __shared__ unsigned long long red[PM_MAX_GALAXIES][4];
+    if (threadIdx.x < PM_MAX_GALAXIES * 4) (&red[0][0])[threadIdx.x] = 0;
+    __syncthreads();
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long b = (long long)blockIdx.x * blockDim.x; b < p.n; b += stride) {
+        const long long i = b + threadIdx.x;
+        int g = -1, Dx = 0, Dy = 0, Dz = 0;
+        long long M = 0;
+        if (i < p.n) {
+            const uint32_t f = p.flags[i];
+            const int gi = p.gal[i];
+            const T x = p.x[i], y = p.y[i], z = p.z[i], m = p.m[i];
+            if (!(f & PM_FLAG_LOST)) g = com_contrib(s, cen, gi, x, y, z, m, M, Dx, Dy, Dz);
+        }
+        com_warp_add(s, red, g, M, Dx, Dy, Dz);
+    }
+    com_write_partials(s, red, part);
+}
+
+// Step a8 (+a9): acceleration by Eq. (eqn:diff) on the grids the combination
+// rule selects for each galaxy (Sec. 2.1), then
+//   MODE 0: leap-frog kick-drift   MODE 1: write acceleration
+//   MODE 2: kick only              MODE 3: energy / angular momentum sums
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256, 3) k_force(PartK<T> p, const __grid_constant__ SysK s, const CenK *cen,
+                                                  T dt, T *ax, T *ay, T *az, double *diag) {
+    double dsum[7] = {0, 0, 0, 0, 0, 0, 0};
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long b = (long long)blockIdx.x * blockDim.x; b < p.n; b += stride) {
+        const long long i = b + threadIdx.x;
+        if (i < p.n) {
+            if (p.flags[i] & PM_FLAG_LOST) {
+                if (MODE == 1) { ax[i] = 0; ay[i] = 0; az[i] = 0; }
+            } else {
+                const T xT = p.x[i], yT = p.y[i], zT = p.z[i];
+                const float sx = pm_canon(xT, s.sc[0], s.sc_hi[0], s.sc_lo[0]);
+                const float sy = pm_canon(yT, s.sc[1], s.sc_hi[1], s.sc_lo[1]);
+                const float sz = pm_canon(zT, s.sc[2], s.sc_hi[2], s.sc_lo[2]);
+                const T rsx = rel_off(xT, s.sc[0], s.sc_hi[0], s.sc_lo[0]);
+                const T rsy = rel_off(yT, s.sc[1], s.sc_hi[1], s.sc_lo[1]);
+                const T rsz = rel_off(zT, s.sc[2], s.sc_hi[2], s.sc_lo[2]);
+                T acc[3] = {0, 0, 0};
+                T phiv = 0;
+                T *php = (MODE == 3) ? &phiv : nullptr;
+                for (int h = 0; h < s.ngal; ++h) {
+                    const GalK &G = s.gal[h];
+                    const Cen1 ce = load_cen(cen, h);
+                    const float fx = pm_canon(xT, ce.c[0], ce.hi[0], ce.lo[0]);
+                    const float fy = pm_canon(yT, ce.c[1], ce.hi[1], ce.lo[1]);
+                    const float fz = pm_canon(zT, ce.c[2], ce.hi[2], ce.lo[2]);
+                    Cell cf, cm;
+                    const int reg = pm_region(G, fx, fy, fz, cf, cm);
+                    const Cell cc = pm_cells(G.coarse, sx, sy, sz);
+                    if (!cc.ok) continue;  // only after positions changed without a deposit
+                    T dx, dy, dz;
+                    cell_delta(G.coarse, cc, rsx, rsy, rsz, dx, dy, dz);
+                    stencil<T>(G.coarse, static_cast<const T *>(G.phi[4]),
+                               reg == REG_OUTER ? static_cast<const T *>(G.phi[3]) : nullptr, cc, dx, dy, dz, acc, php);
+                    if (reg != REG_OUTER) {
+                        const T rx = rel_off(xT, ce.c[0], ce.hi[0], ce.lo[0]);
+                        const T ry = rel_off(yT, ce.c[1], ce.hi[1], ce.lo[1]);
+                        const T rz = rel_off(zT, ce.c[2], ce.hi[2], ce.lo[2]);
+                        cell_delta(G.med, cm, rx, ry, rz, dx, dy, dz);
+                        stencil<T>(G.med, static_cast<const T *>(G.phi[2]),
+                                   reg == REG_SHELL ? static_cast<const T *>(G.phi[1]) : nullptr, cm, dx, dy, dz, acc, php);
+                        if (reg == REG_CORE) {
+                            cell_delta(G.fine, cf, rx, ry, rz, dx, dy, dz);
+                            stencil<T>(G.fine, static_cast<const T *>(G.phi[0]), nullptr, cf, dx, dy, dz, acc, php);
+                        }
+                    }
+                }
+                if (MODE == 0) {
+                    const T vx = p.vx[i] + dt * acc[0], vy = p.vy[i] + dt * acc[1], vz = p.vz[i] + dt * acc[2];
+                    p.vx[i] = vx; p.vy[i] = vy; p.vz[i] = vz;
+                    p.x[i] = xT + dt * vx; p.y[i] = yT + dt * vy; p.z[i] = zT + dt * vz;
+                } else if (MODE == 1) {
+                    ax[i] = acc[0]; ay[i] = acc[1]; az[i] = acc[2];
+                } else if (MODE == 2) {
+                    p.vx[i] += dt * acc[0]; p.vy[i] += dt * acc[1]; p.vz[i] += dt * acc[2];
+                } else {
+                    const double x = (double)xT, y = (double)yT, z = (double)zT;
+                    const double hdt = 0.5 * (double)dt;
+                    const double vx = (double)p.vx[i] + hdt * (double)acc[0];
+                    const double vy = (double)p.vy[i] + hdt * (double)acc[1];
+                    const double vz = (double)p.vz[i] + hdt * (double)acc[2];
+                    const double m = (double)p.m[i];
+                    dsum[0] += 0.5 * m * (vx * vx + vy * vy + vz * vz);
+                    dsum[1] += -0.5 * m * (double)phiv;
+                    dsum[3] += m * (y * vz - z * vy);
+                    dsum[4] += m * (z * vx - x * vz);
+                    dsum[5] += m * (x * vy - y * vx);
+                    dsum[6] += 1.0;
+                }
+            }
+        }
+    }
+    if (MODE == 3) {
+        dsum[2] = dsum[0] + dsum[1];
+        __shared__ double dred[8][7];
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+        for (int k = 0; k < 7; ++k) {
+            const double v = warp_sum(dsum[k]);
+            if (lane == 0) dred[w][k] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < 7) {
+            double v = 0;
+            for (int k = 0; k < (int)(blockDim.x >> 5); ++k) v += dred[k][threadIdx.x];
+            atomicAdd(diag + threadIdx.x, v);
         }
     }
 }
@@ -612,51 +636,47 @@ __global__ void __launch_bounds__(256) k_recentre(PartK<T> p, const SysK *sk, Ce
 // share addresses.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256) k_sort_key(PartK<T> p, const SysK *sk, const CenK *cen, SortK so,
-                                                  unsigned *count, unsigned *key, unsigned *rank) {
-    __shared__ SysK s;
-    __shared__ CenK cs;
-    stage_sys(s, sk, cs, cen);
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += stride) {
-        unsigned k = (unsigned)(so.nkeys - 1);  // lost
-        const int g = p.gal[i];
-        if (!(p.flags[i] & PM_FLAG_LOST) && g >= 0 && g < s.ngal) {
-            const T x = p.x[i], y = p.y[i], z = p.z[i];
-            const GalK &G = s.gal[g];
-            const float fx = pm_canon(x, cs.c[g][0], cs.hi[g][0], cs.lo[g][0]);
-            const float fy = pm_canon(y, cs.c[g][1], cs.hi[g][1], cs.lo[g][1]);
-            const float fz = pm_canon(z, cs.c[g][2], cs.hi[g][2], cs.lo[g][2]);
-            Cell cf, cm;
-            const int reg = pm_region(G, fx, fy, fz, cf, cm);
-            const GeomK *gm;
-            Cell c;
-            if (reg == REG_CORE) { gm = &G.fine; c = cf; }
-            else if (reg == REG_SHELL) { gm = &G.med; c = cm; }
-            else {
-                gm = &G.coarse;
-                c = pm_cells(G.coarse, pm_canon(x, s.sc[0], s.sc_hi[0], s.sc_lo[0]),
-                             pm_canon(y, s.sc[1], s.sc_hi[1], s.sc_lo[1]), pm_canon(z, s.sc[2], s.sc_hi[2], s.sc_lo[2]));
-            }
-            if (c.ok) {
-                const int b = so.shift[g][reg];
-                const long long bin = ((long long)(c.k >> b) * (gm->ny >> b) + (c.j >> b)) * (gm->nx >> b) + (c.i >> b);
-                k = (unsigned)(so.base[g][reg] + bin);
-            }
+__global__ void __launch_bounds__(256) k_sort_key(PartK<T> p, const __grid_constant__ SysK s, const CenK *cen,
+                                                  SortK so, unsigned *count, unsigned *key, unsigned *rank) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= p.n) return;
+    unsigned k = (unsigned)(so.nkeys - 1);  // lost
+    const int g = p.gal[i];
+    if (!(p.flags[i] & PM_FLAG_LOST) && g >= 0 && g < s.ngal) {
+        const T x = p.x[i], y = p.y[i], z = p.z[i];
+        const GalK &G = s.gal[g];
+        const Cen1 ce = load_cen(cen, g);
+        const float fx = pm_canon(x, ce.c[0], ce.hi[0], ce.lo[0]);
+        const float fy = pm_canon(y, ce.c[1], ce.hi[1], ce.lo[1]);
+        const float fz = pm_canon(z, ce.c[2], ce.hi[2], ce.lo[2]);
+        Cell cf, cm;
+        const int reg = pm_region(G, fx, fy, fz, cf, cm);
+        const GeomK *gm;
+        Cell c;
+        if (reg == REG_CORE) { gm = &G.fine; c = cf; }
+        else if (reg == REG_SHELL) { gm = &G.med; c = cm; }
+        else {
+            gm = &G.coarse;
+            c = pm_cells(G.coarse, pm_canon(x, s.sc[0], s.sc_hi[0], s.sc_lo[0]),
+                         pm_canon(y, s.sc[1], s.sc_hi[1], s.sc_lo[1]), pm_canon(z, s.sc[2], s.sc_hi[2], s.sc_lo[2]));
         }
-        key[i] = k;
-        // warp-aggregated ranking: lanes with the same key take consecutive
-        // ranks from one atomic (the lanes of a warp run this loop together
-        // only while i < n, so use the lanes that are here)
-        const unsigned act = __activemask();
-        const unsigned peers = __match_any_sync(act, k);
-        const int lane = threadIdx.x & 31;
-        const int leader = __ffs(peers) - 1;
-        unsigned base = 0;
-        if (lane == leader) base = atomicAdd(count + k, (unsigned)__popc(peers));
-        base = __shfl_sync(peers, base, leader);
-        rank[i] = base + __popc(peers & ((1u << lane) - 1u));
+        if (c.ok) {
+            const int b = so.shift[g][reg];
+            const long long bin = ((long long)(c.k >> b) * (gm->ny >> b) + (c.j >> b)) * (gm->nx >> b) + (c.i >> b);
+            k = (unsigned)(so.base[g][reg] + bin);
+        }
     }
+    key[i] = k;
+    // warp-aggregated ranking: lanes with the same key take consecutive ranks
+    // from one atomic (lanes past the end have returned: use the lanes here)
+    const unsigned act = __activemask();
+    const unsigned peers = __match_any_sync(act, k);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(peers) - 1;
+    unsigned base = 0;
+    if (lane == leader) base = atomicAdd(count + k, (unsigned)__popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    rank[i] = base + __popc(peers & ((1u << lane) - 1u));
 }
 
 constexpr int SCAN_TILE = 2048;  // 256 threads x 8
@@ -717,27 +737,44 @@ static __global__ void __launch_bounds__(1024) k_scan_top(unsigned *bsum, int nb
         }
 }
 
+// The count array is allocated with a multiple of SCAN_TILE elements, so a
+// thread's eight values are two aligned uint4.
 static __global__ void __launch_bounds__(256) k_scan_down(unsigned *a, long long n, const unsigned *bsum) {
     __shared__ unsigned tmp[32];
     const long long t0 = (long long)blockIdx.x * SCAN_TILE + (long long)threadIdx.x * (SCAN_TILE / 256);
-    unsigned v[SCAN_TILE / 256];
+    uint4 *a4 = reinterpret_cast<uint4 *>(a + t0);
+    uint4 u0 = a4[0], u1 = a4[1];
+    unsigned v[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
     unsigned sum = 0;
 #pragma unroll
-    for (int k = 0; k < SCAN_TILE / 256; ++k) {
-        v[k] = (t0 + k < n) ? a[t0 + k] : 0u;
+    for (int k = 0; k < 8; ++k) {
+        if (t0 + k >= n) v[k] = 0u;
         sum += v[k];
     }
     unsigned total;
     unsigned run = block_excl_scan(sum, tmp, total) + bsum[blockIdx.x];
+    unsigned o[8];
 #pragma unroll
-    for (int k = 0; k < SCAN_TILE / 256; ++k) {
-        if (t0 + k < n) a[t0 + k] = run;
-        run += v[k];
-    }
+    for (int k = 0; k < 8; ++k) { o[k] = run; run += v[k]; }
+    a4[0] = make_uint4(o[0], o[1], o[2], o[3]);
+    a4[1] = make_uint4(o[4], o[5], o[6], o[7]);
 }
 
 // One particle per thread (full grid): every load is issued before the
 // destination is known, so a warp keeps all its reads in flight.
+// Copies the nine particle arrays (7 of T, 2 of 32-bit ints) from src to
+// dst, n elements each.
+template <typename T>
+__global__ void __launch_bounds__(256) k_copy_particles(PartK<T> src, PartK<T> dst) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= src.n) return;
+    dst.x[i] = src.x[i]; dst.y[i] = src.y[i]; dst.z[i] = src.z[i];
+    dst.vx[i] = src.vx[i]; dst.vy[i] = src.vy[i]; dst.vz[i] = src.vz[i];
+    const_cast<T *>(dst.m)[i] = src.m[i];
+    const_cast<int32_t *>(dst.gal)[i] = src.gal[i];
+    dst.flags[i] = src.flags[i];
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_sort_scatter(PartK<T> p, PartK<T> d, const unsigned *key, const unsigned *rank,
                                                       const unsigned *off, long long *perm) {
@@ -780,9 +817,11 @@ __global__ void k_store_hhat(const double *in, T *out, long long n, double scale
 // ---------------------------------------------------------------------------
 namespace pmk_host {
 
+// One particle per thread up to 2^16 blocks (16.7M particles); larger sets
+// loop (grid-stride).
 inline int particle_grid(long long n) {
     long long b = (n + 255) / 256;
-    const long long cap = 152LL * 8;
+    const long long cap = 1LL << 16;
     return (int)(b < cap ? (b > 0 ? b : 1) : cap);
 }
 
@@ -859,14 +898,14 @@ template <typename T> cudaError_t pm_launch_col(const FftArgs &a, int mode, int 
 }
 
 template <typename T>
-cudaError_t pm_launch_deposit(const PartK<T> &p, const SysK *sk, const CenK *cen, int aggregate, cudaStream_t st) {
+cudaError_t pm_launch_deposit(const PartK<T> &p, const SysK &sk, const CenK *cen, int aggregate, cudaStream_t st) {
     if (p.n <= 0) return cudaSuccess;
     pmk::k_deposit<T><<<pmk_host::particle_grid(p.n), 256, 0, st>>>(p, sk, cen, aggregate);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t pm_launch_force(int mode, const PartK<T> &p, const SysK *sk, const CenK *cen, double dt,
+cudaError_t pm_launch_force(int mode, const PartK<T> &p, const SysK &sk, const CenK *cen, double dt,
                             T *ax, T *ay, T *az, double *diag, cudaStream_t st) {
     if (p.n <= 0) return cudaSuccess;
     const int g = pmk_host::particle_grid(p.n);
@@ -881,39 +920,32 @@ cudaError_t pm_launch_force(int mode, const PartK<T> &p, const SysK *sk, const C
 }
 
 template <typename T>
-cudaError_t pm_launch_recentre(const PartK<T> &p, const SysK *sk, CenK *cen, long long *part,
-                               unsigned *ticket, cudaStream_t st) {
+cudaError_t pm_launch_recentre(const PartK<T> &p, const SysK &sk, CenK *cen, long long *part, cudaStream_t st) {
     if (p.n <= 0) return cudaSuccess;
-    long long nb = (p.n + 255) / 256;
-    if (nb > pmk::RECENTRE_MAX_BLOCKS) nb = pmk::RECENTRE_MAX_BLOCKS;
-    pmk::k_recentre<T><<<(int)nb, 256, 0, st>>>(p, sk, cen, part, ticket);
+    pmk::k_recentre<T><<<pmk_host::particle_grid(p.n), 256, 0, st>>>(p, sk, cen, part);
+    pmk::k_com_apply<<<1, 256, 0, st>>>(sk, part, cen);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t pm_launch_sort(const PartK<T> &p, const PartK<T> &scratch, const SysK *sk, const CenK *cen,
+cudaError_t pm_launch_sort(const PartK<T> &p, const PartK<T> &scratch, const SysK &sk, const CenK *cen,
                            const SortK &so, unsigned *count, unsigned *key, unsigned *rank, unsigned *bsum,
                            long long *perm, cudaStream_t st) {
     if (p.n <= 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(count, 0, (size_t)so.nkeys * sizeof(unsigned), st);
     if (e) return e;
-    const int g = pmk_host::particle_grid(p.n);
+    const unsigned g = (unsigned)((p.n + 255) / 256);
     pmk::k_sort_key<T><<<g, 256, 0, st>>>(p, sk, cen, so, count, key, rank);
     const int nb = (int)((so.nkeys + pmk::SCAN_TILE - 1) / pmk::SCAN_TILE);
     pmk::k_scan_reduce<<<nb, 256, 0, st>>>(count, so.nkeys, bsum);
     pmk::k_scan_top<<<1, 1024, 0, st>>>(bsum, nb);
     pmk::k_scan_down<<<nb, 256, 0, st>>>(count, so.nkeys, bsum);
-    pmk::k_sort_scatter<T><<<(unsigned)((p.n + 255) / 256), 256, 0, st>>>(p, scratch, key, rank, count, perm);
+    pmk::k_sort_scatter<T><<<g, 256, 0, st>>>(p, scratch, key, rank, count, perm);
     if ((e = cudaGetLastError())) return e;
-    const size_t b = (size_t)p.n * sizeof(T);
-    void *const src[9] = {scratch.x, scratch.y, scratch.z, scratch.vx, scratch.vy, scratch.vz,
-                          (void *)scratch.m, (void *)scratch.gal, scratch.flags};
-    void *const dst[9] = {p.x, p.y, p.z, p.vx, p.vy, p.vz, (void *)p.m, (void *)p.gal, p.flags};
-    for (int k = 0; k < 9; ++k) {
-        const size_t bytes = k < 7 ? b : (size_t)p.n * 4;
-        if ((e = cudaMemcpyAsync(dst[k], src[k], bytes, cudaMemcpyDeviceToDevice, st))) return e;
-    }
-    return cudaSuccess;
+    PartK<T> sc = scratch;
+    sc.n = p.n;
+    pmk::k_copy_particles<T><<<g, 256, 0, st>>>(sc, p);
+    return cudaGetLastError();
 }
 
 template <typename T>
@@ -934,13 +966,13 @@ cudaError_t pm_store_hhat(const double *in, T *out, long long n, double scale, c
     template cudaError_t pm_launch_xfwd<T>(const FftArgs &, int, cudaStream_t);                               \
     template cudaError_t pm_launch_xinv<T>(const FftArgs &, int, cudaStream_t);                               \
     template cudaError_t pm_launch_col<T>(const FftArgs &, int, int, cudaStream_t);                           \
-    template cudaError_t pm_launch_deposit<T>(const PartK<T> &, const SysK *, const CenK *, int, cudaStream_t); \
-    template cudaError_t pm_launch_force<T>(int, const PartK<T> &, const SysK *, const CenK *, double, T *,   \
-                                            T *, T *, double *, cudaStream_t);                                 \
-    template cudaError_t pm_launch_recentre<T>(const PartK<T> &, const SysK *, CenK *, long long *,            \
-                                               unsigned *, cudaStream_t);                                      \
+    template cudaError_t pm_launch_deposit<T>(const PartK<T> &, const SysK &, const CenK *, int, cudaStream_t); \
+    template cudaError_t pm_launch_force<T>(int, const PartK<T> &, const SysK &, const CenK *, double, T *, T *, \
+                                            T *, double *, cudaStream_t);                                      \
+    template cudaError_t pm_launch_recentre<T>(const PartK<T> &, const SysK &, CenK *, long long *,            \
+                                               cudaStream_t);                                                  \
     template cudaError_t pm_launch_count_lost<T>(const PartK<T> &, unsigned long long *, cudaStream_t);       \
-    template cudaError_t pm_launch_sort<T>(const PartK<T> &, const PartK<T> &, const SysK *, const CenK *,     \
+    template cudaError_t pm_launch_sort<T>(const PartK<T> &, const PartK<T> &, const SysK &, const CenK *,     \
                                            const SortK &, unsigned *, unsigned *, unsigned *, unsigned *,       \
                                            long long *, cudaStream_t);                                          \
     template cudaError_t pm_store_hhat<T>(const double *, T *, long long, double, cudaStream_t);

@@ -27,19 +27,19 @@ template <typename T> cudaError_t pm_launch_col(const FftArgs &a, int mode, int 
 template <typename T> cudaError_t pm_launch_xinv(const FftArgs &a, int nsets, cudaStream_t st);
 
 template <typename T>
-cudaError_t pm_launch_deposit(const PartK<T> &p, const SysK *sk, const CenK *cen, int aggregate, cudaStream_t st);
+cudaError_t pm_launch_deposit(const PartK<T> &p, const SysK &sk, const CenK *cen, int aggregate, cudaStream_t st);
 // mode: 0 kick-drift, 1 write accelerations, 2 kick only, 3 diagnostics
 template <typename T>
-cudaError_t pm_launch_force(int mode, const PartK<T> &p, const SysK *sk, const CenK *cen, double dt,
+cudaError_t pm_launch_force(int mode, const PartK<T> &p, const SysK &sk, const CenK *cen, double dt,
                             T *ax, T *ay, T *az, double *diag, cudaStream_t st);
+// Recentring from the current positions (part: zeroed accumulators).
 template <typename T>
-cudaError_t pm_launch_recentre(const PartK<T> &p, const SysK *sk, CenK *cen, long long *part,
-                               unsigned *ticket, cudaStream_t st);
+cudaError_t pm_launch_recentre(const PartK<T> &p, const SysK &sk, CenK *cen, long long *part, cudaStream_t st);
 template <typename T>
 cudaError_t pm_launch_count_lost(const PartK<T> &p, unsigned long long *out, cudaStream_t st);
 // Counting sort by spatial key; permutes p's arrays in place through scratch.
 template <typename T>
-cudaError_t pm_launch_sort(const PartK<T> &p, const PartK<T> &scratch, const SysK *sk, const CenK *cen,
+cudaError_t pm_launch_sort(const PartK<T> &p, const PartK<T> &scratch, const SysK &sk, const CenK *cen,
                            const SortK &so, unsigned *count, unsigned *key, unsigned *rank, unsigned *bsum,
                            long long *perm, cudaStream_t st);
 
