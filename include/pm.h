@@ -39,6 +39,8 @@ extern "C" {
 #define PM_E_OVERFLOW  -4   /* mass bound leaves no fixed-point headroom    */
 #define PM_E_CUDA      -5   /* a CUDA runtime call failed                   */
 #define PM_E_STATE     -6   /* call not valid in the context's state        */
+#define PM_E_TIMEOUT   -7   /* a kernel's bounded wait for a tensor copy expired
+                               (reported by the next synchronising call)     */
 
 #define PM_FP32 1
 #define PM_FP64 2
@@ -154,7 +156,10 @@ int pm_step(pm_ctx *ctx, const pm_particles *p, double dt, int32_t nsteps);
  * out[6] = number of live particles.  FP64 sums.  Synchronises. */
 int pm_diagnostics(pm_ctx *ctx, const pm_particles *p, double dt, double *out);
 
-/* Test and inspection hooks (synchronise).  set = 1..5 as in the paper. */
+/* Test and inspection hooks (synchronise).  set = 1..5 as in the paper.
+ * pm_get_potential returns the potentials as the force stencils combine
+ * them: set 1 Phi_1, set 2 Phi_2 + Phi_3, set 3 Phi_3, set 4 Phi_4 + Phi_5,
+ * set 5 Phi_5. */
 int pm_get_density(pm_ctx *ctx, int32_t gal, int32_t set, int64_t *host_out);
 int pm_get_potential(pm_ctx *ctx, int32_t gal, int32_t set, void *host_out);
 int pm_get_centres(pm_ctx *ctx, double *host_out);          /* ngal*3 */

@@ -14,6 +14,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -101,11 +102,20 @@ CenK make_cenk(const double *c, int ngal) {
     return k;
 }
 
+// Two mass sets of one geometry transformed together as rho_a + i rho_b
+// (b < 0: no partner), with their work array and tensor maps.
+struct Pair {
+    int gi, a, b;
+    void *work = nullptr;
+    CUtensorMap yfwd, yinv, zmap;
+};
+
 struct GeoBuf {
     pm_geometry g;
-    long long A, workN, hatN;
+    long long A, workN, hatN;   // workN: complex elements of a pair's work array
     void *hhat = nullptr;
     std::vector<std::pair<int, int>> sets;   // (galaxy, set index 0..4)
+    std::vector<Pair> pairs;
 };
 
 }  // namespace
@@ -121,13 +131,13 @@ struct pm_ctx {
     int set_geo[PM_MAX_GALAXIES][PM_SETS];
     long long *rho[PM_MAX_GALAXIES][PM_SETS];
     void *phi[PM_MAX_GALAXIES][PM_SETS];
-    void *work[PM_MAX_GALAXIES][PM_SETS];
     long long *rho_all = nullptr;
     size_t rho_bytes = 0;
     SysK hs;
     SysK *d_sys = nullptr;
     CenK *d_cen = nullptr;
     long long *d_csum = nullptr;   // centre-of-mass accumulators (zero between uses)
+    int *d_err = nullptr;          // set by a kernel whose bounded wait expired
     double *d_diag = nullptr;
     unsigned long long *d_cnt = nullptr;
     void *d_tw[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -179,6 +189,15 @@ template <typename T> PartK<T> part_k(const pm_particles *p) {
     k.flags = p->flags;
     k.n = p->n;
     return k;
+}
+
+// After a synchronisation: a kernel's bounded wait that expired is reported.
+int check_device_error(pm_ctx *c) {
+    int h = 0;
+    PM_CK(cudaMemcpyAsync(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->user));
+    PM_CK(cudaStreamSynchronize(c->user));
+    if (h) return fail(PM_E_TIMEOUT, "a tensor copy of an FFT pass did not complete within its time limit");
+    return PM_OK;
 }
 
 int check_particles(const pm_particles *p) {
@@ -247,7 +266,7 @@ template <typename T> int upload_twiddles(pm_ctx *c) {
     return PM_OK;
 }
 
-// ---- the passes of pm_solve, one launch per geometry -----------------------
+// ---- the passes of pm_solve --------------------------------------------------
 enum { PASS_XFWD = 0, PASS_YFWD, PASS_ZCONV, PASS_YINV, PASS_XINV, NPASS };
 
 template <typename T> int launch_pass(pm_ctx *c, int pass, cudaStream_t st, int only = -1) {
@@ -255,41 +274,39 @@ template <typename T> int launch_pass(pm_ctx *c, int pass, cudaStream_t st, int 
         if (only >= 0 && gi != only) continue;
         const GeoBuf &gb = c->geos[gi];
         const pm_geometry &g = gb.g;
-        for (size_t b0 = 0; b0 < gb.sets.size(); b0 += PM_MAX_BATCH) {
-            const int nb = (int)std::min<size_t>(PM_MAX_BATCH, gb.sets.size() - b0);
-            FftArgs a;
+        for (const Pair &pr : gb.pairs) {
+            PairArgs a;
             std::memset(&a, 0, sizeof(a));
-            for (int s = 0; s < nb; ++s) {
-                const int gi = gb.sets[b0 + s].first, k = gb.sets[b0 + s].second;
-                a.rho[s] = c->rho[gi][k];
-                a.work[s] = c->work[gi][k];
-                a.phi[s] = c->phi[gi][k];
-            }
+            a.rho_a = c->rho[pr.gi][pr.a];
+            a.rho_b = pr.b >= 0 ? c->rho[pr.gi][pr.b] : nullptr;
+            a.work = pr.work;
+            a.phi_b = pr.b >= 0 ? c->phi[pr.gi][pr.b] : nullptr;
+            a.phi_sum = c->phi[pr.gi][pr.a];
             a.hhat = gb.hhat;
-            a.nx = g.nx; a.ny = g.ny; a.nz = g.nz; a.P = g.nx + 1;
+            a.nx = g.nx; a.ny = g.ny; a.nz = g.nz;
             a.scale = std::ldexp(1.0, -c->shift);
+            a.err = c->d_err;
             cudaError_t e;
             switch (pass) {
                 case PASS_XFWD:
                     a.tw = c->d_tw[tw_index(2 * g.nx)];
-                    a.nitems = (long long)g.ny * g.nz / 2;
-                    e = pm_launch_xfwd<T>(a, nb, st);
+                    e = pm_launch_xfwd<T>(a, st);
                     break;
                 case PASS_YFWD:
-                case PASS_YINV:
                     a.tw = c->d_tw[tw_index(2 * g.ny)];
-                    a.nitems = (long long)g.nz * a.P;
-                    e = pm_launch_col<T>(a, pass == PASS_YFWD ? COL_YFWD : COL_YINV, nb, st);
+                    e = pm_launch_col<T>(a, pr.yfwd, COL_YFWD, st);
                     break;
                 case PASS_ZCONV:
                     a.tw = c->d_tw[tw_index(2 * g.nz)];
-                    a.nitems = (long long)2 * g.ny * a.P;
-                    e = pm_launch_col<T>(a, COL_ZCONV, nb, st);
+                    e = pm_launch_col<T>(a, pr.zmap, COL_ZCONV, st);
+                    break;
+                case PASS_YINV:
+                    a.tw = c->d_tw[tw_index(2 * g.ny)];
+                    e = pm_launch_col<T>(a, pr.yinv, COL_YINV, st);
                     break;
                 default:
                     a.tw = c->d_tw[tw_index(2 * g.nx)];
-                    a.nitems = (long long)g.ny * g.nz / 2;
-                    e = pm_launch_xinv<T>(a, nb, st);
+                    e = pm_launch_xinv<T>(a, st);
                     break;
             }
             if (e != cudaSuccess) return fail(PM_E_CUDA, "FFT pass %d launch failed: %s", pass, cudaGetErrorString(e));
@@ -461,6 +478,58 @@ template <typename T> int force_impl(pm_ctx *c, int mode, const pm_particles *p,
 
 }  // namespace
 
+// ---- tensor maps of the column passes --------------------------------------
+namespace {
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+// 2D map over 8-byte elements: dim0 contiguous, dim1 rows of stride1 bytes.
+int encode2d(CUtensorMap *m, void *base, unsigned long long dim0, unsigned long long dim1,
+             unsigned long long stride1, unsigned box0, unsigned box1) {
+    EncodeTiledFn f = encode_fn();
+    if (!f) return fail(PM_E_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    const cuuint64_t gdim[2] = {dim0, dim1};
+    const cuuint64_t gstr[1] = {stride1};
+    const cuuint32_t box[2] = {box0, box1};
+    const cuuint32_t es[2] = {1, 1};
+    const CUresult r = f(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, base, gdim, gstr, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(PM_E_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return PM_OK;
+}
+}  // namespace
+
+int pm_encode_col_maps(void *work, int nx, int ny, int nz, int esz, CUtensorMap *yfwd, CUtensorMap *yinv,
+                       CUtensorMap *zmap) {
+    const unsigned long long epc = esz == 4 ? 1 : 2;   // 8-byte elements per complex value
+    const unsigned long long nx2 = 2ull * nx, ny2 = 2ull * ny;
+    const unsigned cy = (unsigned)pm_col_cols(2 * ny, esz), cz = (unsigned)pm_col_cols(2 * nz, esz);
+    // y passes: dim0 = kx, dim1 = the (z, y) rows, box = COLS columns x rows
+    PM_TRY(encode2d(yfwd, work, nx2 * epc, ny2 * nz, nx2 * epc * 8, cy * (unsigned)epc, (unsigned)std::min(ny, 256)));
+    PM_TRY(encode2d(yinv, work, nx2 * epc, ny2 * nz, nx2 * epc * 8, cy * (unsigned)epc,
+                    (unsigned)std::min(2 * ny, 256)));
+    // z pass: dim0 = the (ky, kx) columns, dim1 = z
+    PM_TRY(encode2d(zmap, work, nx2 * ny2 * epc, nz, nx2 * ny2 * epc * 8, cz * (unsigned)epc,
+                    (unsigned)std::min(nz, 256)));
+    return PM_OK;
+}
+
 int pm_internal_fail(int code, const char *msg) {
     g_err = msg;
     return code;
@@ -535,7 +604,6 @@ int pm_create_grids(const pm_system *sys, const pm_galaxy *gals, void *stream, p
     std::memset(c->set_geo, -1, sizeof(c->set_geo));
     std::memset(c->rho, 0, sizeof(c->rho));
     std::memset(c->phi, 0, sizeof(c->phi));
-    std::memset(c->work, 0, sizeof(c->work));
     std::memset(&c->gkey, 0, sizeof(c->gkey));
 
     auto cleanup = [&](int rc) { pm_destroy(c); return rc; };
@@ -553,7 +621,7 @@ int pm_create_grids(const pm_system *sys, const pm_galaxy *gals, void *stream, p
             GeoBuf gb;
             gb.g = g;
             gb.A = (long long)g.nx * g.ny * g.nz;
-            gb.workN = (long long)g.nz * 2 * g.ny * (g.nx + 1);
+            gb.workN = (long long)g.nz * 2 * g.ny * 2 * g.nx;
             gb.hatN = (long long)(g.nx + 1) * (g.ny + 1) * (g.nz + 1);
             c->geos.push_back(gb);
             id = (int)c->geos.size() - 1;
@@ -588,9 +656,29 @@ int pm_create_grids(const pm_system *sys, const pm_galaxy *gals, void *stream, p
             c->rho[gi][k] = c->rho_all + off;
             off += (size_t)gb.A;
             if ((rc = dev_alloc(c, &c->phi[gi][k], gb.A * c->esz))) return cleanup(rc);
-            if ((rc = dev_alloc(c, &c->work[gi][k], gb.workN * 2 * c->esz))) return cleanup(rc);
-            if (cudaMemsetAsync(c->work[gi][k], 0, gb.workN * 2 * c->esz, c->user) != cudaSuccess)
+        }
+    // pairs: grid 1 alone, grids 2+3, grids 4+5 (grid 5 alone without grid 4)
+    for (int gi = 0; gi < sys->ngal; ++gi) {
+        auto add_pair = [&](int a, int b) {
+            GeoBuf &gb = c->geos[c->set_geo[gi][a]];
+            Pair pr;
+            pr.gi = gi; pr.a = a; pr.b = b;
+            gb.pairs.push_back(pr);
+        };
+        if (c->set_geo[gi][0] >= 0) add_pair(0, -1);
+        if (c->set_geo[gi][1] >= 0) add_pair(1, 2);
+        if (c->set_geo[gi][3] >= 0) add_pair(3, 4);
+        else add_pair(4, -1);
+    }
+    for (GeoBuf &gb : c->geos)
+        for (Pair &pr : gb.pairs) {
+            const size_t bytes = (size_t)gb.workN * 2 * c->esz;
+            if ((rc = dev_alloc(c, &pr.work, bytes))) return cleanup(rc);
+            if (cudaMemsetAsync(pr.work, 0, bytes, c->user) != cudaSuccess)
                 return cleanup(fail(PM_E_CUDA, "memset failed"));
+            if ((rc = pm_encode_col_maps(pr.work, gb.g.nx, gb.g.ny, gb.g.nz, (int)c->esz, &pr.yfwd, &pr.yinv,
+                                         &pr.zmap)))
+                return cleanup(rc);
         }
     if (cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess)
         return cleanup(fail(PM_E_CUDA, "cudaEventCreate failed"));
@@ -632,10 +720,12 @@ int pm_create_grids(const pm_system *sys, const pm_galaxy *gals, void *stream, p
         K.ro2 = (float)(G.r_out * G.r_out);
         K.recentre = G.recentre ? 1 : 0;
         K.sD = G.r_core > 0 ? 24 - ceil_log2(G.r_core) : 0;
-        for (int k = 0; k < PM_SETS; ++k) {
-            K.rho[k] = (unsigned long long *)c->rho[gi][k];
-            K.phi[k] = c->phi[gi][k];
-        }
+        for (int k = 0; k < PM_SETS; ++k) K.rho[k] = (unsigned long long *)c->rho[gi][k];
+        K.phi_fine = c->phi[gi][0];
+        K.phi_m23 = c->phi[gi][1];
+        K.phi_m3 = c->phi[gi][2];
+        K.phi_call = geom_present(G.medium) ? c->phi[gi][3] : c->phi[gi][4];
+        K.phi_c5 = c->phi[gi][4];
     }
     {   // key layout of the spatial sort
         SortK &so = c->sortk;
@@ -662,6 +752,7 @@ int pm_create_grids(const pm_system *sys, const pm_galaxy *gals, void *stream, p
     // centre-of-mass accumulators: 64 rows x 8 galaxies x 4 sums, kept zero
     // between uses by the kernel that consumes them
     if ((rc = dev_alloc(c, (void **)&c->d_csum, sizeof(long long) * 4 * PM_MAX_GALAXIES * 64))) return cleanup(rc);
+    if ((rc = dev_alloc(c, (void **)&c->d_err, sizeof(int)))) return cleanup(rc);
     if ((rc = dev_alloc(c, (void **)&c->d_diag, sizeof(double) * 8))) return cleanup(rc);
     if ((rc = dev_alloc(c, (void **)&c->d_cnt, sizeof(unsigned long long)))) return cleanup(rc);
     double cen[3 * PM_MAX_GALAXIES] = {0};
@@ -671,6 +762,7 @@ int pm_create_grids(const pm_system *sys, const pm_galaxy *gals, void *stream, p
     if (cudaMemcpyAsync(c->d_sys, &hs, sizeof(SysK), cudaMemcpyHostToDevice, c->user) != cudaSuccess ||
         cudaMemcpyAsync(c->d_cen, &ck, sizeof(CenK), cudaMemcpyHostToDevice, c->user) != cudaSuccess ||
         cudaMemsetAsync(c->d_csum, 0, sizeof(long long) * 4 * PM_MAX_GALAXIES * 64, c->user) != cudaSuccess ||
+        cudaMemsetAsync(c->d_err, 0, sizeof(int), c->user) != cudaSuccess ||
         cudaStreamSynchronize(c->user) != cudaSuccess)
         return cleanup(fail(PM_E_CUDA, "context upload failed: %s", cudaGetErrorString(cudaGetLastError())));
     *out = c;
@@ -772,7 +864,7 @@ int pm_diagnostics(pm_ctx *c, const pm_particles *p, double dt, double *out) {
     PM_CK(cudaMemcpyAsync(h, c->d_diag, sizeof(h), cudaMemcpyDeviceToHost, c->user));
     PM_CK(cudaStreamSynchronize(c->user));
     for (int k = 0; k < 7; ++k) out[k] = h[k];
-    return PM_OK;
+    return check_device_error(c);
 }
 
 int pm_get_density(pm_ctx *c, int32_t gal, int32_t set, int64_t *host_out) {
@@ -782,7 +874,7 @@ int pm_get_density(pm_ctx *c, int32_t gal, int32_t set, int64_t *host_out) {
     const GeoBuf &gb = c->geos[c->set_geo[gal][set - 1]];
     PM_CK(cudaMemcpyAsync(host_out, c->rho[gal][set - 1], gb.A * 8, cudaMemcpyDeviceToHost, c->user));
     PM_CK(cudaStreamSynchronize(c->user));
-    return PM_OK;
+    return check_device_error(c);
 }
 
 int pm_get_potential(pm_ctx *c, int32_t gal, int32_t set, void *host_out) {
@@ -792,7 +884,7 @@ int pm_get_potential(pm_ctx *c, int32_t gal, int32_t set, void *host_out) {
     const GeoBuf &gb = c->geos[c->set_geo[gal][set - 1]];
     PM_CK(cudaMemcpyAsync(host_out, c->phi[gal][set - 1], gb.A * c->esz, cudaMemcpyDeviceToHost, c->user));
     PM_CK(cudaStreamSynchronize(c->user));
-    return PM_OK;
+    return check_device_error(c);
 }
 
 int pm_get_centres(pm_ctx *c, double *host_out) {
@@ -821,7 +913,7 @@ int pm_count_lost(pm_ctx *c, const pm_particles *p, int64_t *host_out) {
     PM_CK(cudaMemcpyAsync(&h, c->d_cnt, sizeof(h), cudaMemcpyDeviceToHost, c->user));
     PM_CK(cudaStreamSynchronize(c->user));
     *host_out = (int64_t)h;
-    return PM_OK;
+    return check_device_error(c);
 }
 
 int pm_info(pm_ctx *c, int64_t *out) {

@@ -112,11 +112,48 @@ template <int SIGN, typename C> struct Dft<16, SIGN, C> {
     static __device__ __forceinline__ void run(C *v) { dft_split<4, 4, SIGN>(v); }
 };
 
+// Radix 16 as 4 x 4 with two prunings of the doubled-grid transforms:
+// ZIN: inputs 8..15 are zero (the padding half of a forward input), so each
+// first-level DFT4 has two nonzero inputs; HOUT: only outputs 0..7 are kept
+// (the active half of an inverse output), so each final DFT4 computes two.
+template <int SIGN, bool ZIN, bool HOUT, typename C>
+__device__ __forceinline__ void dft16(C *v) {
+    C y[16];
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+        C t[4];
+        if (ZIN) {
+            const C a = v[n2], b = v[4 + n2], wb = cmul_i<SIGN>(b);
+            t[0] = cadd(a, b); t[1] = cadd(a, wb); t[2] = csub(a, b); t[3] = csub(a, wb);
+        } else {
+            t[0] = v[n2]; t[1] = v[4 + n2]; t[2] = v[8 + n2]; t[3] = v[12 + n2];
+            Dft<4, SIGN, C>::run(t);
+        }
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) y[n2 * 4 + k1] = rot16<SIGN>(n2 * k1, t[k1]);
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+        const C t0 = y[k1], t1 = y[4 + k1], t2 = y[8 + k1], t3 = y[12 + k1];
+        if (HOUT) {
+            v[k1] = cadd(cadd(t0, t2), cadd(t1, t3));
+            v[k1 + 4] = cadd(csub(t0, t2), cmul_i<SIGN>(csub(t1, t3)));
+        } else {
+            C t[4] = {t0, t1, t2, t3};
+            Dft<4, SIGN, C>::run(t);
+#pragma unroll
+            for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = t[k2];
+        }
+    }
+}
+
 // Butterflies of stage S on the thread's E registers.  Thread t of a column
 // owns the stage items j = t + kk*TPC (kk < E/R); register kk*R + r holds the
 // input x[j + r*L/R] and afterwards the output y[(j/Ns)*Ns*R + j%Ns + r*Ns].
 // tw[m] = exp(-2 pi i m / L) (conjugated for SIGN > 0).
-template <int L, int S, bool REV, int SIGN, typename C>
+// ZIN / HOUT select the pruned radix-16 (see dft16); they are only passed
+// for radix-16 stages.
+template <int L, int S, bool REV, int SIGN, bool ZIN = false, bool HOUT = false, typename C>
 __device__ __forceinline__ void stage_butterflies(C *v, int t, const C *tw) {
     constexpr int R = radix(L, S, REV), Ns = stride_before(L, S, REV), TPC = L / E;
 #pragma unroll
@@ -130,7 +167,8 @@ __device__ __forceinline__ void stage_butterflies(C *v, int t, const C *tw) {
                 v[kk * R + r] = (SIGN < 0) ? cmul(v[kk * R + r], w) : cconjmul(v[kk * R + r], w);
             }
         }
-        Dft<R, SIGN, C>::run(v + kk * R);
+        if (R == 16 && (ZIN || HOUT)) dft16<SIGN, ZIN, HOUT>(v + kk * R);
+        else Dft<R, SIGN, C>::run(v + kk * R);
     }
 }
 
@@ -148,47 +186,74 @@ __device__ __forceinline__ int in_row(int t, int kk, int r) {
     return t + kk * TPC + r * (L / R);
 }
 
-// Writes stage S's outputs to shared memory (column c of a [L][ldc] array).
-template <int L, int S, bool REV, typename C>
-__device__ __forceinline__ void store_stage(C *sm, int ldc, int c, int t, const C *v) {
+// Shared-memory layouts of the exchange between stages.  A layout maps the
+// row (FFT index) of the calling thread's transform to an element offset.
+struct ColLayout {              // [row][ldc] array, transform = column c
+    int ldc, c;
+    __device__ __forceinline__ int operator()(int row) const { return row * ldc + c; }
+};
+struct RowLayout {              // one transform per padded row: a pad element
+    int base;                   // after every 16 keeps the strides of the
+    __device__ __forceinline__ int operator()(int row) const { return base + row + (row >> 4); }
+};                              // stage exchanges free of bank conflicts
+
+// Writes stage S's outputs to shared memory.
+template <int L, int S, bool REV, typename C, class LAY>
+__device__ __forceinline__ void store_stage(C *sm, const LAY &lay, int t, const C *v) {
     constexpr int R = radix(L, S, REV);
 #pragma unroll
     for (int kk = 0; kk < E / R; ++kk)
 #pragma unroll
-        for (int r = 0; r < R; ++r) sm[out_row<L, S, REV>(t, kk, r) * ldc + c] = v[kk * R + r];
+        for (int r = 0; r < R; ++r) sm[lay(out_row<L, S, REV>(t, kk, r))] = v[kk * R + r];
 }
 // Reads stage S's inputs from shared memory.
-template <int L, int S, bool REV, typename C>
-__device__ __forceinline__ void load_stage(const C *sm, int ldc, int c, int t, C *v) {
+template <int L, int S, bool REV, typename C, class LAY>
+__device__ __forceinline__ void load_stage(const C *sm, const LAY &lay, int t, C *v) {
     constexpr int R = radix(L, S, REV);
 #pragma unroll
     for (int kk = 0; kk < E / R; ++kk)
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[kk * R + r] = sm[in_row<L, S, REV>(t, kk, r) * ldc + c];
+        for (int r = 0; r < R; ++r) v[kk * R + r] = sm[lay(in_row<L, S, REV>(t, kk, r))];
+}
+template <int L, int S, bool REV, typename C>
+__device__ __forceinline__ void store_stage(C *sm, int ldc, int c, int t, const C *v) {
+    store_stage<L, S, REV>(sm, ColLayout{ldc, c}, t, v);
+}
+template <int L, int S, bool REV, typename C>
+__device__ __forceinline__ void load_stage(const C *sm, int ldc, int c, int t, C *v) {
+    load_stage<L, S, REV>(sm, ColLayout{ldc, c}, t, v);
 }
 
 // Runs stages 0..NS-1 given stage 0's inputs in registers; exchanges through
-// shared memory between stages.  On return the registers hold the last
-// stage's outputs (natural order rows in_row of the last stage).  All
-// threads of the block must call it (it synchronises).
-template <int L, bool REV, int SIGN, typename C>
-__device__ __forceinline__ void fft_core(C *v, C *sm, int ldc, int c, int t, const C *tw) {
+// shared memory (layout lay) between stages.  On return the registers hold
+// the last stage's outputs (natural order rows in_row of the last stage).
+// All threads of the block must call it (it synchronises).
+// ZIN: the inputs of rows >= L/2 are zero (forward transforms of padded
+// data; the first stage is radix 16 and only registers r < 8 are read).
+// HOUT: only the outputs of rows < L/2 are used (inverse transforms; the
+// last stage of a reversed plan is radix 16, outputs in registers r < 8).
+template <int L, bool REV, int SIGN, bool ZIN = false, bool HOUT = false, typename C, class LAY>
+__device__ __forceinline__ void fft_core(C *v, C *sm, const LAY &lay, int t, const C *tw) {
     constexpr int NS = nstages(L);
-    stage_butterflies<L, 0, REV, SIGN>(v, t, tw);
+    stage_butterflies<L, 0, REV, SIGN, ZIN, HOUT && NS == 1>(v, t, tw);
     if (NS > 1) {
-        store_stage<L, 0, REV>(sm, ldc, c, t, v);
+        store_stage<L, 0, REV>(sm, lay, t, v);
         __syncthreads();
-        load_stage<L, (NS > 1 ? 1 : 0), REV>(sm, ldc, c, t, v);
+        load_stage<L, (NS > 1 ? 1 : 0), REV>(sm, lay, t, v);
         __syncthreads();
-        stage_butterflies<L, (NS > 1 ? 1 : 0), REV, SIGN>(v, t, tw);
+        stage_butterflies<L, (NS > 1 ? 1 : 0), REV, SIGN, false, HOUT && NS == 2>(v, t, tw);
     }
     if (NS > 2) {
-        store_stage<L, (NS > 1 ? 1 : 0), REV>(sm, ldc, c, t, v);
+        store_stage<L, (NS > 1 ? 1 : 0), REV>(sm, lay, t, v);
         __syncthreads();
-        load_stage<L, (NS > 2 ? 2 : 0), REV>(sm, ldc, c, t, v);
+        load_stage<L, (NS > 2 ? 2 : 0), REV>(sm, lay, t, v);
         __syncthreads();
-        stage_butterflies<L, (NS > 2 ? 2 : 0), REV, SIGN>(v, t, tw);
+        stage_butterflies<L, (NS > 2 ? 2 : 0), REV, SIGN, false, HOUT>(v, t, tw);
     }
+}
+template <int L, bool REV, int SIGN, bool ZIN = false, bool HOUT = false, typename C>
+__device__ __forceinline__ void fft_core(C *v, C *sm, int ldc, int c, int t, const C *tw) {
+    fft_core<L, REV, SIGN, ZIN, HOUT>(v, sm, ColLayout{ldc, c}, t, tw);
 }
 
 }  // namespace pmfft

@@ -29,7 +29,13 @@ struct GalK {
     float rc2, ro2;            // (float)(r_core^2), (float)(r_out^2)
     int recentre, sD;          // recentring flag, offset fixed-point shift
     unsigned long long *rho[PM_SETS];   // int64 densities (two's complement)
-    const void *phi[PM_SETS];           // potentials, context precision
+    // potentials in the context precision, combined as the force stencils
+    // read them (combination rule of Sec. 2.1)
+    const void *phi_fine;   // Phi_1
+    const void *phi_m3;     // Phi_3
+    const void *phi_m23;    // Phi_2 + Phi_3
+    const void *phi_c5;     // Phi_5
+    const void *phi_call;   // Phi_4 + Phi_5 (Phi_5 when there is no medium grid)
 };
 
 struct SysK {

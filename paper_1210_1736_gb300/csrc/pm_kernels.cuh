@@ -2,259 +2,9 @@
 // precision T (float or double).  Included once per precision.
 #pragma once
 
-#include "pm_fft.cuh"
-#include "pm_launch.h"
+#include "pm_passes.cuh"
 
 namespace pmk {
-
-using pmfft::E;
-using pmfft::nstages;
-using pmfft::radix;
-
-constexpr int NT = 256;  // threads per block for every FFT pass
-
-template <int L> struct XShape {          // x passes: lines (row pairs) per block
-    static constexpr int TPC = L / E, LINES = NT / TPC, LDC = LINES + 1;
-};
-template <int L> struct CShape {          // column passes: columns per block
-    static constexpr int TPC = L / E, COLS = NT / TPC, LDC = COLS;
-};
-
-template <typename T, int L> constexpr size_t xpass_smem() {
-    return (size_t)(L + L * XShape<L>::LDC) * sizeof(typename cplx_t<T>::type);
-}
-template <typename T, int L> constexpr size_t col_smem() {
-    return (size_t)(L + L * CShape<L>::LDC) * sizeof(typename cplx_t<T>::type);
-}
-
-template <typename C> __device__ __forceinline__ void load_twiddles(C *tw, const C *g, int L) {
-    for (int i = threadIdx.x; i < L; i += blockDim.x) tw[i] = g[i];
-}
-
-// ---------------------------------------------------------------------------
-// x forward pass: int64 density rows -> half spectra along x (R2C) with the
-// zero padding of the doubled grid implicit (rows are nx long, transforms
-// L = 2nx).  Two real rows travel as one complex line and are separated
-// after the transform: A = (Z[k] + conj Z[L-k]) / 2, B = (Z[k] - conj Z[L-k]) / 2i.
-// ---------------------------------------------------------------------------
-template <typename T, int L>
-__global__ void __launch_bounds__(NT) k_xfwd(FftArgs a) {
-    typedef typename cplx_t<T>::type C;
-    typedef XShape<L> S;
-    constexpr int NX = L / 2, P = NX + 1, NS = nstages(L);
-    extern __shared__ __align__(16) unsigned char smraw[];
-    C *tw = reinterpret_cast<C *>(smraw);
-    C *sm = tw + L;
-    const int tid = threadIdx.x;
-    load_twiddles(tw, static_cast<const C *>(a.tw), L);
-
-    const long long *rho = a.rho[blockIdx.y];
-    C *work = static_cast<C *>(a.work[blockIdx.y]);
-    const long long p0 = (long long)blockIdx.x * S::LINES;
-    const T scale = (T)a.scale;
-    const int ny = a.ny;
-
-    for (int e = tid; e < S::LINES * NX; e += NT) {
-        const int line = e / NX, x = e % NX;
-        const long long p = p0 + line;
-        C val = czero<C>();
-        if (p < a.nitems) {
-            const long long r0 = 2 * p;
-            val.x = (T)rho[r0 * NX + x] * scale;
-            val.y = (T)rho[(r0 + 1) * NX + x] * scale;
-        }
-        sm[x * S::LDC + line] = val;
-    }
-    __syncthreads();
-
-    const int c = tid % S::LINES, t = tid / S::LINES;
-    C v[E];
-    constexpr int R0 = radix(L, 0, false);
-#pragma unroll
-    for (int kk = 0; kk < E / R0; ++kk)
-#pragma unroll
-        for (int r = 0; r < R0; ++r)
-            v[kk * R0 + r] = (r < R0 / 2) ? sm[pmfft::in_row<L, 0, false>(t, kk, r) * S::LDC + c] : czero<C>();
-    __syncthreads();
-    pmfft::fft_core<L, false, -1>(v, sm, S::LDC, c, t, tw);
-    pmfft::store_stage<L, NS - 1, false>(sm, S::LDC, c, t, v);
-    __syncthreads();
-
-    for (int e = tid; e < S::LINES * P; e += NT) {
-        const int line = e / P, k = e % P;
-        const long long p = p0 + line;
-        if (p >= a.nitems) continue;
-        const C zk = sm[k * S::LDC + line];
-        const C zm = sm[((L - k) & (L - 1)) * S::LDC + line];
-        C A, B;
-        A.x = (T)0.5 * (zk.x + zm.x);
-        A.y = (T)0.5 * (zk.y - zm.y);
-        B.x = (T)0.5 * (zk.y + zm.y);
-        B.y = (T)-0.5 * (zk.x - zm.x);
-        const long long r0 = 2 * p, z = r0 / ny, y = r0 % ny;
-        C *row = work + ((size_t)z * 2 * ny + y) * P;
-        row[k] = A;
-        row[P + k] = B;
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Column passes along y or z (stride > 1): each block owns COLS consecutive
-// columns; a thread reads its first-stage inputs straight from global memory
-// (a warp reads contiguous row segments) and writes its last-stage outputs
-// back in place.
-//   COL_YFWD : forward along y, inputs y < ny (rest is padding), all 2ny out
-//   COL_ZCONV: forward along z (inputs z < nz), multiply by the real, even
-//              H-hat, inverse along z, keep z < nz       (Sec. 2.1)
-//   COL_YINV : inverse along y, keep y < ny
-// ---------------------------------------------------------------------------
-template <typename T, int L, int MODE>
-__global__ void __launch_bounds__(NT, 4) k_col(FftArgs a) {
-    typedef typename cplx_t<T>::type C;
-    typedef CShape<L> S;
-    constexpr int NS = nstages(L);
-    constexpr bool REV_IN = (MODE == COL_YINV);
-    constexpr int SIGN_IN = (MODE == COL_YINV) ? 1 : -1;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    C *tw = reinterpret_cast<C *>(smraw);
-    C *sm = tw + L;
-    const int tid = threadIdx.x;
-    load_twiddles(tw, static_cast<const C *>(a.tw), L);
-
-    const int c = tid % S::COLS, t = tid / S::COLS;
-    const long long q = (long long)blockIdx.x * S::COLS + c;
-    const bool valid = q < a.nitems;
-    const int P = a.P;
-    const size_t ny2P = (size_t)2 * a.ny * P;
-    size_t off, stride;
-    if (MODE == COL_ZCONV) {
-        off = (size_t)q;
-        stride = ny2P;
-    } else {
-        off = (size_t)(q / P) * ny2P + (size_t)(q % P);
-        stride = (size_t)P;
-    }
-    C *col = static_cast<C *>(a.work[blockIdx.y]) + (valid ? off : 0);
-    __syncthreads();
-
-    C v[E];
-    constexpr int R0 = radix(L, 0, REV_IN);
-#pragma unroll
-    for (int kk = 0; kk < E / R0; ++kk)
-#pragma unroll
-        for (int r = 0; r < R0; ++r) {
-            const bool need = valid && (MODE == COL_YINV || r < R0 / 2);
-            v[kk * R0 + r] = need ? col[(size_t)pmfft::in_row<L, 0, REV_IN>(t, kk, r) * stride] : czero<C>();
-        }
-    pmfft::fft_core<L, REV_IN, SIGN_IN>(v, sm, S::LDC, c, t, tw);
-
-    if (MODE == COL_YFWD) {
-        constexpr int RL = radix(L, NS - 1, false);
-        if (valid) {
-#pragma unroll
-            for (int kk = 0; kk < E / RL; ++kk)
-#pragma unroll
-                for (int r = 0; r < RL; ++r)
-                    col[(size_t)pmfft::in_row<L, NS - 1, false>(t, kk, r) * stride] = v[kk * RL + r];
-        }
-        return;
-    }
-    if (MODE == COL_ZCONV) {
-        constexpr int RL = radix(L, NS - 1, false);
-        const T *hh = static_cast<const T *>(a.hhat);
-        const int ny = a.ny;
-        const int ky = valid ? (int)(q / P) : 0, kx = valid ? (int)(q % P) : 0;
-        const int kyr = ky <= ny ? ky : 2 * ny - ky;
-#pragma unroll
-        for (int kk = 0; kk < E / RL; ++kk)
-#pragma unroll
-            for (int r = 0; r < RL; ++r) {
-                const int kz = pmfft::in_row<L, NS - 1, false>(t, kk, r);
-                const int kzr = kz <= L / 2 ? kz : L - kz;
-                const T h = valid ? hh[((size_t)kzr * (ny + 1) + kyr) * P + kx] : (T)0;
-                v[kk * RL + r].x *= h;
-                v[kk * RL + r].y *= h;
-            }
-        pmfft::fft_core<L, true, 1>(v, sm, S::LDC, c, t, tw);
-    }
-    // inverse outputs (COL_ZCONV, COL_YINV): the last stage of the reversed
-    // plan is radix 16 and its outputs below L/2 are registers r < 8.
-    constexpr int RL = radix(L, NS - 1, true);
-    if (valid) {
-#pragma unroll
-        for (int kk = 0; kk < E / RL; ++kk)
-#pragma unroll
-            for (int r = 0; r < RL / 2; ++r)
-                col[(size_t)pmfft::in_row<L, NS - 1, true>(t, kk, r) * stride] = v[kk * RL + r];
-    }
-}
-
-// ---------------------------------------------------------------------------
-// x inverse pass: two half-spectrum rows A, B -> Z = A + iB completed by
-// Hermitian symmetry, inverse transform, a = Re, b = Im; keep x < nx -> Phi.
-// ---------------------------------------------------------------------------
-template <typename T, int L>
-__global__ void __launch_bounds__(NT) k_xinv(FftArgs a) {
-    typedef typename cplx_t<T>::type C;
-    typedef XShape<L> S;
-    constexpr int NX = L / 2, P = NX + 1, NS = nstages(L);
-    extern __shared__ __align__(16) unsigned char smraw[];
-    C *tw = reinterpret_cast<C *>(smraw);
-    C *sm = tw + L;
-    const int tid = threadIdx.x;
-    load_twiddles(tw, static_cast<const C *>(a.tw), L);
-
-    const C *work = static_cast<const C *>(a.work[blockIdx.y]);
-    T *phi = static_cast<T *>(a.phi[blockIdx.y]);
-    const long long p0 = (long long)blockIdx.x * S::LINES;
-    const int ny = a.ny;
-
-    for (int e = tid; e < S::LINES * P; e += NT) {
-        const int line = e / P, k = e % P;
-        const long long p = p0 + line;
-        C A = czero<C>(), B = czero<C>();
-        if (p < a.nitems) {
-            const long long r0 = 2 * p, z = r0 / ny, y = r0 % ny;
-            const C *row = work + ((size_t)z * 2 * ny + y) * P;
-            A = row[k];
-            B = row[P + k];
-        }
-        C zk;
-        if (k == 0 || k == NX) {
-            zk.x = A.x; zk.y = B.x;
-            sm[k * S::LDC + line] = zk;
-        } else {
-            zk.x = A.x - B.y; zk.y = A.y + B.x;
-            sm[k * S::LDC + line] = zk;
-            C zm;
-            zm.x = A.x + B.y; zm.y = B.x - A.y;
-            sm[(L - k) * S::LDC + line] = zm;
-        }
-    }
-    __syncthreads();
-
-    const int c = tid % S::LINES, t = tid / S::LINES;
-    C v[E];
-    pmfft::load_stage<L, 0, true>(sm, S::LDC, c, t, v);
-    __syncthreads();
-    pmfft::fft_core<L, true, 1>(v, sm, S::LDC, c, t, tw);
-    constexpr int RL = radix(L, NS - 1, true);
-#pragma unroll
-    for (int kk = 0; kk < E / RL; ++kk)
-#pragma unroll
-        for (int r = 0; r < RL / 2; ++r)
-            sm[pmfft::in_row<L, NS - 1, true>(t, kk, r) * S::LDC + c] = v[kk * RL + r];
-    __syncthreads();
-
-    for (int e = tid; e < S::LINES * NX; e += NT) {
-        const int line = e / NX, x = e % NX;
-        const long long p = p0 + line;
-        if (p >= a.nitems) continue;
-        const C val = sm[x * S::LDC + line];
-        phi[(2 * p) * NX + x] = val.x;
-        phi[(2 * p + 1) * NX + x] = val.y;
-    }
-}
 
 // ---------------------------------------------------------------------------
 // Particle kernels.  The system description is a __grid_constant__ kernel
@@ -571,18 +321,18 @@ __global__ void __launch_bounds__(256, 3) k_force(PartK<T> p, const __grid_const
                     if (!cc.ok) continue;  // only after positions changed without a deposit
                     T dx, dy, dz;
                     cell_delta(G.coarse, cc, rsx, rsy, rsz, dx, dy, dz);
-                    stencil<T>(G.coarse, static_cast<const T *>(G.phi[4]),
-                               reg == REG_OUTER ? static_cast<const T *>(G.phi[3]) : nullptr, cc, dx, dy, dz, acc, php);
+                    stencil<T>(G.coarse, static_cast<const T *>(reg == REG_OUTER ? G.phi_call : G.phi_c5), nullptr,
+                               cc, dx, dy, dz, acc, php);
                     if (reg != REG_OUTER) {
                         const T rx = rel_off(xT, ce.c[0], ce.hi[0], ce.lo[0]);
                         const T ry = rel_off(yT, ce.c[1], ce.hi[1], ce.lo[1]);
                         const T rz = rel_off(zT, ce.c[2], ce.hi[2], ce.lo[2]);
                         cell_delta(G.med, cm, rx, ry, rz, dx, dy, dz);
-                        stencil<T>(G.med, static_cast<const T *>(G.phi[2]),
-                                   reg == REG_SHELL ? static_cast<const T *>(G.phi[1]) : nullptr, cm, dx, dy, dz, acc, php);
+                        stencil<T>(G.med, static_cast<const T *>(reg == REG_SHELL ? G.phi_m23 : G.phi_m3), nullptr,
+                                   cm, dx, dy, dz, acc, php);
                         if (reg == REG_CORE) {
                             cell_delta(G.fine, cf, rx, ry, rz, dx, dy, dz);
-                            stencil<T>(G.fine, static_cast<const T *>(G.phi[0]), nullptr, cf, dx, dy, dz, acc, php);
+                            stencil<T>(G.fine, static_cast<const T *>(G.phi_fine), nullptr, cf, dx, dy, dz, acc, php);
                         }
                     }
                 }
@@ -825,36 +575,72 @@ inline int particle_grid(long long n) {
     return (int)(b < cap ? (b > 0 ? b : 1) : cap);
 }
 
+template <typename T, int L, int MODE> int col_blocks_per_sm() {
+    static int cached = 0;
+    if (!cached) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pmk::k_col<T, L, MODE>, pmk::CShape<T, L>::THREADS,
+                                                          pmk::col_smem<T, L, MODE>()) != cudaSuccess || nb < 1)
+            nb = 1;
+        cached = nb;
+    }
+    return cached;
+}
+
+inline int num_sms() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 1;
+    }
+    return n;
+}
+
 template <typename T, int L> cudaError_t attrs_L() {
     cudaError_t e;
     e = cudaFuncSetAttribute(pmk::k_xfwd<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pmk::xpass_smem<T, L>());
     if (e) return e;
     e = cudaFuncSetAttribute(pmk::k_xinv<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pmk::xpass_smem<T, L>());
     if (e) return e;
-    e = cudaFuncSetAttribute(pmk::k_col<T, L, COL_YFWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pmk::col_smem<T, L>());
+    e = cudaFuncSetAttribute(pmk::k_col<T, L, COL_YFWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)pmk::col_smem<T, L, COL_YFWD>());
     if (e) return e;
-    e = cudaFuncSetAttribute(pmk::k_col<T, L, COL_ZCONV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pmk::col_smem<T, L>());
+    e = cudaFuncSetAttribute(pmk::k_col<T, L, COL_ZCONV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)pmk::col_smem<T, L, COL_ZCONV>());
     if (e) return e;
-    return cudaFuncSetAttribute(pmk::k_col<T, L, COL_YINV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pmk::col_smem<T, L>());
+    return cudaFuncSetAttribute(pmk::k_col<T, L, COL_YINV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)pmk::col_smem<T, L, COL_YINV>());
 }
 
-template <typename T, int L> cudaError_t xfwd_L(const FftArgs &a, int nsets, cudaStream_t st) {
-    dim3 grid((unsigned)((a.nitems + pmk::XShape<L>::LINES - 1) / pmk::XShape<L>::LINES), nsets);
-    pmk::k_xfwd<T, L><<<grid, pmk::NT, pmk::xpass_smem<T, L>(), st>>>(a);
+template <typename T, int L> cudaError_t xfwd_L(const PairArgs &a, cudaStream_t st) {
+    const long long rows = (long long)a.ny * a.nz;
+    pmk::k_xfwd<T, L><<<(unsigned)((rows + pmk::XShape<L>::LINES - 1) / pmk::XShape<L>::LINES), pmk::NT,
+                        pmk::xpass_smem<T, L>(), st>>>(a);
     return cudaGetLastError();
 }
-template <typename T, int L> cudaError_t xinv_L(const FftArgs &a, int nsets, cudaStream_t st) {
-    dim3 grid((unsigned)((a.nitems + pmk::XShape<L>::LINES - 1) / pmk::XShape<L>::LINES), nsets);
-    pmk::k_xinv<T, L><<<grid, pmk::NT, pmk::xpass_smem<T, L>(), st>>>(a);
+template <typename T, int L> cudaError_t xinv_L(const PairArgs &a, cudaStream_t st) {
+    const long long rows = (long long)a.ny * a.nz;
+    pmk::k_xinv<T, L><<<(unsigned)((rows + pmk::XShape<L>::LINES - 1) / pmk::XShape<L>::LINES), pmk::NT,
+                        pmk::xpass_smem<T, L>(), st>>>(a);
     return cudaGetLastError();
 }
-template <typename T, int L> cudaError_t col_L(const FftArgs &a, int mode, int nsets, cudaStream_t st) {
-    dim3 grid((unsigned)((a.nitems + pmk::CShape<L>::COLS - 1) / pmk::CShape<L>::COLS), nsets);
-    const size_t sm = pmk::col_smem<T, L>();
-    if (mode == COL_YFWD) pmk::k_col<T, L, COL_YFWD><<<grid, pmk::NT, sm, st>>>(a);
-    else if (mode == COL_ZCONV) pmk::k_col<T, L, COL_ZCONV><<<grid, pmk::NT, sm, st>>>(a);
-    else pmk::k_col<T, L, COL_YINV><<<grid, pmk::NT, sm, st>>>(a);
+template <typename T, int L, int MODE> cudaError_t col_LM(const PairArgs &a, const CUtensorMap &map, cudaStream_t st) {
+    constexpr int COLS = pmk::CShape<T, L>::COLS;
+    long long ntiles;
+    if (MODE == COL_ZCONV) ntiles = ((long long)4 * a.ny * a.nx + COLS - 1) / COLS;
+    else ntiles = (long long)a.nz * ((2 * a.nx + COLS - 1) / COLS);
+    long long grid = (long long)col_blocks_per_sm<T, L, MODE>() * num_sms();
+    if (grid > ntiles) grid = ntiles;
+    if (grid < 1) grid = 1;
+    pmk::k_col<T, L, MODE><<<(unsigned)grid, pmk::CShape<T, L>::THREADS, pmk::col_smem<T, L, MODE>(), st>>>(a, map,
+                                                                                                          ntiles);
     return cudaGetLastError();
+}
+template <typename T, int L> cudaError_t col_L(const PairArgs &a, const CUtensorMap &map, int mode, cudaStream_t st) {
+    if (mode == COL_YFWD) return col_LM<T, L, COL_YFWD>(a, map, st);
+    if (mode == COL_ZCONV) return col_LM<T, L, COL_ZCONV>(a, map, st);
+    return col_LM<T, L, COL_YINV>(a, map, st);
 }
 
 #define PM_SWITCH_L(L, CALL)                          \
@@ -880,19 +666,19 @@ template <typename T> cudaError_t pm_set_attrs() {
     return pmk_host::attrs_L<T, 512>();
 }
 
-template <typename T> cudaError_t pm_launch_xfwd(const FftArgs &a, int nsets, cudaStream_t st) {
-#define PM_XF(LL) pmk_host::xfwd_L<T, LL>(a, nsets, st)
+template <typename T> cudaError_t pm_launch_xfwd(const PairArgs &a, cudaStream_t st) {
+#define PM_XF(LL) pmk_host::xfwd_L<T, LL>(a, st)
     PM_SWITCH_L(2 * a.nx, PM_XF)
 #undef PM_XF
 }
-template <typename T> cudaError_t pm_launch_xinv(const FftArgs &a, int nsets, cudaStream_t st) {
-#define PM_XI(LL) pmk_host::xinv_L<T, LL>(a, nsets, st)
+template <typename T> cudaError_t pm_launch_xinv(const PairArgs &a, cudaStream_t st) {
+#define PM_XI(LL) pmk_host::xinv_L<T, LL>(a, st)
     PM_SWITCH_L(2 * a.nx, PM_XI)
 #undef PM_XI
 }
-template <typename T> cudaError_t pm_launch_col(const FftArgs &a, int mode, int nsets, cudaStream_t st) {
+template <typename T> cudaError_t pm_launch_col(const PairArgs &a, const CUtensorMap &map, int mode, cudaStream_t st) {
     const int L = (mode == COL_ZCONV) ? 2 * a.nz : 2 * a.ny;
-#define PM_CO(LL) pmk_host::col_L<T, LL>(a, mode, nsets, st)
+#define PM_CO(LL) pmk_host::col_L<T, LL>(a, map, mode, st)
     PM_SWITCH_L(L, PM_CO)
 #undef PM_CO
 }
@@ -963,9 +749,9 @@ cudaError_t pm_store_hhat(const double *in, T *out, long long n, double scale, c
 
 #define PM_INSTANTIATE(T)                                                                                       \
     template cudaError_t pm_set_attrs<T>();                                                                    \
-    template cudaError_t pm_launch_xfwd<T>(const FftArgs &, int, cudaStream_t);                               \
-    template cudaError_t pm_launch_xinv<T>(const FftArgs &, int, cudaStream_t);                               \
-    template cudaError_t pm_launch_col<T>(const FftArgs &, int, int, cudaStream_t);                           \
+    template cudaError_t pm_launch_xfwd<T>(const PairArgs &, cudaStream_t);                                   \
+    template cudaError_t pm_launch_xinv<T>(const PairArgs &, cudaStream_t);                                   \
+    template cudaError_t pm_launch_col<T>(const PairArgs &, const CUtensorMap &, int, cudaStream_t);          \
     template cudaError_t pm_launch_deposit<T>(const PartK<T> &, const SysK &, const CenK *, int, cudaStream_t); \
     template cudaError_t pm_launch_force<T>(int, const PartK<T> &, const SysK &, const CenK *, double, T *, T *, \
                                             T *, double *, cudaStream_t);                                      \

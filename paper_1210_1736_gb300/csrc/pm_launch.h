@@ -2,29 +2,43 @@
 // instantiated per precision in pm_fp32.cu and pm_fp64.cu.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include "pm_internal.cuh"
 
-#define PM_MAX_BATCH 16
-
-// One FFT pass over every mass set of one geometry (gridDim.y = nsets).
-struct FftArgs {
-    const long long *rho[PM_MAX_BATCH];   // int64 densities (x forward pass)
-    void *work[PM_MAX_BATCH];             // spectra, [z][y in 2ny][kx in nx+1]
-    void *phi[PM_MAX_BATCH];              // potentials (x inverse pass)
+// One FFT pass over a pair of mass sets of one geometry packed as
+// rho_a + i rho_b (rho_b may be null).
+struct PairArgs {
+    const long long *rho_a, *rho_b;       // int64 densities [z][y][x]
+    void *work;                           // complex [nz][2ny][2nx]
+    void *phi_b;                          // Phi_b (null without partner)
+    void *phi_sum;                        // Phi_a + Phi_b (or Phi_a)
     const void *hhat;                     // H-hat octant [nz+1][ny+1][nx+1]
-    const void *tw;                       // exp(-2 pi i m / L), m < L
-    int nx, ny, nz, P;                    // P = nx + 1
-    long long nitems;                     // row pairs (x passes) or columns
-    double scale;                         // 2^-s (x forward pass)
+    const void *tw;                       // exp(-2 pi i m / L), m < L, this pass's L
+    int nx, ny, nz;
+    double scale;                         // 2^-s
+    int *err;                             // set to 1 if a tensor copy never completes
 };
 
 enum { COL_YFWD = 0, COL_ZCONV = 1, COL_YINV = 2 };
 
+// Columns per tile of the column passes for transform length L and real
+// size esz: 16 threads per column, 256 threads per block, and a tensor-map
+// box row of at most 256 eight-byte elements.
+__host__ __device__ constexpr int pm_col_cols(int L, int esz) {
+    return (4096 / L) < (esz == 4 ? 256 : 128) ? (4096 / L) : (esz == 4 ? 256 : 128);
+}
+
+// Tensor maps (2D, 8-byte elements) of one pair's work array for the
+// column passes: y forward (box rows ny), y inverse (box rows min(2ny,256)),
+// z (box rows nz).  Host only; no device memory is touched.
+int pm_encode_col_maps(void *work, int nx, int ny, int nz, int esz, CUtensorMap *yfwd, CUtensorMap *yinv,
+                       CUtensorMap *zmap);
+
 template <typename T> cudaError_t pm_set_attrs();
-template <typename T> cudaError_t pm_launch_xfwd(const FftArgs &a, int nsets, cudaStream_t st);
-template <typename T> cudaError_t pm_launch_col(const FftArgs &a, int mode, int nsets, cudaStream_t st);
-template <typename T> cudaError_t pm_launch_xinv(const FftArgs &a, int nsets, cudaStream_t st);
+template <typename T> cudaError_t pm_launch_xfwd(const PairArgs &a, cudaStream_t st);
+template <typename T> cudaError_t pm_launch_col(const PairArgs &a, const CUtensorMap &map, int mode, cudaStream_t st);
+template <typename T> cudaError_t pm_launch_xinv(const PairArgs &a, cudaStream_t st);
 
 template <typename T>
 cudaError_t pm_launch_deposit(const PartK<T> &p, const SysK &sk, const CenK *cen, int aggregate, cudaStream_t st);

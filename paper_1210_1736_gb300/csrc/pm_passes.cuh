@@ -1,0 +1,362 @@
+// FFT passes of the doubled-grid convolution (Sec. 2.1) on pair-packed mass
+// sets: two real densities of one geometry (grids 2 and 3, or 4 and 5) travel
+// as one complex field rho_a + i rho_b, so every transform is a plain complex
+// FFT of power-of-two length and, H being real, the result is
+// Phi_a + i Phi_b.  A set without partner uses rho_b = 0.
+//
+// Work array per pair: complex [z < nz][y < 2ny][kx < 2nx].
+//   x forward : rows (z, y < ny), inputs x < nx (zero padding implicit)
+//   y forward : columns (z, kx), inputs y < ny, all 2ny outputs
+//   z convolve: columns (ky, kx), forward z (inputs z < nz), times the real,
+//               even H-hat, inverse z, outputs z < nz
+//   y inverse : columns (z, kx), all 2ny inputs, outputs y < ny
+//   x inverse : rows (z, y < ny), outputs x < nx: Phi_b = Im, Phi_a + Phi_b
+//
+// The column passes are persistent: each block walks tiles of COLS adjacent
+// columns; a TMA tensor copy brings the next-but-one tile's input rows into
+// shared memory (double buffer, mbarrier completion) while the block
+// transforms the current one; outputs go from registers straight to global
+// memory.
+#pragma once
+
+#include <cuda.h>
+
+#include "pm_fft.cuh"
+#include "pm_launch.h"
+
+namespace pmk {
+
+using pmfft::E;
+using pmfft::nstages;
+using pmfft::radix;
+
+constexpr int NT = 256;  // threads per block of the x passes
+
+template <int L> struct XShape {          // x passes: rows per block, padded row length
+    static constexpr int TPC = L / E, LINES = NT / TPC, LDR = L + L / 16;
+};
+
+template <typename T, int L> constexpr size_t xpass_smem() {
+    return (size_t)(L + XShape<L>::LINES * XShape<L>::LDR) * sizeof(typename cplx_t<T>::type);
+}
+
+template <typename C> __device__ __forceinline__ void load_twiddles(C *tw, const C *g, int L) {
+    for (int i = threadIdx.x; i < L; i += blockDim.x) tw[i] = g[i];
+}
+
+// ---------------------------------------------------------------------------
+// x passes: the TPC = L/16 threads of a row are consecutive lanes, so a
+// stage's inputs (rows t + k L/R) and the natural-order outputs are read and
+// written straight between global memory and registers with warp-contiguous
+// addresses; shared memory only carries the exchanges between stages.
+// ---------------------------------------------------------------------------
+// x forward: z[x] = rho_a + i rho_b (scaled to mass), forward FFT of length
+// L = 2nx, all L outputs written to the row of the work array.
+template <typename T, int L>
+__global__ void __launch_bounds__(NT) k_xfwd(PairArgs a) {
+    typedef typename cplx_t<T>::type C;
+    typedef XShape<L> S;
+    constexpr int NX = L / 2, NS = nstages(L);
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C *tw = reinterpret_cast<C *>(smraw);
+    C *sm = tw + L;
+    const int tid = threadIdx.x, line = tid / S::TPC, t = tid % S::TPC;
+    load_twiddles(tw, static_cast<const C *>(a.tw), L);
+    const long long nrows = (long long)a.ny * a.nz;
+    const long long r = (long long)blockIdx.x * S::LINES + line;
+    const bool valid = r < nrows;
+    const T scale = (T)a.scale;
+    const long long *ra = a.rho_a + (valid ? r * NX : 0);
+    const long long *rb = a.rho_b ? a.rho_b + (valid ? r * NX : 0) : nullptr;
+
+    C v[E];
+    constexpr int R0 = radix(L, 0, false);
+#pragma unroll
+    for (int kk = 0; kk < E / R0; ++kk)
+#pragma unroll
+        for (int q = 0; q < R0; ++q) {
+            C val = czero<C>();
+            if (valid && q < R0 / 2) {   // inputs x >= nx are the zero padding
+                const int x = pmfft::in_row<L, 0, false>(t, kk, q);
+                val.x = (T)ra[x] * scale;
+                if (rb) val.y = (T)rb[x] * scale;
+            }
+            v[kk * R0 + q] = val;
+        }
+    __syncthreads();   // twiddles
+    pmfft::fft_core<L, false, -1, true, false>(v, sm, pmfft::RowLayout{line * S::LDR}, t, tw);
+    if (!valid) return;
+    const long long z = r / a.ny, y = r % a.ny;
+    C *out = static_cast<C *>(a.work) + ((size_t)z * 2 * a.ny + y) * L;
+    constexpr int RL = radix(L, NS - 1, false);
+#pragma unroll
+    for (int kk = 0; kk < E / RL; ++kk)
+#pragma unroll
+        for (int q = 0; q < RL; ++q) out[pmfft::in_row<L, NS - 1, false>(t, kk, q)] = v[kk * RL + q];
+}
+
+// x inverse: inverse FFT of length L = 2nx of each row y < ny; x < nx kept:
+// Phi_b = Im, Phi_sum = Re + Im (or Re without partner).
+template <typename T, int L>
+__global__ void __launch_bounds__(NT) k_xinv(PairArgs a) {
+    typedef typename cplx_t<T>::type C;
+    typedef XShape<L> S;
+    constexpr int NX = L / 2, NS = nstages(L);
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C *tw = reinterpret_cast<C *>(smraw);
+    C *sm = tw + L;
+    const int tid = threadIdx.x, line = tid / S::TPC, t = tid % S::TPC;
+    load_twiddles(tw, static_cast<const C *>(a.tw), L);
+    const long long nrows = (long long)a.ny * a.nz;
+    const long long r = (long long)blockIdx.x * S::LINES + line;
+    const bool valid = r < nrows;
+    const long long z = valid ? r / a.ny : 0, y = valid ? r % a.ny : 0;
+    const C *in = static_cast<const C *>(a.work) + ((size_t)z * 2 * a.ny + y) * L;
+
+    C v[E];
+    constexpr int R0 = radix(L, 0, true);
+#pragma unroll
+    for (int kk = 0; kk < E / R0; ++kk)
+#pragma unroll
+        for (int q = 0; q < R0; ++q)
+            v[kk * R0 + q] = valid ? in[pmfft::in_row<L, 0, true>(t, kk, q)] : czero<C>();
+    __syncthreads();   // twiddles
+    pmfft::fft_core<L, true, 1, false, true>(v, sm, pmfft::RowLayout{line * S::LDR}, t, tw);
+    if (!valid) return;
+    T *phi_b = static_cast<T *>(a.phi_b);
+    T *phi_s = static_cast<T *>(a.phi_sum) + r * NX;
+    constexpr int RL = radix(L, NS - 1, true);
+#pragma unroll
+    for (int kk = 0; kk < E / RL; ++kk)
+#pragma unroll
+        for (int q = 0; q < RL / 2; ++q) {   // outputs x < nx: registers q < 8 of the radix-16 last stage
+            const int x = pmfft::in_row<L, NS - 1, true>(t, kk, q);
+            const C val = v[kk * RL + q];
+            if (phi_b) {
+                phi_b[r * NX + x] = val.y;
+                phi_s[x] = val.x + val.y;
+            } else {
+                phi_s[x] = val.x;
+            }
+        }
+}
+
+// ---------------------------------------------------------------------------
+// TMA and mbarrier helpers (inline PTX)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned phase) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Waits for the phase with a time limit (2 s); false if it did not complete.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned phase) {
+    if (mbar_try_wait(bar, phase)) return true;
+    const unsigned long long t0 = globaltimer_ns();
+    while (!mbar_try_wait(bar, phase))
+        if (globaltimer_ns() - t0 > 2000000000ull) return false;
+    return true;
+}
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Columns per tile and threads per block of the column passes (shared with
+// the host, which encodes the tensor-map boxes).
+template <typename T, int L> struct CShape {
+    static constexpr int TPC = L / E;
+    static constexpr int COLS = pm_col_cols(L, (int)sizeof(T));
+    static constexpr int THREADS = COLS * TPC;
+    static constexpr int EPC = sizeof(typename cplx_t<T>::type) / 8;   // 8-byte tensor elements per complex
+};
+
+template <int MODE> struct ColRows;       // input rows per tile for a transform of length L
+template <> struct ColRows<COL_YFWD> { __host__ __device__ static constexpr int of(int L) { return L / 2; } };
+template <> struct ColRows<COL_ZCONV> { __host__ __device__ static constexpr int of(int L) { return L / 2; } };
+template <> struct ColRows<COL_YINV> { __host__ __device__ static constexpr int of(int L) { return L; } };
+
+template <typename T, int L, int MODE> constexpr size_t col_smem() {
+    typedef typename cplx_t<T>::type C;
+    constexpr int COLS = CShape<T, L>::COLS;
+    return 128 + (size_t)L * sizeof(C) + (size_t)L * COLS * sizeof(C) +
+           2 * (size_t)ColRows<MODE>::of(L) * COLS * sizeof(C) + 3 * 128;
+}
+
+// Persistent column pass.  map: 2D tensor map over 8-byte elements whose box
+// is (COLS * EPC, min(rows, 256)); tile t covers COLS columns.
+template <typename T, int L, int MODE>
+__global__ void __launch_bounds__(CShape<T, L>::THREADS, 3) k_col(PairArgs a, const __grid_constant__ CUtensorMap map,
+                                                               long long ntiles) {
+    typedef typename cplx_t<T>::type C;
+    typedef CShape<T, L> S;
+    constexpr int COLS = S::COLS, NS = nstages(L), ROWS = ColRows<MODE>::of(L);
+    constexpr int BOXR = ROWS < 256 ? ROWS : 256, NBOX = ROWS / BOXR;
+    constexpr unsigned TILE_BYTES = (unsigned)(ROWS * COLS * sizeof(C));
+    constexpr bool REV_IN = (MODE == COL_YINV);
+    constexpr int SIGN_IN = (MODE == COL_YINV) ? 1 : -1;
+
+    extern __shared__ __align__(128) unsigned char smraw[];
+    unsigned char *base = reinterpret_cast<unsigned char *>(((uintptr_t)smraw + 127) & ~(uintptr_t)127);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(base);                 // 2 mbarriers
+    C *buf0 = reinterpret_cast<C *>(base + 128);
+    C *buf1 = buf0 + ROWS * COLS;
+    C *sm = buf1 + ROWS * COLS;
+    C *tw = sm + L * COLS;
+    const int tid = threadIdx.x;
+    const int c = tid % COLS, t = tid / COLS;
+    C *work = static_cast<C *>(a.work);
+    const int nx2 = 2 * a.nx, ny2 = 2 * a.ny;
+    const long long tiles_per_z = (nx2 + COLS - 1) / COLS;
+
+    // tile -> TMA coordinates and the first column it covers
+    auto coords = [&](long long tile, int &x, int &y) {
+        if (MODE == COL_ZCONV) {
+            x = (int)(tile * COLS * S::EPC);
+            y = 0;
+        } else {
+            x = (int)((tile % tiles_per_z) * COLS * S::EPC);
+            y = (int)((tile / tiles_per_z) * ny2);
+        }
+    };
+    auto issue = [&](long long tile, int b) {
+        int x, y;
+        coords(tile, x, y);
+        C *dst = b ? buf1 : buf0;
+        mbar_expect_tx(&bar[b], TILE_BYTES);
+#pragma unroll
+        for (int k = 0; k < NBOX; ++k) tma_load_2d(dst + k * BOXR * COLS, &map, x, y + k * BOXR, &bar[b]);
+    };
+
+    if (tid == 0) {
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map)) : "memory");
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    load_twiddles(tw, static_cast<const C *>(a.tw), L);
+    __syncthreads();
+    int issued[2] = {0, 0};   // loads issued per buffer (thread 0's count)
+    if (tid == 0) {
+        if (blockIdx.x < ntiles) { issue(blockIdx.x, 0); ++issued[0]; }
+        if (blockIdx.x + gridDim.x < ntiles) { issue(blockIdx.x + gridDim.x, 1); ++issued[1]; }
+    }
+
+    int it = 0;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+        const int b = it & 1;
+        const unsigned phase = (unsigned)((it >> 1) & 1);
+        // a tensor copy that never lands: report, wait (bounded) for the other
+        // copy in flight, stop; the decision is the same for the whole block
+        if (!__syncthreads_and(mbar_wait(&bar[b], phase) ? 1 : 0)) {
+            if (tid == 0) {
+                atomicExch(a.err, 1);
+                const int o = b ^ 1, used_o = it >> 1;   // uses of buffer o completed so far
+                if (issued[o] > used_o) mbar_wait(&bar[o], (unsigned)(used_o & 1));
+            }
+            break;
+        }
+        const C *in = b ? buf1 : buf0;
+        C v[E];
+        constexpr int R0 = radix(L, 0, REV_IN);
+#pragma unroll
+        for (int kk = 0; kk < E / R0; ++kk)
+#pragma unroll
+            for (int r = 0; r < R0; ++r) {
+                const bool need = (MODE == COL_YINV) || r < R0 / 2;   // forward inputs above L/2 are padding
+                v[kk * R0 + r] = need ? in[pmfft::in_row<L, 0, REV_IN>(t, kk, r) * COLS + c] : czero<C>();
+            }
+        __syncthreads();   // buffer b consumed, previous tile's exchange done
+        if (tid == 0 && tile + 2 * (long long)gridDim.x < ntiles) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(tile + 2 * (long long)gridDim.x, b);
+            ++issued[b];
+        }
+
+        // column of this thread
+        long long q;
+        bool valid;
+        C *col;
+        size_t stride;
+        if (MODE == COL_ZCONV) {
+            q = tile * COLS + c;
+            valid = q < (long long)ny2 * nx2;
+            col = work + q;
+            stride = (size_t)ny2 * nx2;
+        } else {
+            const long long z = tile / tiles_per_z, kx = (tile % tiles_per_z) * COLS + c;
+            q = kx;
+            valid = kx < nx2;
+            col = work + (size_t)z * ny2 * nx2 + kx;
+            stride = (size_t)nx2;
+        }
+
+        pmfft::fft_core<L, REV_IN, SIGN_IN, MODE != COL_YINV, MODE == COL_YINV>(v, sm, COLS, c, t, tw);
+        if (MODE == COL_YFWD) {
+            constexpr int RL = radix(L, NS - 1, false);
+            if (valid) {
+#pragma unroll
+                for (int kk = 0; kk < E / RL; ++kk)
+#pragma unroll
+                    for (int r = 0; r < RL; ++r)
+                        col[(size_t)pmfft::in_row<L, NS - 1, false>(t, kk, r) * stride] = v[kk * RL + r];
+            }
+            continue;
+        }
+        if (MODE == COL_ZCONV) {
+            constexpr int RL = radix(L, NS - 1, false);
+            const T *hh = static_cast<const T *>(a.hhat);
+            const int ky = valid ? (int)(q / nx2) : 0, kx = valid ? (int)(q % nx2) : 0;
+            const int kyr = ky <= a.ny ? ky : ny2 - ky;
+            const int kxr = kx <= a.nx ? kx : nx2 - kx;
+            const size_t hrow = ((size_t)kyr * (a.nx + 1) + kxr);
+            const size_t hplane = (size_t)(a.ny + 1) * (a.nx + 1);
+#pragma unroll
+            for (int kk = 0; kk < E / RL; ++kk)
+#pragma unroll
+                for (int r = 0; r < RL; ++r) {
+                    const int kz = pmfft::in_row<L, NS - 1, false>(t, kk, r);
+                    const int kzr = kz <= L / 2 ? kz : L - kz;
+                    const T h = valid ? __ldg(hh + (size_t)kzr * hplane + hrow) : (T)0;
+                    v[kk * RL + r].x *= h;
+                    v[kk * RL + r].y *= h;
+                }
+            pmfft::fft_core<L, true, 1, false, true>(v, sm, COLS, c, t, tw);
+        }
+        // inverse outputs (COL_ZCONV, COL_YINV): the reversed plan ends with
+        // radix 16, whose outputs below L/2 are registers r < 8
+        constexpr int RL = radix(L, NS - 1, true);
+        if (valid) {
+#pragma unroll
+            for (int kk = 0; kk < E / RL; ++kk)
+#pragma unroll
+                for (int r = 0; r < RL / 2; ++r)
+                    col[(size_t)pmfft::in_row<L, NS - 1, true>(t, kk, r) * stride] = v[kk * RL + r];
+        }
+    }
+}
+
+}  // namespace pmk

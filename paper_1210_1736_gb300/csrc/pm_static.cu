@@ -75,15 +75,16 @@ template <typename T>
 int run(const int64_t *rho, void *phi, int nx, int ny, int nz, double l_xy, double l_z, double G, double h000,
         int shift, unsigned char *base, cudaStream_t st) {
     typedef typename cplx_t<T>::type C;
-    const size_t P = nx + 1, oct = (size_t)(nx + 1) * (ny + 1) * (nz + 1);
+    const size_t oct = (size_t)(nx + 1) * (ny + 1) * (nz + 1);
     const int nmax = std::max(nx, std::max(ny, nz)) + 1;
     size_t off = 0;
     auto take = [&](size_t bytes) { unsigned char *p = base + off; off += up256(bytes); return p; };
-    C *work = (C *)take((size_t)nz * 2 * ny * P * sizeof(C));
+    C *work = (C *)take((size_t)nz * 2 * ny * 2 * nx * sizeof(C));
     T *hhat = (T *)take(oct * sizeof(T));
     double *h = (double *)take(oct * sizeof(double));
     double *t1 = (double *)take(oct * sizeof(double));
     double *cm = (double *)take((size_t)nmax * nmax * sizeof(double));
+    int *err = (int *)take(sizeof(int));
     C *twx = (C *)take((size_t)2 * nx * sizeof(C));
     C *twy = (C *)take((size_t)2 * ny * sizeof(C));
     C *twz = (C *)take((size_t)2 * nz * sizeof(C));
@@ -111,39 +112,40 @@ int run(const int64_t *rho, void *phi, int nx, int ny, int nz, double l_xy, doub
     SCK(pm_axis_transform(h, t1, cm, nz + 1, 1, (long long)(ny + 1) * (nx + 1), st));
     SCK(pm_store_hhat<T>(t1, hhat, (long long)oct, G / (l_xy * 8.0 * nx * ny * nz), st));
 
-    FftArgs a;
+    CUtensorMap yfwd, yinv, zmap;
+    if (pm_encode_col_maps(work, nx, ny, nz, (int)sizeof(T), &yfwd, &yinv, &zmap) != PM_OK) return PM_E_CUDA;
+    SCK(cudaMemsetAsync(err, 0, sizeof(int), st));
+    PairArgs a;
     std::memset(&a, 0, sizeof(a));
-    a.rho[0] = (const long long *)rho;
-    a.work[0] = work;
-    a.phi[0] = phi;
+    a.rho_a = (const long long *)rho;
+    a.rho_b = nullptr;
+    a.work = work;
+    a.phi_b = nullptr;
+    a.phi_sum = phi;
     a.hhat = hhat;
-    a.nx = nx; a.ny = ny; a.nz = nz; a.P = nx + 1;
+    a.nx = nx; a.ny = ny; a.nz = nz;
     a.scale = std::ldexp(1.0, -shift);
+    a.err = err;
     a.tw = twx;
-    a.nitems = (long long)ny * nz / 2;
-    SCK(pm_launch_xfwd<T>(a, 1, st));
+    SCK(pm_launch_xfwd<T>(a, st));
     a.tw = twy;
-    a.nitems = (long long)nz * (nx + 1);
-    SCK(pm_launch_col<T>(a, COL_YFWD, 1, st));
+    SCK(pm_launch_col<T>(a, yfwd, COL_YFWD, st));
     a.tw = twz;
-    a.nitems = (long long)2 * ny * (nx + 1);
-    SCK(pm_launch_col<T>(a, COL_ZCONV, 1, st));
+    SCK(pm_launch_col<T>(a, zmap, COL_ZCONV, st));
     a.tw = twy;
-    a.nitems = (long long)nz * (nx + 1);
-    SCK(pm_launch_col<T>(a, COL_YINV, 1, st));
+    SCK(pm_launch_col<T>(a, yinv, COL_YINV, st));
     a.tw = twx;
-    a.nitems = (long long)ny * nz / 2;
-    SCK(pm_launch_xinv<T>(a, 1, st));
+    SCK(pm_launch_xinv<T>(a, st));
 #undef SCK
     return PM_OK;
 }
 
 size_t scratch_bytes(int nx, int ny, int nz, size_t esz) {
-    const size_t P = nx + 1, oct = (size_t)(nx + 1) * (ny + 1) * (nz + 1);
+    const size_t oct = (size_t)(nx + 1) * (ny + 1) * (nz + 1);
     const size_t nmax = std::max(nx, std::max(ny, nz)) + 1;
-    return up256((size_t)nz * 2 * ny * P * 2 * esz) + up256(oct * esz) + 2 * up256(oct * 8) +
-           up256(nmax * nmax * 8) + up256((size_t)2 * nx * 2 * esz) + up256((size_t)2 * ny * 2 * esz) +
-           up256((size_t)2 * nz * 2 * esz);
+    return up256((size_t)nz * 2 * ny * 2 * nx * 2 * esz) + up256(oct * esz) + 2 * up256(oct * 8) +
+           up256(nmax * nmax * 8) + up256(sizeof(int)) + up256((size_t)2 * nx * 2 * esz) +
+           up256((size_t)2 * ny * 2 * esz) + up256((size_t)2 * nz * 2 * esz);
 }
 
 }  // namespace
