@@ -32,6 +32,14 @@ sys.path.insert(0, ROOT)
 METRIC = "particle-steps/s per nested-grid step; FFT-convolve GB/s vs HBM peak"
 UNIT = "particle-steps/s"
 WORKLOAD = "galaxy_1m"
+WORKLOAD_DESC = {
+    "galaxy_1m": "galaxy_1m: 1M particles (400k exp. disc, 100k Hernquist bulge, 500k truncated NFW halo); "
+                 "grids coarse 128^3, medium 128^3 q=1/4, fine 128x128x32; dt=0.01",
+    "merger_4m": "merger_4m: 4M-particle galaxy + 100k Plummer satellite; galaxy grids 128^3, 128^3 q=1/4, "
+                 "256x256x32; satellite grids 64^3 x 3; dt=0.01",
+    "large_16m": "large_16m: 16M-particle galaxy + two 250k Plummer satellites; galaxy grids 256^3, 256^3 q=1/4, "
+                 "256x256x64; satellite grids 128^3 x 3 each; dt=0.01",
+}
 PHASES = ["recentre", "deposit", "fft_x_fwd", "fft_y_fwd", "fft_z_conv", "fft_y_inv", "fft_x_inv", "force_kick_drift"]
 SORT_PHASE = 9
 
@@ -163,7 +171,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    w = getattr(W, WORKLOAD)()
+    w = getattr(W, args.workload)()
     dt = w["dt"]
     m32 = w["m"].astype(np.float32)
     ctx = pm.Context(w, mass_bound(m32))
@@ -245,12 +253,10 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": Wm,
         "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic (seeded disc-bulge-halo galaxy, random order)",
-        "config": {"workload": f"{WORKLOAD}: 1M particles (400k exp. disc, 100k Hernquist bulge, "
-                               "500k truncated NFW halo); grids coarse 128^3, medium 128^3 q=1/4, "
-                               "fine 128x128x32; dt=0.01",
-                   "particles_per_gpu": n, "grids": 5, "geometries": 3,
+        "config": {"workload": WORKLOAD_DESC[args.workload],
+                   "particles_per_gpu": n, "galaxies": len(w["galaxies"]), "geometries": ctx.info()["ngeom"],
                    "spatial_sort_every": args.sort_every,
-                   "l2": "working set per step ~0.29 GB > 129 MB L2 (no flush needed)",
+                   "l2": f"working set per step ~{ctx.info()['bytes'] / 1e9:.2f} GB > 129 MB L2 (no flush needed)",
                    "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
@@ -263,14 +269,14 @@ def run_ours(args):
         "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = oracle_rate(w, budget_s=25.0, max_steps=3)
+        line["cpu_baseline"] = oracle_rate(w, args.workload, budget_s=25.0, max_steps=3)
     if world > 1:
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(line), flush=True)
 
 
-def oracle_rate(w, budget_s, max_steps, warmup=0):
+def oracle_rate(w, workload, budget_s, max_steps, warmup=0):
     """The FP64 oracle, as it stands, on this host: full steps of the same
     workload until max_steps or the time budget is reached."""
     import oracle as O
@@ -289,7 +295,7 @@ def oracle_rate(w, budget_s, max_steps, warmup=0):
     el = time.perf_counter() - t0
     n = len(state.m)
     return {"value": n * done / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{done} full FP64 oracle step(s) of {WORKLOAD} ({n} particles), "
+            "sample": f"{done} full FP64 oracle step(s) of {workload} ({n} particles), "
                       f"{el:.1f} s, single-threaded numpy"}
 
 
@@ -298,12 +304,12 @@ def run_reference(args):
     rank, _, world = env_rank()
     if rank != 0:
         return
-    w = getattr(W, WORKLOAD)()
-    cb = oracle_rate(w, budget_s=90.0, max_steps=max(1, args.steps), warmup=min(args.warmup, 1))
+    w = getattr(W, args.workload)()
+    cb = oracle_rate(w, args.workload, budget_s=90.0, max_steps=max(1, args.steps), warmup=min(args.warmup, 1))
     line = {"metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic (seeded disc-bulge-halo galaxy)", "impl": "reference",
-            "config": {"workload": WORKLOAD},
+            "config": {"workload": WORKLOAD_DESC[args.workload]},
             "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -316,6 +322,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOAD_DESC))
     ap.add_argument("--sort-every", type=int, default=10,
                     help="re-sort particles by cell every k steps inside the timed steps (0: never)")
     args = ap.parse_args()

@@ -57,7 +57,7 @@ __all__ = [
     "potential_direct", "accel_from_grid", "phi_at_particle",
     "accelerations", "kick", "drift", "recentre", "step", "diagnostics",
     "State", "solve_all", "rho_real", "mass_sets", "combination", "lost_mask",
-    "grid_cells", "r2_f32", "half_kick_start", "REGION_CORE", "REGION_SHELL",
+    "grid_cells", "r2_f32", "half_kick_start", "potential_at", "REGION_CORE", "REGION_SHELL",
     "REGION_OUTER", "FLAG_LOST",
 ]
 
@@ -349,6 +349,24 @@ def potential_direct(rho: np.ndarray, g: Geometry, G: float, h000: float) -> np.
     H[r2 == 0] = h000
     phi = (G / g.l_xy) * (H @ rho.ravel())
     return phi.reshape(g.shape)
+
+
+def potential_at(rho: np.ndarray, g: Geometry, G: float, h000: float, cells) -> np.ndarray:
+    """Eq. (eq:poisson) evaluated at selected cells only, as the plain sum over
+    the occupied cells of rho (any grid size): Phi[a] = G/l_xy sum rho H."""
+    occ = np.nonzero(rho)
+    w = rho[occ]
+    cz, cy, cx = (np.asarray(c, dtype=np.float64) for c in occ)
+    out = np.empty(len(cells))
+    for n, (k, j, i) in enumerate(cells):
+        dx = cx - i
+        dy = cy - j
+        dz = (cz - k) * g.q
+        r2 = dx * dx + dy * dy + dz * dz
+        with np.errstate(divide="ignore"):
+            H = np.where(r2 > 0, 1.0 / np.sqrt(np.where(r2 > 0, r2, 1.0)), h000)
+        out[n] = (G / g.l_xy) * np.sum(w * H)
+    return out
 
 
 def solve_all(rho, system: System, s: int):

@@ -18,6 +18,9 @@ galaxy_small  the same model scaled to 48k particles on 32^3 / 32^3 (q = 0.8,
             the oracle inside a test).
 merger_4m   galaxy scaled to 4M particles plus a 100k Plummer satellite; six
             geometries (galaxy 128^3, 128^3, 256x256x32; satellite 64^3 x 3).
+large_16m   16M-particle galaxy on 256^3 / 256^3 / 256x256x64 grids plus two
+            250k Plummer satellites with 128^3 grids.
+merger_small, big_box, galaxy_256: test-size and largest-grid cases.
 """
 from __future__ import annotations
 
@@ -81,35 +84,94 @@ def galaxy_small(precision="fp32", n_total=48_000, seed_id=11):
                   name="galaxy_small", q_m=0.8)
 
 
-def merger(n_gal=4_000_000, n_sat=100_000, grids=((128,), (128,), (256, 256, 32), (64,)),
-           seed_id=2, precision="fp32", name="merger_4m"):
-    """Galaxy plus a Plummer satellite (M = 0.1 M_disc, a = 0.05) at apocentre
-    8 R_d on an orbit of eccentricity 0.5, inclined 30 degrees; the apocentre
-    speed is the point-mass value sqrt(G M(<8) (1 - e) / 8)."""
-    pos, vel, m = _galaxy_particles(n_gal, seed_id)
-    ps, vs, ms = synth.plummer(n_sat, synth.rng_for(seed_id, 4), M=0.1, a=0.05, r_trunc=0.5)
-    R_A, e, inc = 8.0, 0.5, np.deg2rad(30.0)
-    m_enc = float(m[np.linalg.norm(pos, axis=0) < R_A].sum())
+def _satellite(pos_g, m_g, n_sat, rng, M, a, R_A, phase, inc_deg, ns, e=0.5):
+    """Plummer satellite (truncated at 10a) at apocentre R_A in the disc plane
+    at azimuth `phase`, orbit eccentricity e and inclination inc_deg; the
+    apocentre speed is the point-mass value sqrt(G M(<R_A) (1 - e) / R_A)
+    (the construction of Sec. 6.1 of the paper)."""
+    ps, vs, ms = synth.plummer(n_sat, rng, M=M, a=a, r_trunc=10 * a)
+    inc = np.deg2rad(inc_deg)
+    m_enc = float(m_g[np.linalg.norm(pos_g, axis=0) < R_A].sum())
     v_apo = np.sqrt(m_enc * (1 - e) / R_A)
-    ps = ps + np.array([[R_A], [0.0], [0.0]])
-    vs = vs + np.array([[0.0], [v_apo * np.cos(inc)], [v_apo * np.sin(inc)]])
-    n_c = grids[0][0]
-    n_m = grids[1][0]
-    n_f = grids[2]
-    ns = grids[3][0]
-    sat = dict(coarse=(ns, ns, ns, GALAXY_RADII["r_sys"], 1.0),
-               medium=(ns, ns, ns, 0.5, 1.0), fine=(ns, ns, ns, 0.125, 1.0),
-               r_core=0.125, r_out=0.5, centre=(R_A, 0.0, 0.0), recentre=True)
-    allpos = np.concatenate([pos, ps], axis=1)
-    allvel = np.concatenate([vel, vs], axis=1)
-    allm = np.concatenate([m, ms])
-    gal = np.concatenate([np.zeros(pos.shape[1], np.int32), np.ones(n_sat, np.int32)])
-    allpos, allvel, allm, gal = synth.scramble(synth.rng_for(seed_id, 9), allpos, allvel, allm, gal)
+    c, s = np.cos(phase), np.sin(phase)
+    centre = (R_A * c, R_A * s, 0.0)
+    ps = ps + np.array(centre)[:, None]
+    vs = vs + np.array([[-s * v_apo * np.cos(inc)], [c * v_apo * np.cos(inc)], [v_apo * np.sin(inc)]])
+    spec = dict(coarse=(ns, ns, ns, GALAXY_RADII["r_sys"], 1.0),
+                medium=(ns, ns, ns, 10 * a, 1.0), fine=(ns, ns, ns, 2.5 * a, 1.0),
+                r_core=2.5 * a, r_out=10 * a, centre=centre, recentre=True)
+    return ps, vs, ms, spec
+
+
+def _with_satellites(pos, vel, m, gal_spec, sats, seed_id, precision, name, steps):
+    allpos, allvel, allm = [pos], [vel], [m]
+    gal = [np.zeros(pos.shape[1], np.int32)]
+    specs = [gal_spec]
+    for k, (ps, vs, ms, spec) in enumerate(sats):
+        allpos.append(ps); allvel.append(vs); allm.append(ms)
+        gal.append(np.full(ps.shape[1], k + 1, np.int32))
+        specs.append(spec)
+    allpos, allvel, allm, gal = synth.scramble(synth.rng_for(seed_id, 9), np.concatenate(allpos, axis=1),
+                                               np.concatenate(allvel, axis=1), np.concatenate(allm),
+                                               np.concatenate(gal))
     return dict(
-        name=name, precision=precision, dt=0.01, steps=500,
+        name=name, precision=precision, dt=0.01, steps=steps,
         system=dict(r_sys=GALAXY_RADII["r_sys"], sys_centre=(0.0, 0.0, 0.0), G=1.0, h000=1.0),
-        galaxies=[_galaxy_spec(n_c, n_m, n_f), sat],
-        pos=allpos, vel=allvel, m=allm, gal=gal)
+        galaxies=specs, pos=allpos, vel=allvel, m=allm, gal=gal)
+
+
+def merger(n_gal=4_000_000, n_sat=100_000, grids=((128,), (128,), (256, 256, 32), (64,)),
+           seed_id=2, precision="fp32", name="merger_4m", q_m=0.25):
+    """Galaxy plus a Plummer satellite (M = 0.1 M_disc, a = 0.05) at apocentre
+    8 R_d on an orbit of eccentricity 0.5, inclined 30 degrees."""
+    pos, vel, m = _galaxy_particles(n_gal, seed_id)
+    sat = _satellite(pos, m, n_sat, synth.rng_for(seed_id, 4), 0.1, 0.05, 8.0, 0.0, 30.0, grids[3][0])
+    return _with_satellites(pos, vel, m, _galaxy_spec(grids[0][0], grids[1][0], grids[2], q_m=q_m), [sat],
+                            seed_id, precision, name, 500)
+
+
+def merger_4m(precision="fp32"):
+    return merger(precision=precision)
+
+
+def large_16m(precision="fp32", seed_id=4):
+    """16M-particle galaxy (6M disc, 2M bulge, 8M halo, the model of
+    galaxy_1m) on 256^3, 256^3 (q = 1/4) and 256x256x64 grids, plus two
+    250k-particle Plummer satellites (M = 0.1, a = 0.05) with 128^3 grids."""
+    pos, vel, m = synth.galaxy(6_000_000, 2_000_000, 8_000_000, synth.rng_for(seed_id, 1),
+                               synth.rng_for(seed_id, 2), synth.rng_for(seed_id, 3))
+    sats = [_satellite(pos, m, 250_000, synth.rng_for(seed_id, 4), 0.1, 0.05, 8.0, 0.0, 30.0, 128),
+            _satellite(pos, m, 250_000, synth.rng_for(seed_id, 5), 0.1, 0.05, 6.0, 2.0, -45.0, 128)]
+    return _with_satellites(pos, vel, m, _galaxy_spec(256, 256, (256, 256, 64)), sats, seed_id, precision,
+                            "large_16m", 1000)
+
+
+def merger_small(precision="fp32", seed_id=12):
+    """Two galaxies at test size: the small galaxy (24k particles) and a 4k
+    Plummer satellite with its own 16^3 grids, on an inclined orbit."""
+    return merger(n_gal=24_000, n_sat=4_000, grids=((32,), (32,), (32, 32, 8), (16,)), seed_id=seed_id,
+                  precision=precision, name="merger_small", q_m=0.8)
+
+
+def big_box(n=1_000_000, N=256, precision="fp32", seed_id=13):
+    """Plummer sphere (M = 1, a = 1, r <= 10) on one N^3 grid of side 24:
+    the largest transform length (2N = 512) on every axis."""
+    rng = synth.rng_for(seed_id, 0)
+    pos, vel, m = synth.plummer(n, rng, M=1.0, a=1.0, r_trunc=10.0)
+    R = 12.0 * (N - 4) / N
+    return dict(
+        name=f"box{N}", precision=precision, dt=0.01, steps=10,
+        system=dict(r_sys=11.0, sys_centre=(0.0, 0.0, 0.0), G=1.0, h000=1.0),
+        galaxies=[dict(coarse=(N, N, N, R, 1.0), medium=None, fine=None,
+                       r_core=0.0, r_out=0.0, centre=(0.0, 0.0, 0.0), recentre=False)],
+        pos=pos, vel=vel, m=m, gal=np.zeros(pos.shape[1], dtype=np.int32))
+
+
+def galaxy_256(n_total=2_000_000, precision="fp32", seed_id=14):
+    """The disc-bulge-halo galaxy on the large grids: coarse and medium 256^3,
+    fine 256x256x64 (all padded to 512 along x and y)."""
+    return galaxy(n_total, 256, 256, (256, 256, 64), seed_id=seed_id, precision=precision,
+                  name="galaxy_256", q_m=0.25)
 
 
 def mass_bound(m):

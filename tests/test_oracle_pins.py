@@ -307,3 +307,14 @@ def test_planted_mistake_in_combination_rule_is_caught(monkeypatch):
                         lambda reg: (4, 5) if reg == 1 else orig(reg))
     with pytest.raises(AssertionError):
         test_nested_force_matches_plummer_field()
+
+
+def test_potential_at_equals_direct_sum():
+    """The sampled form of Eq. (eq:poisson) used for the large-grid checks
+    is the plain sum itself at every cell."""
+    g = O.Geometry(8, 16, 4, 0.3, 0.15)
+    rho = _random_rho(g, 40)
+    full = O.potential_direct(rho, g, 1.3, 1.0)
+    cells = [(k, j, i) for k in range(4) for j in (0, 5, 15) for i in (0, 3, 7)]
+    got = O.potential_at(rho, g, 1.3, 1.0, cells)
+    assert np.allclose(got, [full[c] for c in cells], rtol=1e-13, atol=0)
