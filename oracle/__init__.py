@@ -4,6 +4,7 @@ TEST INFRASTRUCTURE: imported only by tests/, the smoke check and the
 benchmark's CPU-baseline leg; the product path never imports it.
 """
 from .pm_oracle import *  # noqa: F401,F403
+from .pm_cic import *  # noqa: F401,F403
 from .pm_oracle import Geometry, Galaxy, System, State, cell_length
 import numpy as np
 
