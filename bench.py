@@ -65,16 +65,64 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(phase):
-    """DRAM bytes per launch of a phase from the committed ncu summary, if it
-    was taken on the current kernel sources (else None)."""
+def ncu_traffic(phase, workload):
+    """DRAM bytes per step of a phase from the committed ncu summary, if it
+    was taken on the current kernel sources and this workload (else None)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    if d.get("source_hash") != kernel_source_hash():
+    if d.get("source_hash") != kernel_source_hash() or d.get("workload") != workload:
         return None
     return d.get("phases", {}).get(phase)
+
+
+def fp64_comparison(w, host, m32, n_steps):
+    """The same workload through the FP64 instantiation of the same kernels:
+    its step time, and the FP32 path's force error against it at the
+    initial state (FP64 forces match the oracle to ~1e-14)."""
+    import torch
+    from paper_1210_1736_gb300 import pm
+    from paper_1210_1736_gb300.workloads import mass_bound
+    dt = w["dt"]
+    mb = mass_bound(m32)
+    w32 = dict(w, precision="fp32")
+    w64 = dict(w, precision="fp64")
+    ctx32 = pm.Context(w32, mb)
+    p32 = pm.Particles(host["pos"], host["vel"], m32, w["gal"])
+    ctx32.deposit(p32)
+    ctx32.solve()
+    a32 = [a.double() for a in ctx32.force(p32)]
+    ctx32.close()
+    del p32
+    ctx64 = pm.Context(w64, mb)
+    p64 = pm.Particles(host["pos"].astype(np.float64), host["vel"].astype(np.float64),
+                       m32.astype(np.float64), w["gal"], precision="fp64")
+    ctx64.deposit(p64)
+    ctx64.solve()
+    a64 = ctx64.force(p64)
+    torch.cuda.synchronize()
+    live = (p64.flags & 1) == 0
+    d2 = sum(((x - y)[live] ** 2) for x, y in zip(a32, a64))
+    f2 = sum((y[live] ** 2) for y in a64)
+    rms_ref = float(torch.sqrt(f2.mean()))
+    rms = float(torch.sqrt(d2.mean())) / rms_ref
+    mx = float(torch.sqrt(d2.max())) / rms_ref
+    ctx64.kick(p64, -0.5 * dt)
+    ctx64.step(p64, dt, 2)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    ctx64.step(p64, dt, n_steps)
+    e1.record()
+    torch.cuda.synchronize()
+    ms64 = e0.elapsed_time(e1) / n_steps
+    ctx64.close()
+    del p64, a64, a32
+    torch.cuda.empty_cache()
+    return {"ms_per_step": ms64, "steps": n_steps, "fp32_force_err_rms": rms, "fp32_force_err_max": mx,
+            "note": "FP64 build of the same kernels (graph-replayed steps); force errors relative to the "
+                    "RMS force, over live particles at the initial state"}
 
 
 class Clocks:
@@ -174,8 +222,9 @@ def run_ours(args):
     w = getattr(W, args.workload)()
     dt = w["dt"]
     m32 = w["m"].astype(np.float32)
-    ctx = pm.Context(w, mass_bound(m32))
     host = dict(pos=w["pos"].astype(np.float32), vel=w["vel"].astype(np.float32), m=m32, gal=w["gal"])
+    fp64 = fp64_comparison(w, host, m32, args.fp64_steps) if args.fp64_steps > 0 else None
+    ctx = pm.Context(w, mass_bound(m32))
     parts = pm.Particles(host["pos"], host["vel"], m32, w["gal"])
     n = parts.n
     K, Wm = args.steps, args.warmup
@@ -260,7 +309,7 @@ def run_ours(args):
                    "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": ncu_traffic(dom)},
+                     "traffic": ncu_traffic(dom, args.workload)},
         "fft_convolve": {"gbs": conv_gbs, "frac": conv_gbs / peak, "ms_per_step": conv_ms},
         "phase_ms_per_step": phase_ms,
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -268,6 +317,9 @@ def run_ours(args):
         "gpu_launches": launches_per_step(ctx, True) * K,
         "clocks": clocks,
     }
+    if fp64 is not None:
+        fp64["speedup_fp32"] = fp64["ms_per_step"] / (ms / K)
+        line["fp64_path"] = fp64
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_rate(w, args.workload, budget_s=25.0, max_steps=3)
     if world > 1:
@@ -323,6 +375,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOAD_DESC))
+    ap.add_argument("--fp64-steps", type=int, default=5,
+                    help="steps timed on the FP64 instantiation for comparison (0: skip)")
     ap.add_argument("--sort-every", type=int, default=10,
                     help="re-sort particles by cell every k steps inside the timed steps (0: never)")
     args = ap.parse_args()
