@@ -190,6 +190,44 @@ int pm_set_sort_interval(pm_ctx *ctx, int32_t k);
 int pm_step_timed(pm_ctx *ctx, const pm_particles *p, double dt, int32_t nsteps,
                   float *ms_out);
 
+/* ---- CIC variant for differentiable runs ------------------------------
+ * Not the paper's scheme: nearest-grid-point assignment (Eq. eqn:cell) has
+ * zero position gradient almost everywhere, so gradients of trajectories use
+ * cloud-in-cell instead.  Each particle spreads its mass over the 8 cells
+ * around it with trilinear weights W; the grid field is the central
+ * difference of the potential (the first term of Eq. eqn:diff) at every
+ * cell; the acceleration is that field interpolated with the same weights.
+ * Regions, mass sets, the convolution and the combination rule (Sec. 2.1)
+ * are those of the NGP step; the grid centres are not moved (no recentring),
+ * so they are constants of the map.  The lower CIC cell along an axis is
+ * a - 1 (fraction t + 1) when t = Delta/l < 0, else a (fraction t), with a
+ * the NGP cell and Delta the offset from its centre.  Enqueued on the
+ * context's stream unless stated otherwise.
+ *
+ * pm_cic_deposit: lost test as pm_deposit, then int64 fixed-point CIC mass
+ * (each of the 8 cell shares rounded separately) into the five sets.  Use
+ * pm_solve afterwards.
+ * pm_cic_force: ax, ay, az (device, context precision, n) = CIC acceleration
+ * from the current potentials; lost particles get 0.
+ * pm_cic_kick_drift: v += dt_kick a; x += dt_drift v (live particles).
+ * pm_cic_vjp: vector-Jacobian product of the CIC acceleration at the
+ * current positions and masses, whose potentials must be the current ones
+ * (pm_cic_deposit + pm_solve at these positions): with u = (ux, uy, uz) one
+ * cotangent per particle, adds u^T da/dx to (gx, gy, gz) and u^T da/dm to
+ * gm (device arrays, context precision, n; caller-owned, accumulated into).
+ * Both the particle's own interpolation weights and, through the
+ * (symmetric) convolution, every other particle's mass assignment
+ * contribute.  The adjoint densities are int64 fixed point with a scale
+ * chosen from max |u| (one device-to-host read; the call synchronises), so
+ * the result does not depend on the order of the atomics.  Afterwards the
+ * density and potential buffers hold adjoint fields: deposit and solve again
+ * before the next force.  PM_E_ARG for a non-finite cotangent. */
+int pm_cic_deposit(pm_ctx *ctx, const pm_particles *p);
+int pm_cic_force(pm_ctx *ctx, const pm_particles *p, void *ax, void *ay, void *az);
+int pm_cic_kick_drift(pm_ctx *ctx, const pm_particles *p, double dt_kick, double dt_drift);
+int pm_cic_vjp(pm_ctx *ctx, const pm_particles *p, const void *ux, const void *uy, const void *uz,
+               void *gx, void *gy, void *gz, void *gm);
+
 /* Allocation-free potential of one isolated grid.  The paper has no
  * counterpart: this entry point exists for callers that cannot call
  * cudaMalloc (a host application whose device memory is pre-partitioned by

@@ -269,7 +269,9 @@ template <typename T> int upload_twiddles(pm_ctx *c) {
 // ---- the passes of pm_solve --------------------------------------------------
 enum { PASS_XFWD = 0, PASS_YFWD, PASS_ZCONV, PASS_YINV, PASS_XINV, NPASS };
 
-template <typename T> int launch_pass(pm_ctx *c, int pass, cudaStream_t st, int only = -1) {
+// shift: fixed-point scale of the input densities (2^-shift); the mass scale
+// unless an adjoint solve passes its own.
+template <typename T> int launch_pass(pm_ctx *c, int pass, cudaStream_t st, int only = -1, int shift = INT_MIN) {
     for (int gi = 0; gi < (int)c->geos.size(); ++gi) {
         if (only >= 0 && gi != only) continue;
         const GeoBuf &gb = c->geos[gi];
@@ -284,7 +286,7 @@ template <typename T> int launch_pass(pm_ctx *c, int pass, cudaStream_t st, int 
             a.phi_sum = c->phi[pr.gi][pr.a];
             a.hhat = gb.hhat;
             a.nx = g.nx; a.ny = g.ny; a.nz = g.nz;
-            a.scale = std::ldexp(1.0, -c->shift);
+            a.scale = std::ldexp(1.0, -(shift == INT_MIN ? c->shift : shift));
             a.err = c->d_err;
             cudaError_t e;
             switch (pass) {
@@ -318,10 +320,10 @@ template <typename T> int launch_pass(pm_ctx *c, int pass, cudaStream_t st, int 
 // With ev (phase timing) the passes run pass by pass on st; otherwise each
 // geometry's chain of five passes runs on its own branch stream (forked from
 // and joined back to st), so independent geometries overlap on the GPU.
-template <typename T> int enqueue_solve(pm_ctx *c, cudaStream_t st, cudaEvent_t *ev) {
+template <typename T> int enqueue_solve(pm_ctx *c, cudaStream_t st, cudaEvent_t *ev, int shift = INT_MIN) {
     if (ev || c->geos.size() < 2) {
         for (int pass = 0; pass < NPASS; ++pass) {
-            PM_TRY(launch_pass<T>(c, pass, st));
+            PM_TRY(launch_pass<T>(c, pass, st, -1, shift));
             if (ev) PM_CK(cudaEventRecord(ev[pass], st));
         }
         return PM_OK;
@@ -330,7 +332,7 @@ template <typename T> int enqueue_solve(pm_ctx *c, cudaStream_t st, cudaEvent_t 
     for (int gi = 0; gi < (int)c->geos.size(); ++gi) {
         cudaStream_t b = c->branch[gi];
         PM_CK(cudaStreamWaitEvent(b, c->ev_fork, 0));
-        for (int pass = 0; pass < NPASS; ++pass) PM_TRY(launch_pass<T>(c, pass, b, gi));
+        for (int pass = 0; pass < NPASS; ++pass) PM_TRY(launch_pass<T>(c, pass, b, gi, shift));
         PM_CK(cudaEventRecord(c->ev_join[gi], b));
         PM_CK(cudaStreamWaitEvent(st, c->ev_join[gi], 0));
     }
@@ -468,6 +470,60 @@ template <typename T> int step_timed_impl(pm_ctx *c, const pm_particles *p, doub
     }
     for (auto &e : ev) cudaEventDestroy(e);
     return rc;
+}
+
+// ---- CIC variant (differentiable runs) -------------------------------------
+template <typename T> int cic_deposit_impl(pm_ctx *c, const pm_particles *p) {
+    PM_CK(cudaMemsetAsync(c->rho_all, 0, c->rho_bytes, c->user));
+    PM_CK(pm_launch_cic_deposit<T>(part_k<T>(p), c->hs, c->d_cen, c->user));
+    return PM_OK;
+}
+
+template <typename T> int cic_field_impl(pm_ctx *c, int mode, const pm_particles *p, double dtk, double dtd,
+                                         void *ox, void *oy, void *oz) {
+    PM_CK(pm_launch_cic_field<T>(mode, part_k<T>(p), c->hs, c->d_cen, dtk, dtd, (T *)ox, (T *)oy, (T *)oz, nullptr,
+                                 nullptr, nullptr, 0.0, c->user));
+    return PM_OK;
+}
+
+// Largest (2 c_gx + c_gz) = 1/l_xy + 1/(2 l_z) over the grids: bounds one
+// particle's adjoint density in any cell per unit |u|.
+double cic_coef_bound(const SysK &hs) {
+    double b = 0;
+    for (int g = 0; g < hs.ngal; ++g) {
+        const GeomK *gs[3] = {&hs.gal[g].fine, &hs.gal[g].med, &hs.gal[g].coarse};
+        for (const GeomK *k : gs)
+            if (k->nx) b = std::max(b, 2.0 * k->c_gx + k->c_gz);
+    }
+    return b;
+}
+
+template <typename T> int cic_vjp_impl(pm_ctx *c, const pm_particles *p, const void *ux, const void *uy,
+                                       const void *uz, void *gx, void *gy, void *gz, void *gm) {
+    const PartK<T> pk = part_k<T>(p);
+    const T *u[3] = {(const T *)ux, (const T *)uy, (const T *)uz};
+    // direct term, with the forward potentials still in place
+    PM_CK(pm_launch_cic_field<T>(2, pk, c->hs, c->d_cen, 0.0, 0.0, (T *)gx, (T *)gy, (T *)gz, u[0], u[1], u[2], 0.0,
+                                 c->user));
+    // fixed-point scale of the adjoint densities: |cell sum| <= n max|u| bound
+    PM_CK(cudaMemsetAsync(c->d_cnt, 0, sizeof(unsigned long long), c->user));
+    PM_CK(pm_launch_cic_umax<T>(pk, u[0], u[1], u[2], (unsigned *)c->d_cnt, c->user));
+    unsigned bits = 0;
+    PM_CK(cudaMemcpyAsync(&bits, c->d_cnt, sizeof(bits), cudaMemcpyDeviceToHost, c->user));
+    PM_CK(cudaStreamSynchronize(c->user));
+    float umax;
+    std::memcpy(&umax, &bits, sizeof(umax));
+    if (!std::isfinite(umax)) return fail(PM_E_ARG, "cotangent has a non-finite entry");
+    if (umax == 0.f) return check_device_error(c);
+    const double bound = 1.01 * (double)p->n * (double)umax * cic_coef_bound(c->hs);
+    int sa = 61 - ceil_log2(bound);
+    sa = std::min(120, std::max(-100, sa));
+    PM_CK(cudaMemsetAsync(c->rho_all, 0, c->rho_bytes, c->user));
+    PM_CK(pm_launch_cic_field<T>(3, pk, c->hs, c->d_cen, 0.0, 0.0, nullptr, nullptr, nullptr, u[0], u[1], u[2],
+                                 std::ldexp(1.0, sa), c->user));
+    PM_TRY(enqueue_solve<T>(c, c->user, nullptr, sa));
+    PM_CK(pm_launch_cic_gather<T>(pk, c->hs, c->d_cen, (T *)gx, (T *)gy, (T *)gz, (T *)gm, c->user));
+    return check_device_error(c);
 }
 
 template <typename T> int force_impl(pm_ctx *c, int mode, const pm_particles *p, double dt, void *ax, void *ay,
@@ -865,6 +921,36 @@ int pm_diagnostics(pm_ctx *c, const pm_particles *p, double dt, double *out) {
     PM_CK(cudaStreamSynchronize(c->user));
     for (int k = 0; k < 7; ++k) out[k] = h[k];
     return check_device_error(c);
+}
+
+int pm_cic_deposit(pm_ctx *c, const pm_particles *p) {
+    if (!c) return fail(PM_E_ARG, "ctx is NULL");
+    PM_TRY(check_particles(p));
+    return PM_DISPATCH(c, cic_deposit_impl, c, p);
+}
+
+int pm_cic_force(pm_ctx *c, const pm_particles *p, void *ax, void *ay, void *az) {
+    if (!c) return fail(PM_E_ARG, "ctx is NULL");
+    PM_TRY(check_particles(p));
+    if (p->n > 0 && (!ax || !ay || !az)) return fail(PM_E_ARG, "acceleration array is NULL");
+    return PM_DISPATCH(c, cic_field_impl, c, 1, p, 0.0, 0.0, ax, ay, az);
+}
+
+int pm_cic_kick_drift(pm_ctx *c, const pm_particles *p, double dt_kick, double dt_drift) {
+    if (!c) return fail(PM_E_ARG, "ctx is NULL");
+    PM_TRY(check_particles(p));
+    if (!std::isfinite(dt_kick) || !std::isfinite(dt_drift)) return fail(PM_E_ARG, "dt not finite");
+    return PM_DISPATCH(c, cic_field_impl, c, 0, p, dt_kick, dt_drift, nullptr, nullptr, nullptr);
+}
+
+int pm_cic_vjp(pm_ctx *c, const pm_particles *p, const void *ux, const void *uy, const void *uz, void *gx, void *gy,
+               void *gz, void *gm) {
+    if (!c) return fail(PM_E_ARG, "ctx is NULL");
+    PM_TRY(check_particles(p));
+    if (p->n > 0 && (!ux || !uy || !uz || !gx || !gy || !gz || !gm))
+        return fail(PM_E_ARG, "cotangent or gradient array is NULL");
+    if (p->n == 0) return PM_OK;
+    return PM_DISPATCH(c, cic_vjp_impl, c, p, ux, uy, uz, gx, gy, gz, gm);
 }
 
 int pm_get_density(pm_ctx *c, int32_t gal, int32_t set, int64_t *host_out) {

@@ -3,6 +3,7 @@
 #pragma once
 
 #include "pm_passes.cuh"
+#include "pm_particle.cuh"
 
 namespace pmk {
 
@@ -11,31 +12,6 @@ namespace pmk {
 // parameter (read through the constant cache, no staging); the centres of
 // grids 1-3 are read from device memory.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ size_t cell_off(const GeomK &g, const Cell &c) {
-    return ((size_t)c.k * g.ny + c.j) * g.nx + c.i;
-}
-
-struct Cen1 {
-    double c[3];
-    float hi[3], lo[3];
-};
-__device__ __forceinline__ Cen1 load_cen(const CenK *cen, int g) {
-    Cen1 r;
-    const CenK *cs = cen;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        r.c[k] = __ldg(&cs->c[g][k]);
-        r.hi[k] = __ldg(&cs->hi[g][k]);
-        r.lo[k] = __ldg(&cs->lo[g][k]);
-    }
-    return r;
-}
-
-// Offset used for Delta in Eq. (eqn:diff): the canonical FP32 offset in FP32
-// contexts, the exact FP64 difference in FP64 contexts.
-__device__ __forceinline__ float rel_off(float x, double, float chi, float clo) { return pm_off32s(x, chi, clo); }
-__device__ __forceinline__ double rel_off(double x, double c, float, float) { return __dsub_rn(x, c); }
-
 // Adds q (two's complement int64) to *addr for every lane with active set;
 // lanes that target the same address are combined first (exact: the sum is
 // taken mod 2^64 from four 16-bit chunk sums), so a warp of particles in one
@@ -147,14 +123,6 @@ __device__ __forceinline__ void stencil(const GeomK &g, const T *__restrict__ P1
     acc[1] += gy + hyy * dy + mxy * dx + myz * dz;
     acc[2] += gz + hzz * dz + mxz * dx + myz * dy;
     if (phi) *phi += p0 + gx * dx + gy * dy + gz * dz;
-}
-
-// Offset of a particle from the centre of its cell (Delta of Eq. eqn:diff).
-template <typename T>
-__device__ __forceinline__ void cell_delta(const GeomK &g, const Cell &cl, T rx, T ry, T rz, T &dx, T &dy, T &dz) {
-    dx = rx - (T)(cl.i - (g.nx >> 1)) * (T)g.lxy;
-    dy = ry - (T)(cl.j - (g.ny >> 1)) * (T)g.lxy;
-    dz = rz - (T)(cl.k - (g.nz >> 1)) * (T)g.lz;
 }
 
 __device__ __forceinline__ double warp_sum(double v) {

@@ -57,6 +57,25 @@ cudaError_t pm_launch_sort(const PartK<T> &p, const PartK<T> &scratch, const Sys
                            const SortK &so, unsigned *count, unsigned *key, unsigned *rank, unsigned *bsum,
                            long long *perm, cudaStream_t st);
 
+// CIC variant (differentiable runs).  field modes: 0 kick (dtk) and drift
+// (dtd), 1 write accelerations to o*, 2 add the direct term of the adjoint
+// for cotangent u to o*, 3 spread u into the density slots as int64 with
+// scale qs (adjoint densities).
+template <typename T>
+cudaError_t pm_launch_cic_deposit(const PartK<T> &p, const SysK &sk, const CenK *cen, cudaStream_t st);
+template <typename T>
+cudaError_t pm_launch_cic_field(int mode, const PartK<T> &p, const SysK &sk, const CenK *cen, double dtk, double dtd,
+                                T *ox, T *oy, T *oz, const T *ux, const T *uy, const T *uz, double qs,
+                                cudaStream_t st);
+// Adds the field term of the adjoint (from the adjoint solve's potentials).
+template <typename T>
+cudaError_t pm_launch_cic_gather(const PartK<T> &p, const SysK &sk, const CenK *cen, T *gx, T *gy, T *gz, T *gm,
+                                 cudaStream_t st);
+// max |u| over live particles into *out (float bits, atomicMax; zero it first).
+template <typename T>
+cudaError_t pm_launch_cic_umax(const PartK<T> &p, const T *ux, const T *uy, const T *uz, unsigned *out,
+                               cudaStream_t st);
+
 // FP64 H-hat construction (precision independent) and storage conversion.
 cudaError_t pm_green_octant(double *h, int nx, int ny, int nz, double q, double h000, cudaStream_t st);
 cudaError_t pm_axis_transform(const double *in, double *out, const double *cmat, int n1,

@@ -74,6 +74,10 @@ _SIGS.update({
     "pm_set_sort_interval": (C.c_int, [_vp, C.c_int32]),
     "pm_potential_static": (C.c_int, [_vp, _vp, C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_double,
                                       C.c_double, C.c_double, C.c_int32, C.c_int32, _vp]),
+    "pm_cic_deposit": (C.c_int, [_vp, _P(pm_particles)]),
+    "pm_cic_force": (C.c_int, [_vp, _P(pm_particles), _vp, _vp, _vp]),
+    "pm_cic_kick_drift": (C.c_int, [_vp, _P(pm_particles), C.c_double, C.c_double]),
+    "pm_cic_vjp": (C.c_int, [_vp, _P(pm_particles), _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
 })
 
 _lib = None
@@ -173,6 +177,24 @@ class Particles:
         self.flags = torch.zeros(len(self.m), dtype=torch.int32, device=device)
         self.n = len(self.m)
 
+    @classmethod
+    def from_tensors(cls, pos, vel, m, gal, flags=None):
+        """Wraps device tensors without copying: pos and vel (3, n) contiguous,
+        m (n,), gal int32 (n,), flags int32 (n,) (zeros if None)."""
+        import torch
+        self = cls.__new__(cls)
+        self.dtype = pos.dtype
+        self.x, self.y, self.z = pos[0], pos[1], pos[2]
+        self.vx, self.vy, self.vz = vel[0], vel[1], vel[2]
+        self.m = m
+        self.gal = gal
+        self.flags = torch.zeros(m.shape[0], dtype=torch.int32, device=m.device) if flags is None else flags
+        self.n = int(m.shape[0])
+        for t in (self.x, self.y, self.z, self.vx, self.vy, self.vz, self.m, self.gal, self.flags):
+            if not t.is_contiguous():
+                raise ValueError("particle arrays must be contiguous")
+        return self
+
     def struct(self):
         p = pm_particles()
         for k in ("x", "y", "z", "vx", "vy", "vz", "m", "gal", "flags"):
@@ -240,6 +262,28 @@ class Context:
 
     def kick(self, p, dt):
         _check(lib().pm_kick(self.h, C.byref(p.struct()), float(dt)))
+
+    # CIC variant (differentiable runs; see include/pm.h)
+    def cic_deposit(self, p):
+        _check(lib().pm_cic_deposit(self.h, C.byref(p.struct())))
+
+    def cic_force(self, p):
+        import torch
+        a = [torch.empty(p.n, dtype=p.dtype, device=p.x.device) for _ in range(3)]
+        _check(lib().pm_cic_force(self.h, C.byref(p.struct()), a[0].data_ptr(), a[1].data_ptr(), a[2].data_ptr()))
+        return a
+
+    def cic_kick_drift(self, p, dt_kick, dt_drift):
+        _check(lib().pm_cic_kick_drift(self.h, C.byref(p.struct()), float(dt_kick), float(dt_drift)))
+
+    def cic_vjp(self, p, u, gx, gm):
+        """Adds u^T da/dx to gx (3, n) and u^T da/dm to gm (n,) (device
+        tensors of the context precision); u is (3, n)."""
+        for t in (u, gx, gm):
+            if not t.is_contiguous() or t.dtype != p.dtype:
+                raise ValueError("cotangent and gradient tensors must be contiguous, context precision")
+        _check(lib().pm_cic_vjp(self.h, C.byref(p.struct()), u[0].data_ptr(), u[1].data_ptr(), u[2].data_ptr(),
+                                gx[0].data_ptr(), gx[1].data_ptr(), gx[2].data_ptr(), gm.data_ptr()))
 
     def step(self, p, dt, nsteps=1):
         _check(lib().pm_step(self.h, C.byref(p.struct()), float(dt), int(nsteps)))

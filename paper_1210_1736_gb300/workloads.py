@@ -52,24 +52,34 @@ def plummer32(seed_id=0):
         pos=pos, vel=vel, m=m, gal=np.zeros(n, dtype=np.int32))
 
 
+COMP_DISC, COMP_BULGE, COMP_HALO, COMP_SATELLITE = 0, 1, 2, 3
+
+
+def _components(nd, nb, nh):
+    return np.concatenate([np.full(nd, COMP_DISC, np.int8), np.full(nb, COMP_BULGE, np.int8),
+                           np.full(nh, COMP_HALO, np.int8)])
+
+
 def _galaxy_particles(n_total, seed_id):
+    """Disc, bulge and halo particles (40/10/50 per cent) and their component
+    labels, unscrambled."""
     nd, nb = int(round(0.4 * n_total)), int(round(0.1 * n_total))
     nh = n_total - nd - nb
     pos, vel, m = synth.galaxy(nd, nb, nh, synth.rng_for(seed_id, 1),
                                synth.rng_for(seed_id, 2), synth.rng_for(seed_id, 3))
-    return pos, vel, m
+    return pos, vel, m, _components(nd, nb, nh)
 
 
 def galaxy(n_total=1_000_000, n_c=128, n_m=128, n_f=(128, 128, 32), seed_id=1,
            precision="fp32", name=None, q_m=0.25):
-    pos, vel, m = _galaxy_particles(n_total, seed_id)
-    pos, vel, m = synth.scramble(synth.rng_for(seed_id, 9), pos, vel, m)
+    pos, vel, m, comp = _galaxy_particles(n_total, seed_id)
+    pos, vel, m, comp = synth.scramble(synth.rng_for(seed_id, 9), pos, vel, m, comp)
     n = pos.shape[1]
     return dict(
         name=name or f"galaxy_{n_total}", precision=precision, dt=0.01, steps=100,
         system=dict(r_sys=GALAXY_RADII["r_sys"], sys_centre=(0.0, 0.0, 0.0), G=1.0, h000=1.0),
         galaxies=[_galaxy_spec(n_c, n_m, n_f, q_m=q_m)],
-        pos=pos, vel=vel, m=m, gal=np.zeros(n, dtype=np.int32))
+        pos=pos, vel=vel, m=m, gal=np.zeros(n, dtype=np.int32), comp=comp)
 
 
 def galaxy_1m(precision="fp32"):
@@ -103,31 +113,32 @@ def _satellite(pos_g, m_g, n_sat, rng, M, a, R_A, phase, inc_deg, ns, e=0.5):
     return ps, vs, ms, spec
 
 
-def _with_satellites(pos, vel, m, gal_spec, sats, seed_id, precision, name, steps):
-    allpos, allvel, allm = [pos], [vel], [m]
+def _with_satellites(pos, vel, m, comp, gal_spec, sats, seed_id, precision, name, steps):
+    allpos, allvel, allm, allc = [pos], [vel], [m], [comp]
     gal = [np.zeros(pos.shape[1], np.int32)]
     specs = [gal_spec]
     for k, (ps, vs, ms, spec) in enumerate(sats):
         allpos.append(ps); allvel.append(vs); allm.append(ms)
+        allc.append(np.full(ps.shape[1], COMP_SATELLITE, np.int8))
         gal.append(np.full(ps.shape[1], k + 1, np.int32))
         specs.append(spec)
-    allpos, allvel, allm, gal = synth.scramble(synth.rng_for(seed_id, 9), np.concatenate(allpos, axis=1),
-                                               np.concatenate(allvel, axis=1), np.concatenate(allm),
-                                               np.concatenate(gal))
+    allpos, allvel, allm, gal, allc = synth.scramble(
+        synth.rng_for(seed_id, 9), np.concatenate(allpos, axis=1), np.concatenate(allvel, axis=1),
+        np.concatenate(allm), np.concatenate(gal), np.concatenate(allc))
     return dict(
         name=name, precision=precision, dt=0.01, steps=steps,
         system=dict(r_sys=GALAXY_RADII["r_sys"], sys_centre=(0.0, 0.0, 0.0), G=1.0, h000=1.0),
-        galaxies=specs, pos=allpos, vel=allvel, m=allm, gal=gal)
+        galaxies=specs, pos=allpos, vel=allvel, m=allm, gal=gal, comp=allc)
 
 
 def merger(n_gal=4_000_000, n_sat=100_000, grids=((128,), (128,), (256, 256, 32), (64,)),
-           seed_id=2, precision="fp32", name="merger_4m", q_m=0.25):
+           seed_id=2, precision="fp32", name="merger_4m", q_m=0.25, sat_m=0.1, steps=500, r_apo=8.0):
     """Galaxy plus a Plummer satellite (M = 0.1 M_disc, a = 0.05) at apocentre
     8 R_d on an orbit of eccentricity 0.5, inclined 30 degrees."""
-    pos, vel, m = _galaxy_particles(n_gal, seed_id)
-    sat = _satellite(pos, m, n_sat, synth.rng_for(seed_id, 4), 0.1, 0.05, 8.0, 0.0, 30.0, grids[3][0])
-    return _with_satellites(pos, vel, m, _galaxy_spec(grids[0][0], grids[1][0], grids[2], q_m=q_m), [sat],
-                            seed_id, precision, name, 500)
+    pos, vel, m, comp = _galaxy_particles(n_gal, seed_id)
+    sat = _satellite(pos, m, n_sat, synth.rng_for(seed_id, 4), sat_m, 0.05, r_apo, 0.0, 30.0, grids[3][0])
+    return _with_satellites(pos, vel, m, comp, _galaxy_spec(grids[0][0], grids[1][0], grids[2], q_m=q_m), [sat],
+                            seed_id, precision, name, steps)
 
 
 def merger_4m(precision="fp32"):
@@ -140,17 +151,27 @@ def large_16m(precision="fp32", seed_id=4):
     250k-particle Plummer satellites (M = 0.1, a = 0.05) with 128^3 grids."""
     pos, vel, m = synth.galaxy(6_000_000, 2_000_000, 8_000_000, synth.rng_for(seed_id, 1),
                                synth.rng_for(seed_id, 2), synth.rng_for(seed_id, 3))
+    comp = _components(6_000_000, 2_000_000, 8_000_000)
     sats = [_satellite(pos, m, 250_000, synth.rng_for(seed_id, 4), 0.1, 0.05, 8.0, 0.0, 30.0, 128),
             _satellite(pos, m, 250_000, synth.rng_for(seed_id, 5), 0.1, 0.05, 6.0, 2.0, -45.0, 128)]
-    return _with_satellites(pos, vel, m, _galaxy_spec(256, 256, (256, 256, 64)), sats, seed_id, precision,
+    return _with_satellites(pos, vel, m, comp, _galaxy_spec(256, 256, (256, 256, 64)), sats, seed_id, precision,
                             "large_16m", 1000)
 
 
-def merger_small(precision="fp32", seed_id=12):
+def adjoint_1m(precision="fp32"):
+    """Differentiable-run workload: the 1M-particle galaxy (grids 128^3,
+    128^3 q = 1/4, 128x128x32) plus a 20k-particle Plummer satellite
+    (M = 0.05, a = 0.05, 64^3 grids) at apocentre 8 R_d; 200 steps."""
+    return merger(n_gal=1_000_000, n_sat=20_000, grids=((128,), (128,), (128, 128, 32), (64,)), seed_id=3,
+                  precision=precision, name="adjoint_1m", sat_m=0.05, steps=200)
+
+
+def merger_small(precision="fp32", seed_id=12, r_apo=8.0):
     """Two galaxies at test size: the small galaxy (24k particles) and a 4k
-    Plummer satellite with its own 16^3 grids, on an inclined orbit."""
+    Plummer satellite with its own 16^3 grids, on an inclined orbit with
+    apocentre r_apo."""
     return merger(n_gal=24_000, n_sat=4_000, grids=((32,), (32,), (32, 32, 8), (16,)), seed_id=seed_id,
-                  precision=precision, name="merger_small", q_m=0.8)
+                  precision=precision, name="merger_small", q_m=0.8, r_apo=r_apo)
 
 
 def big_box(n=1_000_000, N=256, precision="fp32", seed_id=13):
