@@ -5,6 +5,7 @@ benchmark's CPU-baseline leg; the product path never imports it.
 """
 from .pm_oracle import *  # noqa: F401,F403
 from .pm_cic import *  # noqa: F401,F403
+from .pm_diag import *  # noqa: F401,F403
 from .pm_oracle import Geometry, Galaxy, System, State, cell_length
 import numpy as np
 
