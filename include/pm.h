@@ -228,6 +228,40 @@ int pm_cic_kick_drift(pm_ctx *ctx, const pm_particles *p, double dt_kick, double
 int pm_cic_vjp(pm_ctx *ctx, const pm_particles *p, const void *ux, const void *uy, const void *uz,
                void *gx, void *gy, void *gz, void *gm);
 
+/* ---- disc diagnostics (Sec. 6 quantities) ------------------------------
+ * FP64 reductions over the selected particles that are not lost: select
+ * (device uint8[n], nonzero = take) or NULL for every particle of galaxy
+ * q->gal.  Positions and velocities are taken relative to the current grid
+ * centre of galaxy q->gal (x, y in the disc plane); velocities are the
+ * stored ones (v(t - dt/2) inside a run: kick by dt/2 first to synchronise).
+ * With R = |(dx, dy)|, phi = atan2(dy, dx), v_R, v_phi the cylindrical
+ * components:
+ *   bins: q->nbins (1..64) radial bins of equal particle numbers, bounded
+ *     by the exact order statistics of R^2 at ranks floor(k n / nbins),
+ *     k = 1..nbins-1 (a particle is in bin #{k : edge_k <= R^2});
+ *   E_heat = sum m |v - vbar_c(R) e_phi|^2 / 2, vbar_c linear in R between
+ *     the bins' (mean R, mean v_phi) and constant beyond (Sec. 6 heat);
+ *   annulus q->r0 - q->dr <= R < q->r0 + q->dr: mass-weighted sigma_R,
+ *     sigma_phi, sigma_z (Sec. 6 dispersion ratio);
+ *   rings: q->nring rings of width q->r_ring / q->nring from R = 0 (R > 0),
+ *     A~_m = (1/S) sum m_j exp(-i m phi_j), m = 1..q->mmax, S the ring area
+ *     (Sec. 6 Fourier modes); nring * mmax <= 1024.
+ * out (host, 6 + 4 nbins + 2 nring mmax doubles): [n, E_heat, sigma_R,
+ * sigma_phi, sigma_z, annulus mass, then per bin (mean R, count,
+ * sqrt<z^2>, mean v_phi), then per ring and mode (Re A~_m, Im A~_m)].
+ * Synchronises (the bin edges take 8 radix passes with a host step each);
+ * allocates 0.1 MB of scratch on the first call. */
+typedef struct {
+    int32_t gal;
+    int32_t nbins;
+    int32_t nring;
+    int32_t mmax;
+    double r_ring;
+    double r0, dr;
+} pm_disc_query;
+int pm_disc_diagnostics(pm_ctx *ctx, const pm_particles *p, const uint8_t *select,
+                        const pm_disc_query *q, double *out);
+
 /* Allocation-free potential of one isolated grid.  The paper has no
  * counterpart: this entry point exists for callers that cannot call
  * cudaMalloc (a host application whose device memory is pre-partitioned by

@@ -161,6 +161,10 @@ struct pm_ctx {
     size_t bytes = 0;
     std::vector<void *> allocs;
     bool any_recentre = false;
+    // disc diagnostics scratch (allocated on first use)
+    unsigned *dg_hist = nullptr;
+    unsigned long long *dg_pref = nullptr, *dg_edges = nullptr;
+    double *dg_acc = nullptr, *dg_tab = nullptr;
 };
 
 namespace {
@@ -523,6 +527,130 @@ template <typename T> int cic_vjp_impl(pm_ctx *c, const pm_particles *p, const v
                                  std::ldexp(1.0, sa), c->user));
     PM_TRY(enqueue_solve<T>(c, c->user, nullptr, sa));
     PM_CK(pm_launch_cic_gather<T>(pk, c->hs, c->d_cen, (T *)gx, (T *)gy, (T *)gz, (T *)gm, c->user));
+    return check_device_error(c);
+}
+
+// ---- disc diagnostics (Sec. 6 quantities) ----------------------------------
+constexpr int DG_MAXBINS = 64, DG_MAXRM = 1024;
+
+template <typename T> int disc_impl(pm_ctx *c, const pm_particles *p, const uint8_t *sel, const pm_disc_query *q,
+                                    double *out) {
+    cudaStream_t st = c->user;
+    if (!c->dg_hist) {
+        PM_TRY(dev_alloc(c, (void **)&c->dg_hist, sizeof(unsigned) * 256 * DG_MAXBINS));
+        PM_TRY(dev_alloc(c, (void **)&c->dg_pref, sizeof(unsigned long long) * DG_MAXBINS));
+        PM_TRY(dev_alloc(c, (void **)&c->dg_edges, sizeof(unsigned long long) * DG_MAXBINS));
+        PM_TRY(dev_alloc(c, (void **)&c->dg_acc, sizeof(double) * (4 * DG_MAXBINS + 8 + 2 * DG_MAXRM)));
+        PM_TRY(dev_alloc(c, (void **)&c->dg_tab, sizeof(double) * 2 * DG_MAXBINS));
+    }
+    CenK ck;
+    PM_CK(cudaMemcpyAsync(&ck, c->d_cen, sizeof(CenK), cudaMemcpyDeviceToHost, st));
+    PM_CK(cudaStreamSynchronize(st));
+    pmk::DiagP<T> d;
+    d.x = (const T *)p->x; d.y = (const T *)p->y; d.z = (const T *)p->z;
+    d.vx = (const T *)p->vx; d.vy = (const T *)p->vy; d.vz = (const T *)p->vz;
+    d.m = (const T *)p->m;
+    d.flags = p->flags;
+    d.sel = sel;
+    d.gal_id = p->gal;
+    d.gal = q->gal;
+    d.n = p->n;
+    for (int k = 0; k < 3; ++k) d.c[k] = ck.c[q->gal][k];
+    const int B = q->nbins, NR = q->nring, MM = q->mmax;
+    const int nacc = 4 * B + 7 + 2 * NR * MM;
+    const int nout = 6 + 4 * B + 2 * NR * MM;
+    for (int k = 0; k < nout; ++k) out[k] = 0.0;
+
+    // exact bin edges: order statistics of R^2 at ranks floor(k n / B)
+    std::vector<unsigned long long> key(B > 1 ? B - 1 : 0, 0ull);
+    std::vector<long long> rank(key.size(), 0);
+    long long nsel = -1;
+    std::vector<unsigned> h(256 * DG_MAXBINS);
+    for (int pass = 0; pass < 8 && (!key.empty()); ++pass) {
+        std::vector<unsigned long long> uniq(key.begin(), key.end());
+        std::sort(uniq.begin(), uniq.end());
+        uniq.erase(std::unique(uniq.begin(), uniq.end()), uniq.end());
+        const int np = pass == 0 ? 1 : (int)uniq.size();
+        PM_CK(cudaMemcpyAsync(c->dg_pref, uniq.data(), sizeof(unsigned long long) * np, cudaMemcpyHostToDevice, st));
+        PM_CK(cudaMemsetAsync(c->dg_hist, 0, sizeof(unsigned) * 256 * np, st));
+        PM_CK(pm_launch_diag_hist<T>(d, pass, c->dg_pref, np, c->dg_hist, st));
+        PM_CK(cudaMemcpyAsync(h.data(), c->dg_hist, sizeof(unsigned) * 256 * np, cudaMemcpyDeviceToHost, st));
+        PM_CK(cudaStreamSynchronize(st));
+        if (pass == 0) {
+            nsel = 0;
+            for (int b = 0; b < 256; ++b) nsel += h[b];
+            if (nsel == 0) return check_device_error(c);
+            for (int k = 1; k < B; ++k) rank[k - 1] = ((long long)k * nsel) / B;
+        }
+        for (size_t k = 0; k < key.size(); ++k) {
+            const int j = pass == 0 ? 0 : (int)(std::lower_bound(uniq.begin(), uniq.end(), key[k]) - uniq.begin());
+            long long cum = 0;
+            int dgt = 0;
+            for (; dgt < 256; ++dgt) {
+                if (cum + h[j * 256 + dgt] > rank[k]) break;
+                cum += h[j * 256 + dgt];
+            }
+            if (dgt == 256) return fail(PM_E_STATE, "radix select lost a rank (particles changed during the call?)");
+            key[k] = (key[k] << 8) | (unsigned long long)dgt;
+            rank[k] -= cum;
+        }
+    }
+    if (!key.empty())
+        PM_CK(cudaMemcpyAsync(c->dg_edges, key.data(), sizeof(unsigned long long) * key.size(), cudaMemcpyHostToDevice,
+                              st));
+    pmk::DiagQ dq;
+    dq.nbins = B; dq.nring = NR; dq.mmax = MM;
+    dq.r_ring = q->r_ring;
+    dq.width = NR > 0 ? q->r_ring / NR : 1.0;
+    dq.rlo = q->r0 - q->dr;
+    dq.rhi = q->r0 + q->dr;
+    PM_CK(cudaMemsetAsync(c->dg_acc, 0, sizeof(double) * (nacc + 1), st));
+    PM_CK(pm_launch_diag_sums<T>(d, dq, c->dg_edges, c->dg_acc, st));
+    std::vector<double> acc(nacc + 1);
+    PM_CK(cudaMemcpyAsync(acc.data(), c->dg_acc, sizeof(double) * nacc, cudaMemcpyDeviceToHost, st));
+    PM_CK(cudaStreamSynchronize(st));
+
+    std::vector<double> xp, fp;
+    long long ntot = 0;
+    for (int b = 0; b < B; ++b) {
+        const double cnt = acc[4 * b + 1];
+        ntot += (long long)cnt;
+        double *o = out + 6 + 4 * b;
+        o[1] = cnt;
+        if (cnt > 0) {
+            o[0] = acc[4 * b] / cnt;
+            o[2] = std::sqrt(acc[4 * b + 2] / cnt);
+            o[3] = acc[4 * b + 3] / cnt;
+            xp.push_back(o[0]);
+            fp.push_back(o[3]);
+        }
+    }
+    out[0] = (double)ntot;
+    const double *a = acc.data() + 4 * B;
+    out[5] = a[0];
+    if (a[0] > 0) {
+        auto disp = [&](int k) {
+            const double mean = a[k] / a[0];
+            return std::sqrt(std::max(a[k + 1] / a[0] - mean * mean, 0.0));
+        };
+        out[2] = disp(1);
+        out[3] = disp(3);
+        out[4] = disp(5);
+    }
+    for (int r = 0; r < NR; ++r) {
+        const double S = M_PI * (((r + 1) * dq.width) * ((r + 1) * dq.width) - (r * dq.width) * (r * dq.width));
+        for (int mo = 0; mo < MM; ++mo)
+            for (int k = 0; k < 2; ++k) out[6 + 4 * B + 2 * (r * MM + mo) + k] = a[7 + 2 * (r * MM + mo) + k] / S;
+    }
+    if (!xp.empty()) {
+        std::vector<double> tab(xp);
+        tab.insert(tab.end(), fp.begin(), fp.end());
+        PM_CK(cudaMemcpyAsync(c->dg_tab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, st));
+        PM_CK(cudaMemsetAsync(c->dg_acc + nacc, 0, sizeof(double), st));
+        PM_CK(pm_launch_diag_heat<T>(d, c->dg_tab, c->dg_tab + xp.size(), (int)xp.size(), c->dg_acc + nacc, st));
+        PM_CK(cudaMemcpyAsync(&out[1], c->dg_acc + nacc, sizeof(double), cudaMemcpyDeviceToHost, st));
+        PM_CK(cudaStreamSynchronize(st));
+    }
     return check_device_error(c);
 }
 
@@ -951,6 +1079,23 @@ int pm_cic_vjp(pm_ctx *c, const pm_particles *p, const void *ux, const void *uy,
         return fail(PM_E_ARG, "cotangent or gradient array is NULL");
     if (p->n == 0) return PM_OK;
     return PM_DISPATCH(c, cic_vjp_impl, c, p, ux, uy, uz, gx, gy, gz, gm);
+}
+
+int pm_disc_diagnostics(pm_ctx *c, const pm_particles *p, const uint8_t *select, const pm_disc_query *q,
+                        double *out) {
+    if (!c || !q || !out) return fail(PM_E_ARG, "ctx, query or out is NULL");
+    PM_TRY(check_particles(p));
+    if (q->gal < 0 || q->gal >= c->sys.ngal) return fail(PM_E_ARG, "no galaxy %d", q->gal);
+    if (q->nbins < 1 || q->nbins > DG_MAXBINS) return fail(PM_E_ARG, "nbins must be in 1..%d", DG_MAXBINS);
+    if (q->nring < 0 || q->mmax < 0 || (long long)q->nring * q->mmax > DG_MAXRM)
+        return fail(PM_E_ARG, "need nring >= 0, mmax >= 0, nring * mmax <= %d", DG_MAXRM);
+    if (q->nring > 0 && q->mmax > 0 && !(q->r_ring > 0 && std::isfinite(q->r_ring)))
+        return fail(PM_E_ARG, "r_ring must be positive");
+    if (!(q->dr >= 0) || !std::isfinite(q->r0) || !std::isfinite(q->dr)) return fail(PM_E_ARG, "bad annulus");
+    const pm_disc_query qq = *q;
+    pm_disc_query q2 = qq;
+    if (q2.mmax == 0) q2.nring = 0;
+    return PM_DISPATCH(c, disc_impl, c, p, select, &q2, out);
 }
 
 int pm_get_density(pm_ctx *c, int32_t gal, int32_t set, int64_t *host_out) {

@@ -125,18 +125,6 @@ __device__ __forceinline__ void stencil(const GeomK &g, const T *__restrict__ P1
     if (phi) *phi += p0 + gx * dx + gy * dy + gz * dz;
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
-}
-
-__device__ __forceinline__ long long warp_sum_ll(long long v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
-}
-
 // ---------------------------------------------------------------------------
 // Step a1 (recentring).  The centre of mass of each recentring galaxy's live
 // particles within R_core of its centre c is accumulated exactly in integers:

@@ -76,6 +76,36 @@ template <typename T>
 cudaError_t pm_launch_cic_umax(const PartK<T> &p, const T *ux, const T *uy, const T *uz, unsigned *out,
                                cudaStream_t st);
 
+// Disc diagnostics (Sec. 6 quantities): particle view and query.
+namespace pmk {
+template <typename T> struct DiagP {
+    const T *x, *y, *z, *vx, *vy, *vz, *m;
+    const uint32_t *flags;
+    const uint8_t *sel;     // null: particles of galaxy `gal`
+    const int32_t *gal_id;
+    int gal;
+    long long n;
+    double c[3];
+};
+
+// Accumulator layout: per bin [sum R, count, sum z^2, sum v_phi]; annulus
+// [M, M vR, M vR^2, M vphi, M vphi^2, M vz, M vz^2]; per ring and mode
+// [sum m cos(m phi), -sum m sin(m phi)].
+struct DiagQ {
+    int nbins, nring, mmax;
+    double width, r_ring, rlo, rhi;
+};
+
+}  // namespace pmk
+// Radix-select pass over the bits of R^2 (pass 0..7), the sums of the bins,
+// annulus and rings, and the heat about an interpolated circular velocity.
+template <typename T> cudaError_t pm_launch_diag_hist(const pmk::DiagP<T> &d, int pass, const unsigned long long *pref,
+                                                      int npref, unsigned *hist, cudaStream_t st);
+template <typename T> cudaError_t pm_launch_diag_sums(const pmk::DiagP<T> &d, const pmk::DiagQ &q,
+                                                      const unsigned long long *edges, double *acc, cudaStream_t st);
+template <typename T> cudaError_t pm_launch_diag_heat(const pmk::DiagP<T> &d, const double *xp, const double *fp,
+                                                      int np, double *acc, cudaStream_t st);
+
 // FP64 H-hat construction (precision independent) and storage conversion.
 cudaError_t pm_green_octant(double *h, int nx, int ny, int nz, double q, double h000, cudaStream_t st);
 cudaError_t pm_axis_transform(const double *in, double *out, const double *cmat, int n1,

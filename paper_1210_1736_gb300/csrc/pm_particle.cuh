@@ -39,4 +39,16 @@ __device__ __forceinline__ void cell_delta(const GeomK &g, const Cell &cl, T rx,
     dz = rz - (T)(cl.k - (g.nz >> 1)) * (T)g.lz;
 }
 
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ long long warp_sum_ll(long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
 }  // namespace pmk

@@ -47,6 +47,11 @@ class pm_particles(C.Structure):
                 ("m", _vp), ("gal", _vp), ("flags", _vp), ("n", C.c_int64)]
 
 
+class pm_disc_query(C.Structure):
+    _fields_ = [("gal", C.c_int32), ("nbins", C.c_int32), ("nring", C.c_int32), ("mmax", C.c_int32),
+                ("r_ring", C.c_double), ("r0", C.c_double), ("dr", C.c_double)]
+
+
 _P = C.POINTER
 _SIGS.update({
     "pm_cell_length": (C.c_double, [C.c_double, C.c_int32, C.c_double]),
@@ -74,6 +79,7 @@ _SIGS.update({
     "pm_set_sort_interval": (C.c_int, [_vp, C.c_int32]),
     "pm_potential_static": (C.c_int, [_vp, _vp, C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_double,
                                       C.c_double, C.c_double, C.c_int32, C.c_int32, _vp]),
+    "pm_disc_diagnostics": (C.c_int, [_vp, _P(pm_particles), _vp, _P(pm_disc_query), _P(C.c_double)]),
     "pm_cic_deposit": (C.c_int, [_vp, _P(pm_particles)]),
     "pm_cic_force": (C.c_int, [_vp, _P(pm_particles), _vp, _vp, _vp]),
     "pm_cic_kick_drift": (C.c_int, [_vp, _P(pm_particles), C.c_double, C.c_double]),
@@ -305,6 +311,28 @@ class Context:
         out = (C.c_double * 8)()
         _check(lib().pm_diagnostics(self.h, C.byref(p.struct()), float(dt), out))
         return {"K": out[0], "W": out[1], "E": out[2], "L": np.array(out[3:6]), "n_live": int(out[6])}
+
+    def disc_diagnostics(self, p, select=None, gal=0, nbins=20, nring=10, mmax=4, r_ring=5.0, r0=3.2, dr=0.4):
+        """Sec. 6 disc quantities (see pm_disc_diagnostics in include/pm.h);
+        select: device uint8/bool tensor (nonzero = take) or None for every
+        particle of galaxy `gal`.  Returns a dict of numpy values."""
+        q = pm_disc_query(int(gal), int(nbins), int(nring), int(mmax), float(r_ring), float(r0), float(dr))
+        nout = 6 + 4 * nbins + 2 * nring * mmax
+        out = (C.c_double * nout)()
+        sp = None
+        if select is not None:
+            import torch
+            sel = select.to(torch.uint8).contiguous()
+            sp = sel.data_ptr()
+        _check(lib().pm_disc_diagnostics(self.h, C.byref(p.struct()), sp, C.byref(q), out))
+        a = np.array(out)
+        bins = a[6:6 + 4 * nbins].reshape(nbins, 4)
+        A = a[6 + 4 * nbins:].reshape(nring, mmax, 2)
+        sR, sphi, sz = a[2], a[3], a[4]
+        return {"raw": a, "n": int(a[0]), "E_heat": a[1], "sigma_R": sR, "sigma_phi": sphi, "sigma_z": sz,
+                "sigma_z_over_R": sz / sR if sR > 0 else float("nan"), "sigma_tot2": sR ** 2 + sphi ** 2 + sz ** 2,
+                "annulus_mass": a[5], "R_mean": bins[:, 0], "count": bins[:, 1], "z_rms": bins[:, 2],
+                "v_c": bins[:, 3], "A": A[..., 0] + 1j * A[..., 1]}
 
     def density(self, gal, k):
         a = np.empty(self.shapes[(gal, k)], dtype=np.int64)
