@@ -29,6 +29,40 @@ __host__ __device__ constexpr int stride_before(int L, int s, bool rev) {
     return s == 0 ? 1 : stride_before(L, s - 1, rev) * radix(L, s - 1, rev);
 }
 
+// Per-stage twiddle tables, laid out so that register r of a thread with
+// j % Ns = jm reads entry r*Ns + jm (consecutive jm: consecutive addresses):
+// table of stage S (S > 0) = w^{(jm r L / (Ns R)) mod L}, r < R, jm < Ns, with
+// w = exp(-2 pi i / L).  The forward plan's tables come first, then the
+// reversed plan's.
+__host__ __device__ constexpr int tw_stage_size(int L, int S, bool rev) {
+    return S == 0 ? 0 : stride_before(L, S, rev) * radix(L, S, rev);
+}
+__host__ __device__ constexpr int tw_dir_size(int L, bool rev) {
+    return tw_stage_size(L, 1, rev) * (nstages(L) > 1) + tw_stage_size(L, 2, rev) * (nstages(L) > 2);
+}
+__host__ __device__ constexpr int tw_offset(int L, int S, bool rev) {
+    return (rev ? tw_dir_size(L, false) : 0) + (S >= 2 ? tw_stage_size(L, 1, rev) : 0);
+}
+__host__ __device__ constexpr int tw_total(int L) { return tw_dir_size(L, false) + tw_dir_size(L, true); }
+
+template <int L, int S, bool REV, typename C>
+__device__ __forceinline__ void expand_stage_twiddles(C *tab, const C *g) {
+    if (S >= nstages(L)) return;
+    constexpr int Ns = stride_before(L, S, REV), R = radix(L, S, REV), OFF = tw_offset(L, S, REV);
+    for (int i = threadIdx.x; i < Ns * R; i += blockDim.x) {
+        const int r = i / Ns, jm = i % Ns;
+        tab[OFF + i] = g[(jm * r * (L / (Ns * R))) & (L - 1)];
+    }
+}
+// Builds the stage tables in shared memory from the plain table
+// g[m] = w^m, m < L (the caller synchronises before use).
+template <int L, typename C> __device__ __forceinline__ void expand_twiddles(C *tab, const C *g) {
+    expand_stage_twiddles<L, 1, false>(tab, g);
+    expand_stage_twiddles<L, 2, false>(tab, g);
+    expand_stage_twiddles<L, 1, true>(tab, g);
+    expand_stage_twiddles<L, 2, true>(tab, g);
+}
+
 // z * exp(SIGN * 2 pi i e / 16) for a compile-time-known e.
 template <int SIGN, typename C> __device__ __forceinline__ C rot16(int e, C z) {
     typedef decltype(z.x) T;
@@ -150,7 +184,7 @@ __device__ __forceinline__ void dft16(C *v) {
 // Butterflies of stage S on the thread's E registers.  Thread t of a column
 // owns the stage items j = t + kk*TPC (kk < E/R); register kk*R + r holds the
 // input x[j + r*L/R] and afterwards the output y[(j/Ns)*Ns*R + j%Ns + r*Ns].
-// tw[m] = exp(-2 pi i m / L) (conjugated for SIGN > 0).
+// tw: the stage tables of expand_twiddles (conjugated for SIGN > 0).
 // ZIN / HOUT select the pruned radix-16 (see dft16); they are only passed
 // for radix-16 stages.
 template <int L, int S, bool REV, int SIGN, bool ZIN = false, bool HOUT = false, typename C>
@@ -160,10 +194,10 @@ __device__ __forceinline__ void stage_butterflies(C *v, int t, const C *tw) {
     for (int kk = 0; kk < E / R; ++kk) {
         const int j = t + kk * TPC;
         if (Ns > 1) {
-            const int jm = j % Ns;
+            const C *tws = tw + tw_offset(L, S, REV) + (j % Ns);
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                C w = tw[(jm * r * (L / (Ns * R))) & (L - 1)];
+                C w = tws[r * Ns];
                 v[kk * R + r] = (SIGN < 0) ? cmul(v[kk * R + r], w) : cconjmul(v[kk * R + r], w);
             }
         }

@@ -37,12 +37,9 @@ template <int L> struct XShape {          // x passes: rows per block, padded ro
 };
 
 template <typename T, int L> constexpr size_t xpass_smem() {
-    return (size_t)(L + XShape<L>::LINES * XShape<L>::LDR) * sizeof(typename cplx_t<T>::type);
+    return (size_t)(pmfft::tw_total(L) + XShape<L>::LINES * XShape<L>::LDR) * sizeof(typename cplx_t<T>::type);
 }
 
-template <typename C> __device__ __forceinline__ void load_twiddles(C *tw, const C *g, int L) {
-    for (int i = threadIdx.x; i < L; i += blockDim.x) tw[i] = g[i];
-}
 
 // ---------------------------------------------------------------------------
 // x passes: the TPC = L/16 threads of a row are consecutive lanes, so a
@@ -59,9 +56,9 @@ __global__ void __launch_bounds__(NT) k_xfwd(PairArgs a) {
     constexpr int NX = L / 2, NS = nstages(L);
     extern __shared__ __align__(16) unsigned char smraw[];
     C *tw = reinterpret_cast<C *>(smraw);
-    C *sm = tw + L;
+    C *sm = tw + pmfft::tw_total(L);
     const int tid = threadIdx.x, line = tid / S::TPC, t = tid % S::TPC;
-    load_twiddles(tw, static_cast<const C *>(a.tw), L);
+    pmfft::expand_twiddles<L>(tw, static_cast<const C *>(a.tw));
     const long long nrows = (long long)a.ny * a.nz;
     const long long r = (long long)blockIdx.x * S::LINES + line;
     const bool valid = r < nrows;
@@ -104,9 +101,9 @@ __global__ void __launch_bounds__(NT) k_xinv(PairArgs a) {
     constexpr int NX = L / 2, NS = nstages(L);
     extern __shared__ __align__(16) unsigned char smraw[];
     C *tw = reinterpret_cast<C *>(smraw);
-    C *sm = tw + L;
+    C *sm = tw + pmfft::tw_total(L);
     const int tid = threadIdx.x, line = tid / S::TPC, t = tid % S::TPC;
-    load_twiddles(tw, static_cast<const C *>(a.tw), L);
+    pmfft::expand_twiddles<L>(tw, static_cast<const C *>(a.tw));
     const long long nrows = (long long)a.ny * a.nz;
     const long long r = (long long)blockIdx.x * S::LINES + line;
     const bool valid = r < nrows;
@@ -202,7 +199,7 @@ template <> struct ColRows<COL_YINV> { __host__ __device__ static constexpr int 
 template <typename T, int L, int MODE> constexpr size_t col_smem() {
     typedef typename cplx_t<T>::type C;
     constexpr int COLS = CShape<T, L>::COLS;
-    return 128 + (size_t)L * sizeof(C) + (size_t)L * COLS * sizeof(C) +
+    return 128 + (size_t)pmfft::tw_total(L) * sizeof(C) + (size_t)L * COLS * sizeof(C) +
            2 * (size_t)ColRows<MODE>::of(L) * COLS * sizeof(C) + 3 * 128;
 }
 
@@ -257,7 +254,7 @@ __global__ void __launch_bounds__(CShape<T, L>::THREADS, 3) k_col(PairArgs a, co
         mbar_init(&bar[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    load_twiddles(tw, static_cast<const C *>(a.tw), L);
+    pmfft::expand_twiddles<L>(tw, static_cast<const C *>(a.tw));
     __syncthreads();
     int issued[2] = {0, 0};   // loads issued per buffer (thread 0's count)
     if (tid == 0) {
@@ -303,7 +300,7 @@ __global__ void __launch_bounds__(CShape<T, L>::THREADS, 3) k_col(PairArgs a, co
         size_t stride;
         if (MODE == COL_ZCONV) {
             q = tile * COLS + c;
-            valid = q < (long long)ny2 * nx2;
+            valid = true;   // COLS (a power of two <= 256) divides the 2ny x 2nx >= 256 columns
             col = work + q;
             stride = (size_t)ny2 * nx2;
         } else {
@@ -318,29 +315,33 @@ __global__ void __launch_bounds__(CShape<T, L>::THREADS, 3) k_col(PairArgs a, co
         if (MODE == COL_YFWD) {
             constexpr int RL = radix(L, NS - 1, false);
             if (valid) {
+                C *colt = col + (size_t)t * stride;
 #pragma unroll
                 for (int kk = 0; kk < E / RL; ++kk)
 #pragma unroll
                     for (int r = 0; r < RL; ++r)
-                        col[(size_t)pmfft::in_row<L, NS - 1, false>(t, kk, r) * stride] = v[kk * RL + r];
+                        colt[(size_t)pmfft::in_row<L, NS - 1, false>(0, kk, r) * stride] = v[kk * RL + r];
             }
             continue;
         }
         if (MODE == COL_ZCONV) {
             constexpr int RL = radix(L, NS - 1, false);
-            const T *hh = static_cast<const T *>(a.hhat);
-            const int ky = valid ? (int)(q / nx2) : 0, kx = valid ? (int)(q % nx2) : 0;
+            const int ky = (int)(q / nx2), kx = (int)(q % nx2);
             const int kyr = ky <= a.ny ? ky : ny2 - ky;
             const int kxr = kx <= a.nx ? kx : nx2 - kx;
-            const size_t hrow = ((size_t)kyr * (a.nx + 1) + kxr);
-            const size_t hplane = (size_t)(a.ny + 1) * (a.nx + 1);
+            const int hp = (a.ny + 1) * (a.nx + 1);   // one kz plane of the octant
+            // row kz = t + o of the forward output (o = kk*TPC + r*L/RL, known at
+            // compile time) reads H-hat row kz when kz <= L/2, else L - kz; no
+            // o range straddles L/2, so each register reads one of two bases
+            const T *hrow = static_cast<const T *>(a.hhat) + ((size_t)kyr * (a.nx + 1) + kxr);
+            const T *hd = hrow + (size_t)t * hp;
+            const T *hm = hrow + (size_t)(L - t) * hp;
 #pragma unroll
             for (int kk = 0; kk < E / RL; ++kk)
 #pragma unroll
                 for (int r = 0; r < RL; ++r) {
-                    const int kz = pmfft::in_row<L, NS - 1, false>(t, kk, r);
-                    const int kzr = kz <= L / 2 ? kz : L - kz;
-                    const T h = valid ? __ldg(hh + (size_t)kzr * hplane + hrow) : (T)0;
+                    const int o = pmfft::in_row<L, NS - 1, false>(0, kk, r);
+                    const T h = (o < L / 2) ? __ldg(hd + o * hp) : __ldg(hm - o * hp);
                     v[kk * RL + r].x *= h;
                     v[kk * RL + r].y *= h;
                 }
@@ -350,11 +351,12 @@ __global__ void __launch_bounds__(CShape<T, L>::THREADS, 3) k_col(PairArgs a, co
         // radix 16, whose outputs below L/2 are registers r < 8
         constexpr int RL = radix(L, NS - 1, true);
         if (valid) {
+            C *colt = col + (size_t)t * stride;
 #pragma unroll
             for (int kk = 0; kk < E / RL; ++kk)
 #pragma unroll
                 for (int r = 0; r < RL / 2; ++r)
-                    col[(size_t)pmfft::in_row<L, NS - 1, true>(t, kk, r) * stride] = v[kk * RL + r];
+                    colt[(size_t)pmfft::in_row<L, NS - 1, true>(0, kk, r) * stride] = v[kk * RL + r];
         }
     }
 }
