@@ -244,8 +244,8 @@ int build_hhat(pm_ctx *c, GeoBuf &gb) {
     PM_CK(cosmat(g.nz));
     PM_CK(pm_axis_transform(h, t1, cm, R, 1, (long long)Q * P, st));
     const double scale = c->sys.G / (g.l_xy * 8.0 * g.nx * g.ny * g.nz);
-    if (c->prec == PM_FP32) PM_CK(pm_store_hhat<float>(t1, (float *)gb.hhat, n, scale, st));
-    else PM_CK(pm_store_hhat<double>(t1, (double *)gb.hhat, n, scale, st));
+    if (c->prec == PM_FP32) PM_CK(pm_store_hhat<float>(t1, (float *)gb.hhat, g.nx, g.ny, g.nz, scale, st));
+    else PM_CK(pm_store_hhat<double>(t1, (double *)gb.hhat, g.nx, g.ny, g.nz, scale, st));
     PM_CK(cudaStreamSynchronize(st));
     cudaFree(h);
     cudaFree(t1);
@@ -684,7 +684,8 @@ EncodeTiledFn encode_fn() {
 
 // 2D map over 8-byte elements: dim0 contiguous, dim1 rows of stride1 bytes.
 int encode2d(CUtensorMap *m, void *base, unsigned long long dim0, unsigned long long dim1,
-             unsigned long long stride1, unsigned box0, unsigned box1) {
+             unsigned long long stride1, unsigned box0, unsigned box1,
+             CUtensorMapSwizzle swz = CU_TENSOR_MAP_SWIZZLE_NONE) {
     EncodeTiledFn f = encode_fn();
     if (!f) return fail(PM_E_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
     const cuuint64_t gdim[2] = {dim0, dim1};
@@ -692,7 +693,7 @@ int encode2d(CUtensorMap *m, void *base, unsigned long long dim0, unsigned long 
     const cuuint32_t box[2] = {box0, box1};
     const cuuint32_t es[2] = {1, 1};
     const CUresult r = f(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, base, gdim, gstr, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(PM_E_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     return PM_OK;
@@ -703,14 +704,18 @@ int pm_encode_col_maps(void *work, int nx, int ny, int nz, int esz, CUtensorMap 
                        CUtensorMap *zmap) {
     const unsigned long long epc = esz == 4 ? 1 : 2;   // 8-byte elements per complex value
     const unsigned long long nx2 = 2ull * nx, ny2 = 2ull * ny;
-    const unsigned cy = (unsigned)pm_col_cols(2 * ny, esz), cz = (unsigned)pm_col_cols(2 * nz, esz);
+    const unsigned cy = (unsigned)pm_col_cols(2 * ny, esz), sz = (unsigned)pm_zsub_cols(2 * nz, esz);
+    const unsigned zrow = sz * (unsigned)epc * 8;   // bytes per box row: 32, 64 or 128
+    const CUtensorMapSwizzle zswz = zrow >= 128 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                    : zrow >= 64 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                    : zrow >= 32 ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_NONE;
     // y passes: dim0 = kx, dim1 = the (z, y) rows, box = COLS columns x rows
     PM_TRY(encode2d(yfwd, work, nx2 * epc, ny2 * nz, nx2 * epc * 8, cy * (unsigned)epc, (unsigned)std::min(ny, 256)));
     PM_TRY(encode2d(yinv, work, nx2 * epc, ny2 * nz, nx2 * epc * 8, cy * (unsigned)epc,
                     (unsigned)std::min(2 * ny, 256)));
     // z pass: dim0 = the (ky, kx) columns, dim1 = z
-    PM_TRY(encode2d(zmap, work, nx2 * ny2 * epc, nz, nx2 * ny2 * epc * 8, cz * (unsigned)epc,
-                    (unsigned)std::min(nz, 256)));
+    PM_TRY(encode2d(zmap, work, nx2 * ny2 * epc, nz, nx2 * ny2 * epc * 8, sz * (unsigned)epc,
+                    (unsigned)std::min(nz, 256), zswz));
     return PM_OK;
 }
 
@@ -806,7 +811,7 @@ int pm_create_grids(const pm_system *sys, const pm_galaxy *gals, void *stream, p
             gb.g = g;
             gb.A = (long long)g.nx * g.ny * g.nz;
             gb.workN = (long long)g.nz * 2 * g.ny * 2 * g.nx;
-            gb.hatN = (long long)(g.nx + 1) * (g.ny + 1) * (g.nz + 1);
+            gb.hatN = pm_hhat_table_size(g.nx, g.ny, g.nz);
             c->geos.push_back(gb);
             id = (int)c->geos.size() - 1;
         }

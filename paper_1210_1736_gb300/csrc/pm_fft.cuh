@@ -266,22 +266,27 @@ __device__ __forceinline__ void load_stage(const C *sm, int ldc, int c, int t, C
 // data; the first stage is radix 16 and only registers r < 8 are read).
 // HOUT: only the outputs of rows < L/2 are used (inverse transforms; the
 // last stage of a reversed plan is radix 16, outputs in registers r < 8).
-template <int L, bool REV, int SIGN, bool ZIN = false, bool HOUT = false, typename C, class LAY>
+// WSYNC: the exchange area of a transform is touched by one warp only, so
+// the exchanges synchronise the warp instead of the block.
+template <bool WSYNC> __device__ __forceinline__ void xsync() {
+    if (WSYNC) __syncwarp(); else __syncthreads();
+}
+template <int L, bool REV, int SIGN, bool ZIN = false, bool HOUT = false, bool WSYNC = false, typename C, class LAY>
 __device__ __forceinline__ void fft_core(C *v, C *sm, const LAY &lay, int t, const C *tw) {
     constexpr int NS = nstages(L);
     stage_butterflies<L, 0, REV, SIGN, ZIN, HOUT && NS == 1>(v, t, tw);
     if (NS > 1) {
         store_stage<L, 0, REV>(sm, lay, t, v);
-        __syncthreads();
+        xsync<WSYNC>();
         load_stage<L, (NS > 1 ? 1 : 0), REV>(sm, lay, t, v);
-        __syncthreads();
+        xsync<WSYNC>();
         stage_butterflies<L, (NS > 1 ? 1 : 0), REV, SIGN, false, HOUT && NS == 2>(v, t, tw);
     }
     if (NS > 2) {
         store_stage<L, (NS > 1 ? 1 : 0), REV>(sm, lay, t, v);
-        __syncthreads();
+        xsync<WSYNC>();
         load_stage<L, (NS > 2 ? 2 : 0), REV>(sm, lay, t, v);
-        __syncthreads();
+        xsync<WSYNC>();
         stage_butterflies<L, (NS > 2 ? 2 : 0), REV, SIGN, false, HOUT>(v, t, tw);
     }
 }

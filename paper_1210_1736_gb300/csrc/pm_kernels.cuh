@@ -510,10 +510,18 @@ __global__ void k_count_lost(PartK<T> p, unsigned long long *out) {
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
 }
 
-template <typename T>
-__global__ void k_store_hhat(const double *in, T *out, long long n, double scale) {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        out[i] = (T)(in[i] * scale);
+template <typename T, int L>
+__global__ void k_store_hhat(const double *oct, T *out, int nx, int ny, double scale) {
+    constexpr int TPC = L / E, NS = nstages(L), RL = radix(L, NS - 1, false);
+    const long long ncol = (long long)(nx + 1) * (ny + 1);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < ncol * L;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long col = i / L;
+        const int w = (int)(i % L), e = w / TPC, t = w % TPC;
+        const int kz = pmfft::in_row<L, NS - 1, false>(t, e / RL, e % RL);
+        const int kzr = kz <= L / 2 ? kz : L - kz;
+        out[i] = (T)(oct[(long long)kzr * ncol + col] * scale);
+    }
 }
 
 }  // namespace pmk
@@ -553,17 +561,29 @@ inline int num_sms() {
     return n;
 }
 
+template <typename T, int L> int zconv_blocks_per_sm() {
+    static int cached = 0;
+    if (!cached) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pmk::k_zconv<T, L>, pmk::ZShape<T, L>::THREADS,
+                                                          pmk::zconv_smem<T, L>()) != cudaSuccess || nb < 1)
+            nb = 1;
+        cached = nb;
+    }
+    return cached;
+}
+
 template <typename T, int L> cudaError_t attrs_L() {
     cudaError_t e;
+    e = cudaFuncSetAttribute(pmk::k_zconv<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)pmk::zconv_smem<T, L>());
+    if (e) return e;
     e = cudaFuncSetAttribute(pmk::k_xfwd<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pmk::xpass_smem<T, L>());
     if (e) return e;
     e = cudaFuncSetAttribute(pmk::k_xinv<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pmk::xpass_smem<T, L>());
     if (e) return e;
     e = cudaFuncSetAttribute(pmk::k_col<T, L, COL_YFWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)pmk::col_smem<T, L, COL_YFWD>());
-    if (e) return e;
-    e = cudaFuncSetAttribute(pmk::k_col<T, L, COL_ZCONV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)pmk::col_smem<T, L, COL_ZCONV>());
     if (e) return e;
     return cudaFuncSetAttribute(pmk::k_col<T, L, COL_YINV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)pmk::col_smem<T, L, COL_YINV>());
@@ -583,9 +603,7 @@ template <typename T, int L> cudaError_t xinv_L(const PairArgs &a, cudaStream_t 
 }
 template <typename T, int L, int MODE> cudaError_t col_LM(const PairArgs &a, const CUtensorMap &map, cudaStream_t st) {
     constexpr int COLS = pmk::CShape<T, L>::COLS;
-    long long ntiles;
-    if (MODE == COL_ZCONV) ntiles = ((long long)4 * a.ny * a.nx + COLS - 1) / COLS;
-    else ntiles = (long long)a.nz * ((2 * a.nx + COLS - 1) / COLS);
+    const long long ntiles = (long long)a.nz * ((2 * a.nx + COLS - 1) / COLS);
     long long grid = (long long)col_blocks_per_sm<T, L, MODE>() * num_sms();
     if (grid > ntiles) grid = ntiles;
     if (grid < 1) grid = 1;
@@ -593,9 +611,18 @@ template <typename T, int L, int MODE> cudaError_t col_LM(const PairArgs &a, con
                                                                                                           ntiles);
     return cudaGetLastError();
 }
+template <typename T, int L> cudaError_t zconv_L(const PairArgs &a, const CUtensorMap &map, cudaStream_t st) {
+    typedef pmk::ZShape<T, L> S;
+    const long long ntiles = ((long long)4 * a.ny * a.nx) / S::COLS;   // COLS divides the 2ny x 2nx columns
+    long long grid = (long long)zconv_blocks_per_sm<T, L>() * num_sms();
+    if (grid > ntiles) grid = ntiles;
+    if (grid < 1) grid = 1;
+    pmk::k_zconv<T, L><<<(unsigned)grid, S::THREADS, pmk::zconv_smem<T, L>(), st>>>(a, map, ntiles);
+    return cudaGetLastError();
+}
 template <typename T, int L> cudaError_t col_L(const PairArgs &a, const CUtensorMap &map, int mode, cudaStream_t st) {
     if (mode == COL_YFWD) return col_LM<T, L, COL_YFWD>(a, map, st);
-    if (mode == COL_ZCONV) return col_LM<T, L, COL_ZCONV>(a, map, st);
+    if (mode == COL_ZCONV) return zconv_L<T, L>(a, map, st);
     return col_LM<T, L, COL_YINV>(a, map, st);
 }
 
@@ -698,9 +725,11 @@ cudaError_t pm_launch_count_lost(const PartK<T> &p, unsigned long long *out, cud
 }
 
 template <typename T>
-cudaError_t pm_store_hhat(const double *in, T *out, long long n, double scale, cudaStream_t st) {
-    pmk::k_store_hhat<T><<<pmk_host::particle_grid(n), 256, 0, st>>>(in, out, n, scale);
-    return cudaGetLastError();
+cudaError_t pm_store_hhat(const double *oct, T *out, int nx, int ny, int nz, double scale, cudaStream_t st) {
+    const int g = pmk_host::particle_grid(pm_hhat_table_size(nx, ny, nz));
+#define PM_SH(LL) (pmk::k_store_hhat<T, LL><<<g, 256, 0, st>>>(oct, out, nx, ny, scale), cudaGetLastError())
+    PM_SWITCH_L(2 * nz, PM_SH)
+#undef PM_SH
 }
 
 #define PM_INSTANTIATE(T)                                                                                       \
@@ -717,4 +746,4 @@ cudaError_t pm_store_hhat(const double *in, T *out, long long n, double scale, c
     template cudaError_t pm_launch_sort<T>(const PartK<T> &, const PartK<T> &, const SysK &, const CenK *,     \
                                            const SortK &, unsigned *, unsigned *, unsigned *, unsigned *,       \
                                            long long *, cudaStream_t);                                          \
-    template cudaError_t pm_store_hhat<T>(const double *, T *, long long, double, cudaStream_t);
+    template cudaError_t pm_store_hhat<T>(const double *, T *, int, int, int, double, cudaStream_t);

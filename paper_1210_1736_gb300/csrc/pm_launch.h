@@ -29,9 +29,17 @@ __host__ __device__ constexpr int pm_col_cols(int L, int esz) {
     return (4096 / L) < (esz == 4 ? 256 : 128) ? (4096 / L) : (esz == 4 ? 256 : 128);
 }
 
+// Columns per swizzled sub-tile of the z pass: as many as fill a 128-byte
+// shared-memory row (16 FP32 or 8 FP64 complex values), at most a tile.
+__host__ __device__ constexpr int pm_zsub_cols(int L, int esz) {
+    return pm_col_cols(L, esz) < (esz == 4 ? 16 : 8) ? pm_col_cols(L, esz) : (esz == 4 ? 16 : 8);
+}
+
 // Tensor maps (2D, 8-byte elements) of one pair's work array for the
 // column passes: y forward (box rows ny), y inverse (box rows min(2ny,256)),
-// z (box rows nz).  Host only; no device memory is touched.
+// z (box pm_zsub_cols columns x min(nz,256) rows, swizzled to the box row
+// width, used for the z pass's loads and stores).  Host only; no device
+// memory is touched.
 int pm_encode_col_maps(void *work, int nx, int ny, int nz, int esz, CUtensorMap *yfwd, CUtensorMap *yinv,
                        CUtensorMap *zmap);
 
@@ -110,8 +118,13 @@ template <typename T> cudaError_t pm_launch_diag_heat(const pmk::DiagP<T> &d, co
 cudaError_t pm_green_octant(double *h, int nx, int ny, int nz, double q, double h000, cudaStream_t st);
 cudaError_t pm_axis_transform(const double *in, double *out, const double *cmat, int n1,
                               long long outer, long long inner, cudaStream_t st);
+// H-hat table of the z pass from the FP64 octant oct[kzr][kyr][kxr]
+// (scaled by `scale`): for each octant column (kyr, kxr) the L = 2nz values
+// H-hat(kz) in the order the z pass's threads hold the forward transform's
+// outputs (register e of thread t at entry e * L/16 + t), kz > L/2 mirrored.
+inline long long pm_hhat_table_size(int nx, int ny, int nz) { return (long long)(nx + 1) * (ny + 1) * 2 * nz; }
 template <typename T>
-cudaError_t pm_store_hhat(const double *in, T *out, long long n, double scale, cudaStream_t st);
+cudaError_t pm_store_hhat(const double *oct, T *out, int nx, int ny, int nz, double scale, cudaStream_t st);
 
 // Records a message for pm_last_error() and returns code (C++ linkage; for
 // translation units other than the C ABI file).

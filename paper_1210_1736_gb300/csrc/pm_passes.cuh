@@ -182,6 +182,19 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
         : "memory");
 }
 
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, int x, int y, const void *src) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y), "r"(smem_addr(src))
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// Waits until the committed stores have read their shared-memory source.
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// Waits until the committed stores are complete.
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
 // Columns per tile and threads per block of the column passes (shared with
 // the host, which encodes the tensor-map boxes).
 template <typename T, int L> struct CShape {
@@ -203,8 +216,9 @@ template <typename T, int L, int MODE> constexpr size_t col_smem() {
            2 * (size_t)ColRows<MODE>::of(L) * COLS * sizeof(C) + 3 * 128;
 }
 
-// Persistent column pass.  map: 2D tensor map over 8-byte elements whose box
-// is (COLS * EPC, min(rows, 256)); tile t covers COLS columns.
+// Persistent y pass (forward or inverse).  map: 2D tensor map over 8-byte
+// elements whose box is (COLS * EPC, min(rows, 256)); tile t covers COLS
+// columns of one z plane.
 template <typename T, int L, int MODE>
 __global__ void __launch_bounds__(CShape<T, L>::THREADS, 3) k_col(PairArgs a, const __grid_constant__ CUtensorMap map,
                                                                long long ntiles) {
@@ -231,13 +245,8 @@ __global__ void __launch_bounds__(CShape<T, L>::THREADS, 3) k_col(PairArgs a, co
 
     // tile -> TMA coordinates and the first column it covers
     auto coords = [&](long long tile, int &x, int &y) {
-        if (MODE == COL_ZCONV) {
-            x = (int)(tile * COLS * S::EPC);
-            y = 0;
-        } else {
-            x = (int)((tile % tiles_per_z) * COLS * S::EPC);
-            y = (int)((tile / tiles_per_z) * ny2);
-        }
+        x = (int)((tile % tiles_per_z) * COLS * S::EPC);
+        y = (int)((tile / tiles_per_z) * ny2);
     };
     auto issue = [&](long long tile, int b) {
         int x, y;
@@ -298,12 +307,7 @@ __global__ void __launch_bounds__(CShape<T, L>::THREADS, 3) k_col(PairArgs a, co
         bool valid;
         C *col;
         size_t stride;
-        if (MODE == COL_ZCONV) {
-            q = tile * COLS + c;
-            valid = true;   // COLS (a power of two <= 256) divides the 2ny x 2nx >= 256 columns
-            col = work + q;
-            stride = (size_t)ny2 * nx2;
-        } else {
+        {
             const long long z = tile / tiles_per_z, kx = (tile % tiles_per_z) * COLS + c;
             q = kx;
             valid = kx < nx2;
@@ -311,6 +315,7 @@ __global__ void __launch_bounds__(CShape<T, L>::THREADS, 3) k_col(PairArgs a, co
             stride = (size_t)nx2;
         }
 
+        static_assert(MODE == COL_YFWD || MODE == COL_YINV, "the z pass is k_zconv");
         pmfft::fft_core<L, REV_IN, SIGN_IN, MODE != COL_YINV, MODE == COL_YINV>(v, sm, COLS, c, t, tw);
         if (MODE == COL_YFWD) {
             constexpr int RL = radix(L, NS - 1, false);
@@ -324,31 +329,8 @@ __global__ void __launch_bounds__(CShape<T, L>::THREADS, 3) k_col(PairArgs a, co
             }
             continue;
         }
-        if (MODE == COL_ZCONV) {
-            constexpr int RL = radix(L, NS - 1, false);
-            const int ky = (int)(q / nx2), kx = (int)(q % nx2);
-            const int kyr = ky <= a.ny ? ky : ny2 - ky;
-            const int kxr = kx <= a.nx ? kx : nx2 - kx;
-            const int hp = (a.ny + 1) * (a.nx + 1);   // one kz plane of the octant
-            // row kz = t + o of the forward output (o = kk*TPC + r*L/RL, known at
-            // compile time) reads H-hat row kz when kz <= L/2, else L - kz; no
-            // o range straddles L/2, so each register reads one of two bases
-            const T *hrow = static_cast<const T *>(a.hhat) + ((size_t)kyr * (a.nx + 1) + kxr);
-            const T *hd = hrow + (size_t)t * hp;
-            const T *hm = hrow + (size_t)(L - t) * hp;
-#pragma unroll
-            for (int kk = 0; kk < E / RL; ++kk)
-#pragma unroll
-                for (int r = 0; r < RL; ++r) {
-                    const int o = pmfft::in_row<L, NS - 1, false>(0, kk, r);
-                    const T h = (o < L / 2) ? __ldg(hd + o * hp) : __ldg(hm - o * hp);
-                    v[kk * RL + r].x *= h;
-                    v[kk * RL + r].y *= h;
-                }
-            pmfft::fft_core<L, true, 1, false, true>(v, sm, COLS, c, t, tw);
-        }
-        // inverse outputs (COL_ZCONV, COL_YINV): the reversed plan ends with
-        // radix 16, whose outputs below L/2 are registers r < 8
+        // inverse outputs (COL_YINV): the reversed plan ends with radix 16,
+        // whose outputs below L/2 are registers r < 8
         constexpr int RL = radix(L, NS - 1, true);
         if (valid) {
             C *colt = col + (size_t)t * stride;
@@ -359,6 +341,162 @@ __global__ void __launch_bounds__(CShape<T, L>::THREADS, 3) k_col(PairArgs a, co
                     colt[(size_t)pmfft::in_row<L, NS - 1, true>(0, kk, r) * stride] = v[kk * RL + r];
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// z pass with warp-private transforms.  A tile is COLS adjacent (ky, kx)
+// columns, the nz = L/2 input rows of each, brought by TMA into a swizzled
+// buffer of NSUB sub-tiles [rows][SW] (SW columns fill one 32/64/128-byte
+// row; the tensor map's swizzle and this kernel's address function agree).
+// The L/16 threads of a column are consecutive lanes of one warp, so the
+// stage exchanges use a private padded row per column and synchronise the
+// warp only.  The outputs (rows < L/2) are written back into the tile's own
+// input buffer, now consumed, and leave by TMA store; the buffer then takes
+// the prefetch of the tile two steps ahead.  Two block barriers per tile.
+// ---------------------------------------------------------------------------
+template <typename T, int L> struct ZShape {
+    typedef typename cplx_t<T>::type C;
+    static constexpr int TPC = L / E;
+    static constexpr int COLS = pm_col_cols(L, (int)sizeof(T));
+    static constexpr int THREADS = COLS * TPC;
+    static constexpr int SW = pm_zsub_cols(L, (int)sizeof(T));
+    static constexpr int NSUB = COLS / SW;
+    static constexpr int P = SW * (int)sizeof(C);                 // bytes per sub-tile row
+    static constexpr int ROWS = L / 2;
+    static constexpr int BOXR = ROWS < 256 ? ROWS : 256, NBOX = ROWS / BOXR;
+    static constexpr int LDR = L + L / 16;
+    static constexpr int EPC = (int)sizeof(C) / 8;
+    static constexpr unsigned BUF = (unsigned)(ROWS * COLS * sizeof(C));
+};
+
+template <typename T, int L> constexpr size_t zconv_smem() {
+    typedef ZShape<T, L> S;
+    return 1024 + 2 * (size_t)S::BUF + (size_t)S::COLS * S::LDR * sizeof(typename S::C) +
+           (size_t)pmfft::tw_total(L) * sizeof(typename S::C) + 64;
+}
+
+// Byte offset of element (row, column c) of a tile buffer (swizzle of the
+// tensor map: 16-byte chunk index XOR the row's 128-byte line index bits).
+template <typename T, int L>
+__device__ __forceinline__ uint32_t zoff(int row, int c) {
+    typedef ZShape<T, L> S;
+    const uint32_t o = (uint32_t)row * S::P + (uint32_t)(c % S::SW) * (uint32_t)sizeof(typename S::C);
+    const uint32_t sw = S::P >= 32 ? (o ^ (((o >> 7) & (uint32_t)(S::P / 16 - 1)) << 4)) : o;
+    return (uint32_t)(c / S::SW) * (uint32_t)(S::ROWS * S::P) + sw;
+}
+
+template <typename T, int L>
+__global__ void __launch_bounds__(ZShape<T, L>::THREADS, (L >= 512 ? 2 : 3)) k_zconv(PairArgs a, const __grid_constant__ CUtensorMap map,
+                                                                  long long ntiles) {
+    typedef ZShape<T, L> S;
+    typedef typename S::C C;
+    constexpr int NS = nstages(L);
+    extern __shared__ __align__(128) unsigned char smraw[];
+    unsigned char *base = reinterpret_cast<unsigned char *>(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+    C *xch = reinterpret_cast<C *>(base + 2 * S::BUF);
+    C *tw = xch + S::COLS * S::LDR;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(tw + pmfft::tw_total(L));
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int t = lane % S::TPC;
+    const int c = warp * (32 / S::TPC) + lane / S::TPC;   // column within the tile
+    const int nx2 = 2 * a.nx, ny2 = 2 * a.ny;
+    const size_t cols_all = (size_t)nx2 * ny2;
+    (void)cols_all;
+
+    auto issue_load = [&](long long tile, int b) {
+        mbar_expect_tx(&bar[b], S::BUF);
+#pragma unroll
+        for (int s = 0; s < S::NSUB; ++s)
+#pragma unroll
+            for (int k = 0; k < S::NBOX; ++k)
+                tma_load_2d(base + b * S::BUF + s * S::ROWS * S::P + k * S::BOXR * S::P, &map,
+                            (int)((tile * S::COLS + s * S::SW) * S::EPC), k * S::BOXR, &bar[b]);
+    };
+
+    if (tid == 0) {
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map)) : "memory");
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    pmfft::expand_twiddles<L>(tw, static_cast<const C *>(a.tw));
+    __syncthreads();
+    int issued0 = 0, issued1 = 0;   // loads issued per buffer (thread 0's count)
+    if (tid == 0) {
+        if (blockIdx.x < ntiles) { issue_load(blockIdx.x, 0); ++issued0; }
+        if (blockIdx.x + gridDim.x < ntiles) { issue_load(blockIdx.x + gridDim.x, 1); ++issued1; }
+    }
+    const pmfft::RowLayout lay{c * S::LDR};
+    const T *hh = static_cast<const T *>(a.hhat);
+
+    int it = 0;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+        const int b = it & 1;
+        const unsigned phase = (unsigned)((it >> 1) & 1);
+        if (!__syncthreads_and(mbar_wait(&bar[b], phase) ? 1 : 0)) {
+            if (tid == 0) {
+                atomicExch(a.err, 1);
+                const int o = b ^ 1, used_o = it >> 1;
+                if ((o ? issued1 : issued0) > used_o) mbar_wait(&bar[o], (unsigned)(used_o & 1));
+            }
+            break;
+        }
+        unsigned char *in = base + b * S::BUF;
+        C v[E];
+        constexpr int R0 = radix(L, 0, false);
+#pragma unroll
+        for (int kk = 0; kk < E / R0; ++kk)
+#pragma unroll
+            for (int r = 0; r < R0; ++r)
+                v[kk * R0 + r] = (r < R0 / 2)   // inputs above nz are the padding
+                                     ? *reinterpret_cast<const C *>(in + zoff<T, L>(pmfft::in_row<L, 0, false>(t, kk, r), c))
+                                     : czero<C>();
+        __syncthreads();   // (A) the tile's inputs are in registers: its buffer takes its outputs
+
+        const long long q = tile * S::COLS + c;
+        pmfft::fft_core<L, false, -1, true, false, true>(v, xch, lay, t, tw);
+        {
+            // H-hat of column (kyr, kxr) in register order (pm_store_hhat):
+            // the lanes of a column read consecutive values
+            const int ky = (int)(q / nx2), kx = (int)(q % nx2);
+            const int kyr = ky <= a.ny ? ky : ny2 - ky;
+            const int kxr = kx <= a.nx ? kx : nx2 - kx;
+            const T *hz = hh + ((size_t)kyr * (a.nx + 1) + kxr) * L + t;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const T h = __ldg(hz + e * S::TPC);
+                v[e].x *= h;
+                v[e].y *= h;
+            }
+        }
+        pmfft::fft_core<L, true, 1, false, true, true>(v, xch, lay, t, tw);
+        {
+            constexpr int RL = radix(L, NS - 1, true);
+#pragma unroll
+            for (int kk = 0; kk < E / RL; ++kk)
+#pragma unroll
+                for (int r = 0; r < RL / 2; ++r)
+                    *reinterpret_cast<C *>(in + zoff<T, L>(pmfft::in_row<L, NS - 1, true>(t, kk, r), c)) =
+                        v[kk * RL + r];
+        }
+        fence_async_smem();
+        __syncthreads();   // (B) the tile's outputs are staged
+        if (tid == 0) {
+#pragma unroll
+            for (int s = 0; s < S::NSUB; ++s)
+#pragma unroll
+                for (int k = 0; k < S::NBOX; ++k)
+                    tma_store_2d(&map, (int)((tile * S::COLS + s * S::SW) * S::EPC), k * S::BOXR,
+                                 in + s * S::ROWS * S::P + k * S::BOXR * S::P);
+            bulk_commit();
+            if (tile + 2 * (long long)gridDim.x < ntiles) {
+                bulk_wait_read();   // the buffer's outputs have been read out
+                issue_load(tile + 2 * (long long)gridDim.x, b);
+                if (b) ++issued1; else ++issued0;
+            }
+        }
+    }
+    if (tid == 0) bulk_wait_all();
 }
 
 }  // namespace pmk

@@ -80,7 +80,7 @@ int run(const int64_t *rho, void *phi, int nx, int ny, int nz, double l_xy, doub
     size_t off = 0;
     auto take = [&](size_t bytes) { unsigned char *p = base + off; off += up256(bytes); return p; };
     C *work = (C *)take((size_t)nz * 2 * ny * 2 * nx * sizeof(C));
-    T *hhat = (T *)take(oct * sizeof(T));
+    T *hhat = (T *)take((size_t)pm_hhat_table_size(nx, ny, nz) * sizeof(T));
     double *h = (double *)take(oct * sizeof(double));
     double *t1 = (double *)take(oct * sizeof(double));
     double *cm = (double *)take((size_t)nmax * nmax * sizeof(double));
@@ -110,7 +110,7 @@ int run(const int64_t *rho, void *phi, int nx, int ny, int nz, double l_xy, doub
     k_static_cosmat<<<64, 256, 0, st>>>(cm, nz);
     SCK(cudaGetLastError());
     SCK(pm_axis_transform(h, t1, cm, nz + 1, 1, (long long)(ny + 1) * (nx + 1), st));
-    SCK(pm_store_hhat<T>(t1, hhat, (long long)oct, G / (l_xy * 8.0 * nx * ny * nz), st));
+    SCK(pm_store_hhat<T>(t1, hhat, nx, ny, nz, G / (l_xy * 8.0 * nx * ny * nz), st));
 
     CUtensorMap yfwd, yinv, zmap;
     if (pm_encode_col_maps(work, nx, ny, nz, (int)sizeof(T), &yfwd, &yinv, &zmap) != PM_OK) return PM_E_CUDA;
@@ -143,7 +143,8 @@ int run(const int64_t *rho, void *phi, int nx, int ny, int nz, double l_xy, doub
 size_t scratch_bytes(int nx, int ny, int nz, size_t esz) {
     const size_t oct = (size_t)(nx + 1) * (ny + 1) * (nz + 1);
     const size_t nmax = std::max(nx, std::max(ny, nz)) + 1;
-    return up256((size_t)nz * 2 * ny * 2 * nx * 2 * esz) + up256(oct * esz) + 2 * up256(oct * 8) +
+    return up256((size_t)nz * 2 * ny * 2 * nx * 2 * esz) + up256((size_t)pm_hhat_table_size(nx, ny, nz) * esz) +
+           2 * up256(oct * 8) +
            up256(nmax * nmax * 8) + up256(sizeof(int)) + up256((size_t)2 * nx * 2 * esz) +
            up256((size_t)2 * ny * 2 * esz) + up256((size_t)2 * nz * 2 * esz);
 }
