@@ -705,7 +705,7 @@ int pm_encode_col_maps(void *work, int nx, int ny, int nz, int esz, CUtensorMap 
     const unsigned long long epc = esz == 4 ? 1 : 2;   // 8-byte elements per complex value
     const unsigned long long nx2 = 2ull * nx, ny2 = 2ull * ny;
     const unsigned cy = (unsigned)pm_col_cols(2 * ny, esz), sz = (unsigned)pm_zsub_cols(2 * nz, esz);
-    const unsigned zrow = sz * (unsigned)epc * 8;   // bytes per box row: 32, 64 or 128
+    const unsigned zrow = sz * (unsigned)epc * 8;   // bytes per z box row: 32, 64 or 128
     const CUtensorMapSwizzle zswz = zrow >= 128 ? CU_TENSOR_MAP_SWIZZLE_128B
                                     : zrow >= 64 ? CU_TENSOR_MAP_SWIZZLE_64B
                                     : zrow >= 32 ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_NONE;

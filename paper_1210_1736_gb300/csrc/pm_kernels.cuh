@@ -551,6 +551,18 @@ template <typename T, int L, int MODE> int col_blocks_per_sm() {
     return cached;
 }
 
+template <typename T, int L> int colw_blocks_per_sm() {
+    static int cached = 0;
+    if (!cached) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pmk::k_colw<T, L>, pmk::WShape<T, L>::THREADS,
+                                                          pmk::colw_smem<T, L>()) != cudaSuccess || nb < 1)
+            nb = 1;
+        cached = nb;
+    }
+    return cached;
+}
+
 inline int num_sms() {
     static int n = 0;
     if (!n) {
@@ -561,44 +573,42 @@ inline int num_sms() {
     return n;
 }
 
-template <typename T, int L> int zconv_blocks_per_sm() {
-    static int cached = 0;
-    if (!cached) {
-        int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pmk::k_zconv<T, L>, pmk::ZShape<T, L>::THREADS,
-                                                          pmk::zconv_smem<T, L>()) != cudaSuccess || nb < 1)
-            nb = 1;
-        cached = nb;
-    }
-    return cached;
-}
-
 template <typename T, int L> cudaError_t attrs_L() {
     cudaError_t e;
-    e = cudaFuncSetAttribute(pmk::k_zconv<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)pmk::zconv_smem<T, L>());
-    if (e) return e;
-    e = cudaFuncSetAttribute(pmk::k_xfwd<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pmk::xpass_smem<T, L>());
-    if (e) return e;
-    e = cudaFuncSetAttribute(pmk::k_xinv<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pmk::xpass_smem<T, L>());
-    if (e) return e;
     e = cudaFuncSetAttribute(pmk::k_col<T, L, COL_YFWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)pmk::col_smem<T, L, COL_YFWD>());
     if (e) return e;
-    return cudaFuncSetAttribute(pmk::k_col<T, L, COL_YINV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)pmk::col_smem<T, L, COL_YINV>());
+    e = cudaFuncSetAttribute(pmk::k_colw<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)pmk::colw_smem<T, L>());
+    if (e) return e;
+    e = cudaFuncSetAttribute(pmk::k_col<T, L, COL_YINV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)pmk::col_smem<T, L, COL_YINV>());
+    if (e) return e;
+    e = cudaFuncSetAttribute(pmk::k_xfwd<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pmk::xpass_smem<T, L>());
+    if (e) return e;
+    return cudaFuncSetAttribute(pmk::k_xinv<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)pmk::xpass_smem<T, L>());
 }
 
+// Persistent x passes: one wave of blocks (occupancy x SMs), each walking
+// groups of rows.
+template <typename K> int resident_blocks(K kernel, int threads, size_t smem) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, smem) != cudaSuccess || nb < 1) nb = 1;
+    return nb;
+}
 template <typename T, int L> cudaError_t xfwd_L(const PairArgs &a, cudaStream_t st) {
-    const long long rows = (long long)a.ny * a.nz;
-    pmk::k_xfwd<T, L><<<(unsigned)((rows + pmk::XShape<L>::LINES - 1) / pmk::XShape<L>::LINES), pmk::NT,
-                        pmk::xpass_smem<T, L>(), st>>>(a);
+    static int nb = resident_blocks(pmk::k_xfwd<T, L>, pmk::NT, pmk::xpass_smem<T, L>());
+    const long long groups = ((long long)a.ny * a.nz + pmk::XShape<L>::LINES - 1) / pmk::XShape<L>::LINES;
+    const long long grid = std::min(groups, (long long)nb * num_sms());
+    pmk::k_xfwd<T, L><<<(unsigned)grid, pmk::NT, pmk::xpass_smem<T, L>(), st>>>(a);
     return cudaGetLastError();
 }
 template <typename T, int L> cudaError_t xinv_L(const PairArgs &a, cudaStream_t st) {
-    const long long rows = (long long)a.ny * a.nz;
-    pmk::k_xinv<T, L><<<(unsigned)((rows + pmk::XShape<L>::LINES - 1) / pmk::XShape<L>::LINES), pmk::NT,
-                        pmk::xpass_smem<T, L>(), st>>>(a);
+    static int nb = resident_blocks(pmk::k_xinv<T, L>, pmk::NT, pmk::xpass_smem<T, L>());
+    const long long groups = ((long long)a.ny * a.nz + pmk::XShape<L>::LINES - 1) / pmk::XShape<L>::LINES;
+    const long long grid = std::min(groups, (long long)nb * num_sms());
+    pmk::k_xinv<T, L><<<(unsigned)grid, pmk::NT, pmk::xpass_smem<T, L>(), st>>>(a);
     return cudaGetLastError();
 }
 template <typename T, int L, int MODE> cudaError_t col_LM(const PairArgs &a, const CUtensorMap &map, cudaStream_t st) {
@@ -612,12 +622,12 @@ template <typename T, int L, int MODE> cudaError_t col_LM(const PairArgs &a, con
     return cudaGetLastError();
 }
 template <typename T, int L> cudaError_t zconv_L(const PairArgs &a, const CUtensorMap &map, cudaStream_t st) {
-    typedef pmk::ZShape<T, L> S;
+    typedef pmk::WShape<T, L> S;
     const long long ntiles = ((long long)4 * a.ny * a.nx) / S::COLS;   // COLS divides the 2ny x 2nx columns
-    long long grid = (long long)zconv_blocks_per_sm<T, L>() * num_sms();
+    long long grid = (long long)colw_blocks_per_sm<T, L>() * num_sms();
     if (grid > ntiles) grid = ntiles;
     if (grid < 1) grid = 1;
-    pmk::k_zconv<T, L><<<(unsigned)grid, S::THREADS, pmk::zconv_smem<T, L>(), st>>>(a, map, ntiles);
+    pmk::k_colw<T, L><<<(unsigned)grid, S::THREADS, pmk::colw_smem<T, L>(), st>>>(a, map, ntiles);
     return cudaGetLastError();
 }
 template <typename T, int L> cudaError_t col_L(const PairArgs &a, const CUtensorMap &map, int mode, cudaStream_t st) {

@@ -36,15 +36,17 @@ __host__ __device__ constexpr int pm_zsub_cols(int L, int esz) {
 }
 
 // Tensor maps (2D, 8-byte elements) of one pair's work array for the
-// column passes: y forward (box rows ny), y inverse (box rows min(2ny,256)),
-// z (box pm_zsub_cols columns x min(nz,256) rows, swizzled to the box row
-// width, used for the z pass's loads and stores).  Host only; no device
-// memory is touched.
+// column passes: y forward (box pm_col_cols columns x min(ny,256) rows), y
+// inverse (box rows min(2ny,256)), z (box pm_zsub_cols columns x
+// min(nz,256) rows, swizzled to the box row width; the z pass's loads and
+// stores).  Host only; no device memory is touched.
 int pm_encode_col_maps(void *work, int nx, int ny, int nz, int esz, CUtensorMap *yfwd, CUtensorMap *yinv,
                        CUtensorMap *zmap);
 
 template <typename T> cudaError_t pm_set_attrs();
 template <typename T> cudaError_t pm_launch_xfwd(const PairArgs &a, cudaStream_t st);
+// Column pass `mode` with its tensor map (y forward: yfwd, z: zmap, y
+// inverse: yinv).
 template <typename T> cudaError_t pm_launch_col(const PairArgs &a, const CUtensorMap &map, int mode, cudaStream_t st);
 template <typename T> cudaError_t pm_launch_xinv(const PairArgs &a, cudaStream_t st);
 

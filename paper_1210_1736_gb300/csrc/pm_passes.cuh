@@ -15,8 +15,7 @@
 // The column passes are persistent: each block walks tiles of COLS adjacent
 // columns; a TMA tensor copy brings the next-but-one tile's input rows into
 // shared memory (double buffer, mbarrier completion) while the block
-// transforms the current one; outputs go from registers straight to global
-// memory.
+// transforms the current one; the outputs leave by TMA store.
 #pragma once
 
 #include <cuda.h>
@@ -48,7 +47,8 @@ template <typename T, int L> constexpr size_t xpass_smem() {
 // addresses; shared memory only carries the exchanges between stages.
 // ---------------------------------------------------------------------------
 // x forward: z[x] = rho_a + i rho_b (scaled to mass), forward FFT of length
-// L = 2nx, all L outputs written to the row of the work array.
+// L = 2nx, all L outputs written to the row of the work array.  Persistent:
+// each block walks groups of LINES rows (the twiddle tables are built once).
 template <typename T, int L>
 __global__ void __launch_bounds__(NT) k_xfwd(PairArgs a) {
     typedef typename cplx_t<T>::type C;
@@ -59,41 +59,47 @@ __global__ void __launch_bounds__(NT) k_xfwd(PairArgs a) {
     C *sm = tw + pmfft::tw_total(L);
     const int tid = threadIdx.x, line = tid / S::TPC, t = tid % S::TPC;
     pmfft::expand_twiddles<L>(tw, static_cast<const C *>(a.tw));
+    __syncthreads();
     const long long nrows = (long long)a.ny * a.nz;
-    const long long r = (long long)blockIdx.x * S::LINES + line;
-    const bool valid = r < nrows;
+    const long long ngroups = (nrows + S::LINES - 1) / S::LINES;
     const T scale = (T)a.scale;
-    const long long *ra = a.rho_a + (valid ? r * NX : 0);
-    const long long *rb = a.rho_b ? a.rho_b + (valid ? r * NX : 0) : nullptr;
-
-    C v[E];
-    constexpr int R0 = radix(L, 0, false);
+    for (long long grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+        const long long r = grp * S::LINES + line;
+        const bool valid = r < nrows;
+        const long long *ra = a.rho_a + (valid ? r * NX : 0);
+        const long long *rb = a.rho_b ? a.rho_b + (valid ? r * NX : 0) : nullptr;
+        C v[E];
+        constexpr int R0 = radix(L, 0, false);
 #pragma unroll
-    for (int kk = 0; kk < E / R0; ++kk)
+        for (int kk = 0; kk < E / R0; ++kk)
 #pragma unroll
-        for (int q = 0; q < R0; ++q) {
-            C val = czero<C>();
-            if (valid && q < R0 / 2) {   // inputs x >= nx are the zero padding
-                const int x = pmfft::in_row<L, 0, false>(t, kk, q);
-                val.x = (T)ra[x] * scale;
-                if (rb) val.y = (T)rb[x] * scale;
+            for (int q = 0; q < R0; ++q) {
+                C val = czero<C>();
+                if (valid && q < R0 / 2) {   // inputs x >= nx are the zero padding
+                    const int x = pmfft::in_row<L, 0, false>(t, kk, q);
+                    val.x = (T)ra[x] * scale;
+                    if (rb) val.y = (T)rb[x] * scale;
+                }
+                v[kk * R0 + q] = val;
             }
-            v[kk * R0 + q] = val;
+        // the previous group's last exchange ended with a block barrier
+        pmfft::fft_core<L, false, -1, true, false>(v, sm, pmfft::RowLayout{line * S::LDR}, t, tw);
+        if (valid) {
+            const long long z = r / a.ny, y = r % a.ny;
+            C *out = static_cast<C *>(a.work) + ((size_t)z * 2 * a.ny + y) * L;
+            constexpr int RL = radix(L, NS - 1, false);
+#pragma unroll
+            for (int kk = 0; kk < E / RL; ++kk)
+#pragma unroll
+                for (int q = 0; q < RL; ++q) out[pmfft::in_row<L, NS - 1, false>(t, kk, q)] = v[kk * RL + q];
         }
-    __syncthreads();   // twiddles
-    pmfft::fft_core<L, false, -1, true, false>(v, sm, pmfft::RowLayout{line * S::LDR}, t, tw);
-    if (!valid) return;
-    const long long z = r / a.ny, y = r % a.ny;
-    C *out = static_cast<C *>(a.work) + ((size_t)z * 2 * a.ny + y) * L;
-    constexpr int RL = radix(L, NS - 1, false);
-#pragma unroll
-    for (int kk = 0; kk < E / RL; ++kk)
-#pragma unroll
-        for (int q = 0; q < RL; ++q) out[pmfft::in_row<L, NS - 1, false>(t, kk, q)] = v[kk * RL + q];
+        if (NS == 1) __syncthreads();   // single-stage transforms use no exchange
+    }
 }
 
 // x inverse: inverse FFT of length L = 2nx of each row y < ny; x < nx kept:
-// Phi_b = Im, Phi_sum = Re + Im (or Re without partner).
+// Phi_b = Im, Phi_sum = Re + Im (or Re without partner).  Persistent as
+// k_xfwd.
 template <typename T, int L>
 __global__ void __launch_bounds__(NT) k_xinv(PairArgs a) {
     typedef typename cplx_t<T>::type C;
@@ -104,38 +110,42 @@ __global__ void __launch_bounds__(NT) k_xinv(PairArgs a) {
     C *sm = tw + pmfft::tw_total(L);
     const int tid = threadIdx.x, line = tid / S::TPC, t = tid % S::TPC;
     pmfft::expand_twiddles<L>(tw, static_cast<const C *>(a.tw));
+    __syncthreads();
     const long long nrows = (long long)a.ny * a.nz;
-    const long long r = (long long)blockIdx.x * S::LINES + line;
-    const bool valid = r < nrows;
-    const long long z = valid ? r / a.ny : 0, y = valid ? r % a.ny : 0;
-    const C *in = static_cast<const C *>(a.work) + ((size_t)z * 2 * a.ny + y) * L;
-
-    C v[E];
-    constexpr int R0 = radix(L, 0, true);
-#pragma unroll
-    for (int kk = 0; kk < E / R0; ++kk)
-#pragma unroll
-        for (int q = 0; q < R0; ++q)
-            v[kk * R0 + q] = valid ? in[pmfft::in_row<L, 0, true>(t, kk, q)] : czero<C>();
-    __syncthreads();   // twiddles
-    pmfft::fft_core<L, true, 1, false, true>(v, sm, pmfft::RowLayout{line * S::LDR}, t, tw);
-    if (!valid) return;
+    const long long ngroups = (nrows + S::LINES - 1) / S::LINES;
     T *phi_b = static_cast<T *>(a.phi_b);
-    T *phi_s = static_cast<T *>(a.phi_sum) + r * NX;
-    constexpr int RL = radix(L, NS - 1, true);
+    for (long long grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+        const long long r = grp * S::LINES + line;
+        const bool valid = r < nrows;
+        const long long z = valid ? r / a.ny : 0, y = valid ? r % a.ny : 0;
+        const C *in = static_cast<const C *>(a.work) + ((size_t)z * 2 * a.ny + y) * L;
+        C v[E];
+        constexpr int R0 = radix(L, 0, true);
 #pragma unroll
-    for (int kk = 0; kk < E / RL; ++kk)
+        for (int kk = 0; kk < E / R0; ++kk)
 #pragma unroll
-        for (int q = 0; q < RL / 2; ++q) {   // outputs x < nx: registers q < 8 of the radix-16 last stage
-            const int x = pmfft::in_row<L, NS - 1, true>(t, kk, q);
-            const C val = v[kk * RL + q];
-            if (phi_b) {
-                phi_b[r * NX + x] = val.y;
-                phi_s[x] = val.x + val.y;
-            } else {
-                phi_s[x] = val.x;
-            }
+            for (int q = 0; q < R0; ++q)
+                v[kk * R0 + q] = valid ? in[pmfft::in_row<L, 0, true>(t, kk, q)] : czero<C>();
+        pmfft::fft_core<L, true, 1, false, true>(v, sm, pmfft::RowLayout{line * S::LDR}, t, tw);
+        if (valid) {
+            T *phi_s = static_cast<T *>(a.phi_sum) + r * NX;
+            constexpr int RL = radix(L, NS - 1, true);
+#pragma unroll
+            for (int kk = 0; kk < E / RL; ++kk)
+#pragma unroll
+                for (int q = 0; q < RL / 2; ++q) {   // outputs x < nx: registers q < 8 of the radix-16 last stage
+                    const int x = pmfft::in_row<L, NS - 1, true>(t, kk, q);
+                    const C val = v[kk * RL + q];
+                    if (phi_b) {
+                        phi_b[r * NX + x] = val.y;
+                        phi_s[x] = val.x + val.y;
+                    } else {
+                        phi_s[x] = val.x;
+                    }
+                }
         }
+        if (NS == 1) __syncthreads();
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -145,6 +155,9 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)
 
 __device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
@@ -343,18 +356,21 @@ __global__ void __launch_bounds__(CShape<T, L>::THREADS, 3) k_col(PairArgs a, co
     }
 }
 
+
 // ---------------------------------------------------------------------------
-// z pass with warp-private transforms.  A tile is COLS adjacent (ky, kx)
-// columns, the nz = L/2 input rows of each, brought by TMA into a swizzled
-// buffer of NSUB sub-tiles [rows][SW] (SW columns fill one 32/64/128-byte
-// row; the tensor map's swizzle and this kernel's address function agree).
-// The L/16 threads of a column are consecutive lanes of one warp, so the
-// stage exchanges use a private padded row per column and synchronise the
-// warp only.  The outputs (rows < L/2) are written back into the tile's own
-// input buffer, now consumed, and leave by TMA store; the buffer then takes
-// the prefetch of the tile two steps ahead.  Two block barriers per tile.
+// z pass (forward z FFT, times H-hat, inverse z FFT) with warp-private
+// transforms.  A tile is COLS adjacent (ky, kx) columns whose nz = L/2 input
+// rows a TMA copy brings into a swizzled buffer of NSUB sub-tiles [rows][SW]
+// (SW columns fill one 32/64/128-byte row; the tensor map's swizzle and this
+// kernel's address function agree, so the first-stage reads are free of bank
+// conflicts).  The L/16 threads of a column are consecutive lanes of one
+// warp, so the stage exchanges use a private padded row per column and
+// synchronise the warp only.  The outputs (rows < L/2) are staged into the
+// tile's own, consumed buffer and leave by TMA store; the buffer then takes
+// the prefetch of the tile two steps ahead.  (The same structure measured
+// slower than k_col for the y passes, so those stay there.)
 // ---------------------------------------------------------------------------
-template <typename T, int L> struct ZShape {
+template <typename T, int L> struct WShape {
     typedef typename cplx_t<T>::type C;
     static constexpr int TPC = L / E;
     static constexpr int COLS = pm_col_cols(L, (int)sizeof(T));
@@ -362,83 +378,100 @@ template <typename T, int L> struct ZShape {
     static constexpr int SW = pm_zsub_cols(L, (int)sizeof(T));
     static constexpr int NSUB = COLS / SW;
     static constexpr int P = SW * (int)sizeof(C);                 // bytes per sub-tile row
-    static constexpr int ROWS = L / 2;
-    static constexpr int BOXR = ROWS < 256 ? ROWS : 256, NBOX = ROWS / BOXR;
+    static constexpr int RIN = L / 2;                             // input and output rows per column
+    static constexpr int BOXI = RIN < 256 ? RIN : 256, NBOXI = RIN / BOXI;
     static constexpr int LDR = L + L / 16;
     static constexpr int EPC = (int)sizeof(C) / 8;
-    static constexpr unsigned BUF = (unsigned)(ROWS * COLS * sizeof(C));
+    static constexpr unsigned BUF = (unsigned)(RIN * COLS * sizeof(C));
+    // the longest transform runs two blocks per SM with the warps decoupled
+    // (thread 0 sends a tile once every warp has arrived on its barrier); the
+    // others measured faster with two block barriers per tile
+    static constexpr bool FREE = L >= 512;
 };
 
-template <typename T, int L> constexpr size_t zconv_smem() {
-    typedef ZShape<T, L> S;
+template <typename T, int L> constexpr size_t colw_smem() {
+    typedef WShape<T, L> S;
     return 1024 + 2 * (size_t)S::BUF + (size_t)S::COLS * S::LDR * sizeof(typename S::C) +
            (size_t)pmfft::tw_total(L) * sizeof(typename S::C) + 64;
 }
 
-// Byte offset of element (row, column c) of a tile buffer (swizzle of the
-// tensor map: 16-byte chunk index XOR the row's 128-byte line index bits).
-template <typename T, int L>
-__device__ __forceinline__ uint32_t zoff(int row, int c) {
-    typedef ZShape<T, L> S;
+// Byte offset of element (row, column c) of a tile buffer whose sub-tiles
+// hold ROWS rows (swizzle of the tensor map: the 16-byte chunk index XOR the
+// index bits of the 128-byte line).
+template <typename T, int L, int ROWS>
+__device__ __forceinline__ uint32_t woff(int row, int c) {
+    typedef WShape<T, L> S;
     const uint32_t o = (uint32_t)row * S::P + (uint32_t)(c % S::SW) * (uint32_t)sizeof(typename S::C);
     const uint32_t sw = S::P >= 32 ? (o ^ (((o >> 7) & (uint32_t)(S::P / 16 - 1)) << 4)) : o;
-    return (uint32_t)(c / S::SW) * (uint32_t)(S::ROWS * S::P) + sw;
+    return (uint32_t)(c / S::SW) * (uint32_t)(ROWS * S::P) + sw;
 }
 
+// map: boxes (SW*EPC, min(nz, 256)), for the loads and the stores.
 template <typename T, int L>
-__global__ void __launch_bounds__(ZShape<T, L>::THREADS, (L >= 512 ? 2 : 3)) k_zconv(PairArgs a, const __grid_constant__ CUtensorMap map,
-                                                                  long long ntiles) {
-    typedef ZShape<T, L> S;
+__global__ void __launch_bounds__(WShape<T, L>::THREADS, (L >= 512 ? 2 : 3))
+    k_colw(PairArgs a, const __grid_constant__ CUtensorMap map, long long ntiles) {
+    typedef WShape<T, L> S;
     typedef typename S::C C;
-    constexpr int NS = nstages(L);
+    constexpr int NS = nstages(L), NWARPS = S::THREADS / 32;
+    constexpr bool FREE = S::FREE;
     extern __shared__ __align__(128) unsigned char smraw[];
     unsigned char *base = reinterpret_cast<unsigned char *>(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
     C *xch = reinterpret_cast<C *>(base + 2 * S::BUF);
     C *tw = xch + S::COLS * S::LDR;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(tw + pmfft::tw_total(L));
+    uint64_t *full = reinterpret_cast<uint64_t *>(tw + pmfft::tw_total(L));   // tile loaded (tx bytes)
+    uint64_t *staged = full + 2;                                            // every warp staged (FREE)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int t = lane % S::TPC;
     const int c = warp * (32 / S::TPC) + lane / S::TPC;   // column within the tile
     const int nx2 = 2 * a.nx, ny2 = 2 * a.ny;
-    const size_t cols_all = (size_t)nx2 * ny2;
-    (void)cols_all;
 
+    // tile <-> sub-tiles of the buffer, each NBOXI boxes of BOXI rows
     auto issue_load = [&](long long tile, int b) {
-        mbar_expect_tx(&bar[b], S::BUF);
+        mbar_expect_tx(&full[b], S::BUF);
 #pragma unroll
         for (int s = 0; s < S::NSUB; ++s)
 #pragma unroll
-            for (int k = 0; k < S::NBOX; ++k)
-                tma_load_2d(base + b * S::BUF + s * S::ROWS * S::P + k * S::BOXR * S::P, &map,
-                            (int)((tile * S::COLS + s * S::SW) * S::EPC), k * S::BOXR, &bar[b]);
+            for (int k = 0; k < S::NBOXI; ++k)
+                tma_load_2d(base + b * S::BUF + s * S::RIN * S::P + k * S::BOXI * S::P, &map,
+                            (int)((tile * S::COLS + s * S::SW) * S::EPC), k * S::BOXI, &full[b]);
+    };
+    auto issue_store = [&](long long tile, const unsigned char *src) {
+#pragma unroll
+        for (int s = 0; s < S::NSUB; ++s)
+#pragma unroll
+            for (int k = 0; k < S::NBOXI; ++k)
+                tma_store_2d(&map, (int)((tile * S::COLS + s * S::SW) * S::EPC), k * S::BOXI,
+                             src + s * S::RIN * S::P + k * S::BOXI * S::P);
     };
 
     if (tid == 0) {
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map)) : "memory");
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
+        mbar_init(&staged[0], NWARPS);
+        mbar_init(&staged[1], NWARPS);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     pmfft::expand_twiddles<L>(tw, static_cast<const C *>(a.tw));
     __syncthreads();
-    int issued0 = 0, issued1 = 0;   // loads issued per buffer (thread 0's count)
+    // thread 0 issues every copy; counts per buffer of loads issued and of
+    // tiles sent (to drain after an expired wait)
+    int issued0 = 0, issued1 = 0, done0 = 0, done1 = 0;
     if (tid == 0) {
         if (blockIdx.x < ntiles) { issue_load(blockIdx.x, 0); ++issued0; }
         if (blockIdx.x + gridDim.x < ntiles) { issue_load(blockIdx.x + gridDim.x, 1); ++issued1; }
     }
     const pmfft::RowLayout lay{c * S::LDR};
-    const T *hh = static_cast<const T *>(a.hhat);
+    bool failed = false;
 
     int it = 0;
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
         const int b = it & 1;
         const unsigned phase = (unsigned)((it >> 1) & 1);
-        if (!__syncthreads_and(mbar_wait(&bar[b], phase) ? 1 : 0)) {
-            if (tid == 0) {
-                atomicExch(a.err, 1);
-                const int o = b ^ 1, used_o = it >> 1;
-                if ((o ? issued1 : issued0) > used_o) mbar_wait(&bar[o], (unsigned)(used_o & 1));
-            }
+        if (FREE) {
+            if (!mbar_wait(&full[b], phase)) { failed = true; break; }
+        } else if (!__syncthreads_and(mbar_wait(&full[b], phase) ? 1 : 0)) {
+            failed = true;
             break;
         }
         unsigned char *in = base + b * S::BUF;
@@ -449,54 +482,70 @@ __global__ void __launch_bounds__(ZShape<T, L>::THREADS, (L >= 512 ? 2 : 3)) k_z
 #pragma unroll
             for (int r = 0; r < R0; ++r)
                 v[kk * R0 + r] = (r < R0 / 2)   // inputs above nz are the padding
-                                     ? *reinterpret_cast<const C *>(in + zoff<T, L>(pmfft::in_row<L, 0, false>(t, kk, r), c))
+                                     ? *reinterpret_cast<const C *>(
+                                           in + woff<T, L, S::RIN>(pmfft::in_row<L, 0, false>(t, kk, r), c))
                                      : czero<C>();
-        __syncthreads();   // (A) the tile's inputs are in registers: its buffer takes its outputs
+        // A column's elements are touched only by the lanes of that column,
+        // and the exchanges synchronise the warp, so the outputs may
+        // overwrite this buffer without a block barrier; the block-synchronous
+        // variant keeps the warps in step.
+        if (!FREE) __syncthreads();
 
-        const long long q = tile * S::COLS + c;
         pmfft::fft_core<L, false, -1, true, false, true>(v, xch, lay, t, tw);
         {
             // H-hat of column (kyr, kxr) in register order (pm_store_hhat):
             // the lanes of a column read consecutive values
+            const long long q = tile * S::COLS + c;
             const int ky = (int)(q / nx2), kx = (int)(q % nx2);
             const int kyr = ky <= a.ny ? ky : ny2 - ky;
             const int kxr = kx <= a.nx ? kx : nx2 - kx;
-            const T *hz = hh + ((size_t)kyr * (a.nx + 1) + kxr) * L + t;
+            const T *hz = static_cast<const T *>(a.hhat) + ((size_t)kyr * (a.nx + 1) + kxr) * L + t;
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 const T h = __ldg(hz + e * S::TPC);
                 v[e].x *= h;
                 v[e].y *= h;
             }
+            pmfft::fft_core<L, true, 1, false, true, true>(v, xch, lay, t, tw);
         }
-        pmfft::fft_core<L, true, 1, false, true, true>(v, xch, lay, t, tw);
         {
+            // inverse outputs below L/2: registers r < RL/2 of the radix-16
+            // last stage of the reversed plan
             constexpr int RL = radix(L, NS - 1, true);
 #pragma unroll
             for (int kk = 0; kk < E / RL; ++kk)
 #pragma unroll
                 for (int r = 0; r < RL / 2; ++r)
-                    *reinterpret_cast<C *>(in + zoff<T, L>(pmfft::in_row<L, NS - 1, true>(t, kk, r), c)) =
+                    *reinterpret_cast<C *>(in + woff<T, L, S::RIN>(pmfft::in_row<L, NS - 1, true>(t, kk, r), c)) =
                         v[kk * RL + r];
         }
-        fence_async_smem();
-        __syncthreads();   // (B) the tile's outputs are staged
+        fence_async_smem();   // the staged outputs are visible to the tensor copies
+        if (FREE) {
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&staged[b]);
+        } else {
+            __syncthreads();
+        }
         if (tid == 0) {
-#pragma unroll
-            for (int s = 0; s < S::NSUB; ++s)
-#pragma unroll
-                for (int k = 0; k < S::NBOX; ++k)
-                    tma_store_2d(&map, (int)((tile * S::COLS + s * S::SW) * S::EPC), k * S::BOXR,
-                                 in + s * S::ROWS * S::P + k * S::BOXR * S::P);
+            if (FREE && !mbar_wait(&staged[b], phase)) { failed = true; break; }
+            issue_store(tile, in);
             bulk_commit();
+            if (b) ++done1; else ++done0;
+            bulk_wait_read();   // the staged outputs have been read out
             if (tile + 2 * (long long)gridDim.x < ntiles) {
-                bulk_wait_read();   // the buffer's outputs have been read out
                 issue_load(tile + 2 * (long long)gridDim.x, b);
                 if (b) ++issued1; else ++issued0;
             }
         }
     }
-    if (tid == 0) bulk_wait_all();
+    if (failed) atomicExch(a.err, 1);
+    if (tid == 0) {
+        bulk_wait_all();
+        // loads still in flight after an expired wait land before the block
+        // leaves (bounded)
+        if (issued0 > done0) mbar_wait(&full[0], (unsigned)(done0 & 1));
+        if (issued1 > done1) mbar_wait(&full[1], (unsigned)(done1 & 1));
+    }
 }
 
 }  // namespace pmk
