@@ -44,7 +44,8 @@ template <typename T, int L> constexpr size_t xpass_smem() {
 // x passes: the TPC = L/16 threads of a row are consecutive lanes, so a
 // stage's inputs (rows t + k L/R) and the natural-order outputs are read and
 // written straight between global memory and registers with warp-contiguous
-// addresses; shared memory only carries the exchanges between stages.
+// addresses; shared memory only carries the exchanges between stages, in a
+// padded row private to the row's warp.
 // ---------------------------------------------------------------------------
 // x forward: z[x] = rho_a + i rho_b (scaled to mass), forward FFT of length
 // L = 2nx, all L outputs written to the row of the work array.  Persistent:
@@ -82,8 +83,9 @@ __global__ void __launch_bounds__(NT) k_xfwd(PairArgs a) {
                 }
                 v[kk * R0 + q] = val;
             }
-        // the previous group's last exchange ended with a block barrier
-        pmfft::fft_core<L, false, -1, true, false>(v, sm, pmfft::RowLayout{line * S::LDR}, t, tw);
+        // a row's TPC threads are consecutive lanes of one warp and its
+        // exchange row is private: the exchanges synchronise the warp only
+        pmfft::fft_core<L, false, -1, true, false, true>(v, sm, pmfft::RowLayout{line * S::LDR}, t, tw);
         if (valid) {
             const long long z = r / a.ny, y = r % a.ny;
             C *out = static_cast<C *>(a.work) + ((size_t)z * 2 * a.ny + y) * L;
@@ -93,7 +95,6 @@ __global__ void __launch_bounds__(NT) k_xfwd(PairArgs a) {
 #pragma unroll
                 for (int q = 0; q < RL; ++q) out[pmfft::in_row<L, NS - 1, false>(t, kk, q)] = v[kk * RL + q];
         }
-        if (NS == 1) __syncthreads();   // single-stage transforms use no exchange
     }
 }
 
@@ -126,7 +127,7 @@ __global__ void __launch_bounds__(NT) k_xinv(PairArgs a) {
 #pragma unroll
             for (int q = 0; q < R0; ++q)
                 v[kk * R0 + q] = valid ? in[pmfft::in_row<L, 0, true>(t, kk, q)] : czero<C>();
-        pmfft::fft_core<L, true, 1, false, true>(v, sm, pmfft::RowLayout{line * S::LDR}, t, tw);
+        pmfft::fft_core<L, true, 1, false, true, true>(v, sm, pmfft::RowLayout{line * S::LDR}, t, tw);
         if (valid) {
             T *phi_s = static_cast<T *>(a.phi_sum) + r * NX;
             constexpr int RL = radix(L, NS - 1, true);
@@ -144,7 +145,6 @@ __global__ void __launch_bounds__(NT) k_xinv(PairArgs a) {
                     }
                 }
         }
-        if (NS == 1) __syncthreads();
     }
 }
 
