@@ -86,6 +86,11 @@ GeomK make_geomk(const pm_geometry &g) {
     k.c_hzz = 1.0 / (g.l_z * g.l_z);
     k.c_mxy = 1.0 / (4.0 * g.l_xy * g.l_xy);
     k.c_mxz = 1.0 / (4.0 * g.l_xy * g.l_z);
+    k.flxy = (float)k.lxy; k.flz = (float)k.lz;
+    k.fc_gx = (float)k.c_gx; k.fc_gz = (float)k.c_gz;
+    k.fc_hxx = (float)k.c_hxx; k.fc_hzz = (float)k.c_hzz;
+    k.fc_mxy = (float)k.c_mxy; k.fc_mxz = (float)k.c_mxz;
+    k.fil_xy = (float)(2.0 * k.c_gx); k.fil_z = (float)(2.0 * k.c_gz);
     return k;
 }
 

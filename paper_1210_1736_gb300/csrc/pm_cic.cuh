@@ -42,8 +42,8 @@ __device__ __forceinline__ Cic<T> cic_cell(const GeomK &g, const Cell &cl, T rx,
     T d[3];
     cell_delta(g, cl, rx, ry, rz, d[0], d[1], d[2]);
     Cic<T> c;
-    c.il[0] = c.il[1] = (T)(2.0 * g.c_gx);
-    c.il[2] = (T)(2.0 * g.c_gz);
+    c.il[0] = c.il[1] = pick<T>(2.0 * g.c_gx, g.fil_xy);
+    c.il[2] = pick<T>(2.0 * g.c_gz, g.fil_z);
     int idx[3] = {cl.i, cl.j, cl.k};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(256) k_cic_deposit(PartK<T> p, const __grid_co
         Cell cf, cm;
         const int reg = pm_region(G, pm_canon(x, ce.c[0], ce.hi[0], ce.lo[0]), pm_canon(y, ce.c[1], ce.hi[1], ce.lo[1]),
                                   pm_canon(z, ce.c[2], ce.hi[2], ce.lo[2]), cf, cm);
-        const T m = p.m[i], qs = (T)s.mscale;
+        const T m = p.m[i], qs = pick<T>(s.mscale, s.mscale_f);
         const Cic<T> kc = cic_cell<T>(G.coarse, cc, rs.rsx, rs.rsy, rs.rsz);
         if (reg == REG_OUTER) {
             cic_spread_mass<T>(G.coarse, G.rho[4], kc, m, qs);
@@ -307,17 +307,17 @@ __global__ void __launch_bounds__(256) k_cic_field(PartK<T> p, const __grid_cons
                 if (reg == REG_CORE) kf = cic_cell<T>(G.fine, cf, rx, ry, rz);
             }
             if (MODE == 3) {
-                T hp[3] = {u[0] * (T)G.coarse.c_gx, u[1] * (T)G.coarse.c_gx, u[2] * (T)G.coarse.c_gz};
+                T hp[3] = {u[0] * pick<T>(G.coarse.c_gx, G.coarse.fc_gx), u[1] * pick<T>(G.coarse.c_gx, G.coarse.fc_gx), u[2] * pick<T>(G.coarse.c_gz, G.coarse.fc_gz)};
                 T hm[3] = {-hp[0], -hp[1], -hp[2]};
                 cic_spread_adj<T>(G.coarse, G.rho[4], kc, hp, qs);         // psi_5 (all points)
                 if (reg == REG_OUTER) continue;
                 cic_spread_adj<T>(G.coarse, G.rho[3], kc, hm, qs);         // psi_4 - psi_5
-                T mp[3] = {u[0] * (T)G.med.c_gx, u[1] * (T)G.med.c_gx, u[2] * (T)G.med.c_gz};
+                T mp[3] = {u[0] * pick<T>(G.med.c_gx, G.med.fc_gx), u[1] * pick<T>(G.med.c_gx, G.med.fc_gx), u[2] * pick<T>(G.med.c_gz, G.med.fc_gz)};
                 cic_spread_adj<T>(G.med, G.rho[2], km, mp, qs);            // psi_3 (core, shell)
                 if (reg == REG_CORE) {
                     T mm[3] = {-mp[0], -mp[1], -mp[2]};
                     cic_spread_adj<T>(G.med, G.rho[1], km, mm, qs);        // psi_2 - psi_3
-                    T fp[3] = {u[0] * (T)G.fine.c_gx, u[1] * (T)G.fine.c_gx, u[2] * (T)G.fine.c_gz};
+                    T fp[3] = {u[0] * pick<T>(G.fine.c_gx, G.fine.fc_gx), u[1] * pick<T>(G.fine.c_gx, G.fine.fc_gx), u[2] * pick<T>(G.fine.c_gz, G.fine.fc_gz)};
                     cic_spread_adj<T>(G.fine, G.rho[0], kf, fp, qs);       // psi_1
                 }
                 continue;

@@ -22,7 +22,17 @@ struct GeomK {
     double c_gx, c_gz;     // 1/(2 l_xy), 1/(2 l_z)         central difference
     double c_hxx, c_hzz;   // 1/l_xy^2, 1/l_z^2              second difference
     double c_mxy, c_mxz;   // 1/(4 l_xy l_xy), 1/(4 l_xy l_z) mixed difference
+    // the same rounded to FP32, so that FP32 kernels convert nothing per
+    // particle (double arithmetic, conversions included, is slow on GB300)
+    float flxy, flz, fc_gx, fc_gz, fc_hxx, fc_hzz, fc_mxy, fc_mxz;
+    float fil_xy, fil_z;   // (float)(1/l_xy), (float)(1/l_z)
 };
+
+// A geometry coefficient in the working precision: the FP64 value for
+// double kernels, its FP32 copy for float kernels.
+template <typename T> __device__ __forceinline__ T pick(double d, float f);
+template <> __device__ __forceinline__ float pick<float>(double, float f) { return f; }
+template <> __device__ __forceinline__ double pick<double>(double d, float) { return d; }
 
 struct GalK {
     GeomK fine, med, coarse;   // nx == 0: absent

@@ -112,13 +112,13 @@ __device__ __forceinline__ void stencil(const GeomK &g, const T *__restrict__ P1
     const T xp = ld(1, 0, 0), xm = ld(-1, 0, 0);
     const T yp = ld(0, 1, 0), ym = ld(0, -1, 0);
     const T zp = ld(0, 0, 1), zm = ld(0, 0, -1);
-    const T mxy = (ld(1, 1, 0) - ld(-1, 1, 0) + ld(-1, -1, 0) - ld(1, -1, 0)) * (T)g.c_mxy;
-    const T mxz = (ld(1, 0, 1) - ld(-1, 0, 1) + ld(-1, 0, -1) - ld(1, 0, -1)) * (T)g.c_mxz;
-    const T myz = (ld(0, 1, 1) - ld(0, -1, 1) + ld(0, -1, -1) - ld(0, 1, -1)) * (T)g.c_mxz;
-    const T gx = (xp - xm) * (T)g.c_gx, gy = (yp - ym) * (T)g.c_gx, gz = (zp - zm) * (T)g.c_gz;
-    const T hxx = (xp + xm - 2 * p0) * (T)g.c_hxx;
-    const T hyy = (yp + ym - 2 * p0) * (T)g.c_hxx;
-    const T hzz = (zp + zm - 2 * p0) * (T)g.c_hzz;
+    const T mxy = (ld(1, 1, 0) - ld(-1, 1, 0) + ld(-1, -1, 0) - ld(1, -1, 0)) * pick<T>(g.c_mxy, g.fc_mxy);
+    const T mxz = (ld(1, 0, 1) - ld(-1, 0, 1) + ld(-1, 0, -1) - ld(1, 0, -1)) * pick<T>(g.c_mxz, g.fc_mxz);
+    const T myz = (ld(0, 1, 1) - ld(0, -1, 1) + ld(0, -1, -1) - ld(0, 1, -1)) * pick<T>(g.c_mxz, g.fc_mxz);
+    const T gx = (xp - xm) * pick<T>(g.c_gx, g.fc_gx), gy = (yp - ym) * pick<T>(g.c_gx, g.fc_gx), gz = (zp - zm) * pick<T>(g.c_gz, g.fc_gz);
+    const T hxx = (xp + xm - 2 * p0) * pick<T>(g.c_hxx, g.fc_hxx);
+    const T hyy = (yp + ym - 2 * p0) * pick<T>(g.c_hxx, g.fc_hxx);
+    const T hzz = (zp + zm - 2 * p0) * pick<T>(g.c_hzz, g.fc_hzz);
     acc[0] += gx + hxx * dx + mxy * dy + mxz * dz;
     acc[1] += gy + hyy * dy + mxy * dx + myz * dz;
     acc[2] += gz + hzz * dz + mxz * dx + myz * dy;

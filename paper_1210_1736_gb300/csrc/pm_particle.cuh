@@ -34,9 +34,9 @@ __device__ __forceinline__ double rel_off(double x, double c, float, float) { re
 // Offset of a particle from the centre of its cell (Delta of Eq. eqn:diff).
 template <typename T>
 __device__ __forceinline__ void cell_delta(const GeomK &g, const Cell &cl, T rx, T ry, T rz, T &dx, T &dy, T &dz) {
-    dx = rx - (T)(cl.i - (g.nx >> 1)) * (T)g.lxy;
-    dy = ry - (T)(cl.j - (g.ny >> 1)) * (T)g.lxy;
-    dz = rz - (T)(cl.k - (g.nz >> 1)) * (T)g.lz;
+    dx = rx - (T)(cl.i - (g.nx >> 1)) * pick<T>(g.lxy, g.flxy);
+    dy = ry - (T)(cl.j - (g.ny >> 1)) * pick<T>(g.lxy, g.flxy);
+    dz = rz - (T)(cl.k - (g.nz >> 1)) * pick<T>(g.lz, g.flz);
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
