@@ -12,22 +12,34 @@ namespace pmk {
 // parameter (read through the constant cache, no staging); the centres of
 // grids 1-3 are read from device memory.
 // ---------------------------------------------------------------------------
-// Adds q (two's complement int64) to *addr for every lane with active set;
-// lanes that target the same address are combined first (exact: the sum is
-// taken mod 2^64 from four 16-bit chunk sums), so a warp of particles in one
-// cell issues one atomic.  Every lane of the warp must call it.
+// Adds q (two's complement int64) to *addr for every lane with active set.
+// After the spatial sort, lanes that target the same cell are mostly
+// adjacent: each run of adjacent active lanes with one address (found with
+// one shuffle of the address and a ballot) is summed exactly -- mod 2^64,
+// from three chunk sums of 22, 21 and 21 bits, each below 2^32 for 32
+// lanes -- and its first lane issues one atomic.  Lanes with one address
+// that are not adjacent form separate runs (still exact).  Every lane of the
+// warp must call it.
 __device__ __forceinline__ void agg_add(unsigned long long *addr, unsigned long long q, bool active) {
-    const unsigned mask = __ballot_sync(0xffffffffu, active);
+    const unsigned FULL = 0xffffffffu;
+    const int lane = (int)(threadIdx.x & 31);
+    const unsigned long long key = active ? (unsigned long long)addr : 0ull;   // no cell lives at address 0
+    const unsigned plo = __shfl_up_sync(FULL, (unsigned)key, 1), phi = __shfl_up_sync(FULL, (unsigned)(key >> 32), 1);
+    const bool head = active && (lane == 0 || plo != (unsigned)key || phi != (unsigned)(key >> 32));
+    const unsigned act = __ballot_sync(FULL, active), heads = __ballot_sync(FULL, head);
     if (!active) return;
-    const unsigned peers = __match_any_sync(mask, (unsigned long long)addr);
-    if (__popc(peers) == 1) { atomicAdd(addr, q); return; }
-    const unsigned s0 = __reduce_add_sync(peers, (unsigned)(q & 0xffffu));
-    const unsigned s1 = __reduce_add_sync(peers, (unsigned)((q >> 16) & 0xffffu));
-    const unsigned s2 = __reduce_add_sync(peers, (unsigned)((q >> 32) & 0xffffu));
-    const unsigned s3 = __reduce_add_sync(peers, (unsigned)(q >> 48));
-    if ((int)(threadIdx.x & 31) == __ffs(peers) - 1)
-        atomicAdd(addr, (unsigned long long)s0 + ((unsigned long long)s1 << 16) + ((unsigned long long)s2 << 32) +
-                            ((unsigned long long)s3 << 48));
+    const unsigned upto = lane == 31 ? FULL : ((2u << lane) - 1u);   // lanes 0..lane
+    const int h = 31 - __clz(heads & upto);                          // this run's head
+    const unsigned after = heads & ~upto;
+    const int nx = after ? __ffs(after) - 1 : 32;                     // next run's head
+    const unsigned run = (nx == 32 ? FULL : ((1u << nx) - 1u)) & ~((1u << h) - 1u);
+    const unsigned peers = run & act;
+    if (peers == (1u << lane)) { atomicAdd(addr, q); return; }
+    const unsigned s0 = __reduce_add_sync(peers, (unsigned)(q & 0x3fffffu));
+    const unsigned s1 = __reduce_add_sync(peers, (unsigned)((q >> 22) & 0x1fffffu));
+    const unsigned s2 = __reduce_add_sync(peers, (unsigned)(q >> 43));
+    if (lane == h)
+        atomicAdd(addr, (unsigned long long)s0 + ((unsigned long long)s1 << 22) + ((unsigned long long)s2 << 43));
 }
 
 // Steps a2-a3: classification and exact fixed-point mass assignment.  The
