@@ -204,9 +204,13 @@ def phase_bytes(w, n, esz):
     return b
 
 
-def launches_per_step(ctx, any_recentre):
-    info = ctx.info()
-    return (2 if any_recentre else 0) + 1 + 5 * info["ngeom"] + 1
+def launches(ctx, steps, sort_every):
+    """Kernels of `steps` graph steps: recentre and its centre update, deposit,
+    five FFT passes per geometry, force/kick-drift; every sort_every-th step
+    adds the six kernels of the spatial sort."""
+    per_step = 2 + 1 + 5 * ctx.info()["ngeom"] + 1
+    sorts = (steps + sort_every - 1) // sort_every if sort_every > 0 else 0
+    return per_step * steps + 6 * sorts
 
 
 def run_ours(args):
@@ -330,7 +334,7 @@ def run_ours(args):
         "phase_ms_per_step": phase_ms,
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": Ke},
-        "gpu_launches": launches_per_step(ctx, True) * K,
+        "gpu_launches": launches(ctx, K, args.sort_every),
         "clocks": clocks,
     }
     if fp64 is not None:

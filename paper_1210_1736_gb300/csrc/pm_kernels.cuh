@@ -162,21 +162,31 @@ __device__ __forceinline__ int com_contrib(const SysK &s, const CenK *cen, int g
     return g;
 }
 
+// Exact warp sum of a two's complement int64 (mod 2^64) from three chunk
+// reductions of 22, 21 and 21 bits (each chunk sum stays below 2^32).
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+    const unsigned FULL = 0xffffffffu;
+    const unsigned s0 = __reduce_add_sync(FULL, (unsigned)(v & 0x3fffffu));
+    const unsigned s1 = __reduce_add_sync(FULL, (unsigned)((v >> 22) & 0x1fffffu));
+    const unsigned s2 = __reduce_add_sync(FULL, (unsigned)(v >> 43));
+    return (unsigned long long)s0 + ((unsigned long long)s1 << 22) + ((unsigned long long)s2 << 43);
+}
+
 // Warp-collective: every lane of the warp calls it (g = -1: no contribution).
 __device__ __forceinline__ void com_warp_add(const SysK &s, unsigned long long (*red)[4], int g, long long M,
                                              int Dx, int Dy, int Dz) {
     for (int h = 0; h < s.ngal; ++h) {
         if (!__any_sync(0xffffffffu, g == h)) continue;
         const bool mine = (g == h);
-        const long long v0 = warp_sum_ll(mine ? M : 0);
-        const long long v1 = warp_sum_ll(mine ? M * Dx : 0);
-        const long long v2 = warp_sum_ll(mine ? M * Dy : 0);
-        const long long v3 = warp_sum_ll(mine ? M * Dz : 0);
+        const unsigned long long v0 = warp_sum_u64(mine ? (unsigned long long)M : 0ull);
+        const unsigned long long v1 = warp_sum_u64(mine ? (unsigned long long)(M * Dx) : 0ull);
+        const unsigned long long v2 = warp_sum_u64(mine ? (unsigned long long)(M * Dy) : 0ull);
+        const unsigned long long v3 = warp_sum_u64(mine ? (unsigned long long)(M * Dz) : 0ull);
         if ((threadIdx.x & 31) == 0) {
-            atomicAdd(&red[h][0], (unsigned long long)v0);
-            atomicAdd(&red[h][1], (unsigned long long)v1);
-            atomicAdd(&red[h][2], (unsigned long long)v2);
-            atomicAdd(&red[h][3], (unsigned long long)v3);
+            atomicAdd(&red[h][0], v0);
+            atomicAdd(&red[h][1], v1);
+            atomicAdd(&red[h][2], v2);
+            atomicAdd(&red[h][3], v3);
         }
     }
 }
