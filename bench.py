@@ -322,6 +322,8 @@ def run_ours(args):
         "config": {"workload": WORKLOAD_DESC[args.workload],
                    "particles_per_gpu": n, "galaxies": len(w["galaxies"]), "geometries": ctx.info()["ngeom"],
                    "spatial_sort_every": args.sort_every,
+                   "solve_schedule": {0: "one branch per geometry", 1: "two staggered lanes",
+                                      -1: "single geometry"}[ctx.info()["solve_schedule"]],
                    "l2": f"working set per step ~{ctx.info()['bytes'] / 1e9:.2f} GB > 129 MB L2 (no flush needed)",
                    "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,

@@ -165,7 +165,13 @@ int pm_get_potential(pm_ctx *ctx, int32_t gal, int32_t set, void *host_out);
 int pm_get_centres(pm_ctx *ctx, double *host_out);          /* ngal*3 */
 int pm_set_centres(pm_ctx *ctx, const double *host_in);     /* ngal*3 */
 int pm_count_lost(pm_ctx *ctx, const pm_particles *p, int64_t *host_out);
-int pm_info(pm_ctx *ctx, int64_t *host_out);  /* [shift, nsets, ngeom, bytes] */
+/* host_out[5] = [fixed-point shift, mass sets, distinct geometries, device
+ * bytes, solve schedule].  The schedule of the geometries' FFT chains is
+ * chosen when the context is created by timing both on the device: 0 = one
+ * branch stream per geometry, all chains starting together; 1 = two branch
+ * streams of about equal work, one running its chains largest first and the
+ * other smallest first; -1 = a single geometry (no branches). */
+int pm_info(pm_ctx *ctx, int64_t *host_out);
 
 /* Spatial sort (no counterpart in the paper; a locality optimisation of the
  * NGP assignment of Eq. eqn:cell): permutes every particle array of p in

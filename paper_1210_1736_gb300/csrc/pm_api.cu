@@ -148,8 +148,12 @@ struct pm_ctx {
     void *d_tw[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     cudaStream_t user = nullptr;
     cudaStream_t cap = nullptr;
-    std::vector<cudaStream_t> branch;   // one per geometry (solve branches)
+    std::vector<cudaStream_t> branch;   // solve branch streams
     std::vector<cudaEvent_t> ev_join;
+    // solve schedule, chosen by timing both at creation: 0 = one branch per
+    // geometry, 1 = the geometries' chains in `lanes` (two branches)
+    int sched = 0;
+    std::vector<std::vector<int>> lanes;
     cudaEvent_t ev_fork = nullptr;
     // captured steps: [0] step, [1] sort + step
     cudaGraph_t graph[2] = {nullptr, nullptr};
@@ -326,9 +330,14 @@ template <typename T> int launch_pass(pm_ctx *c, int pass, cudaStream_t st, int 
     return PM_OK;
 }
 
-// With ev (phase timing) the passes run pass by pass on st; otherwise each
-// geometry's chain of five passes runs on its own branch stream (forked from
-// and joined back to st), so independent geometries overlap on the GPU.
+// With ev (phase timing) the passes run pass by pass on st.  Otherwise the
+// geometries' chains of five passes run on branch streams forked from and
+// joined back to st, by one of two schedules (timed at creation, the faster
+// kept): one branch per geometry, all chains starting together; or two
+// lanes of about equal work, one taking its chains largest first and the
+// other smallest first, so that the compute-bound z pass of one large chain
+// meets the bandwidth-bound x and y passes of another rather than its own z
+// pass.
 template <typename T> int enqueue_solve(pm_ctx *c, cudaStream_t st, cudaEvent_t *ev, int shift = INT_MIN) {
     if (ev || c->geos.size() < 2) {
         for (int pass = 0; pass < NPASS; ++pass) {
@@ -338,14 +347,80 @@ template <typename T> int enqueue_solve(pm_ctx *c, cudaStream_t st, cudaEvent_t 
         return PM_OK;
     }
     PM_CK(cudaEventRecord(c->ev_fork, st));
-    for (int gi = 0; gi < (int)c->geos.size(); ++gi) {
-        cudaStream_t b = c->branch[gi];
+    if (c->sched == 0) {
+        for (int gi = 0; gi < (int)c->geos.size(); ++gi) {
+            cudaStream_t b = c->branch[gi];
+            PM_CK(cudaStreamWaitEvent(b, c->ev_fork, 0));
+            for (int pass = 0; pass < NPASS; ++pass) PM_TRY(launch_pass<T>(c, pass, b, gi, shift));
+            PM_CK(cudaEventRecord(c->ev_join[gi], b));
+            PM_CK(cudaStreamWaitEvent(st, c->ev_join[gi], 0));
+        }
+        return PM_OK;
+    }
+    for (size_t l = 0; l < c->lanes.size(); ++l) {
+        cudaStream_t b = c->branch[l];
         PM_CK(cudaStreamWaitEvent(b, c->ev_fork, 0));
-        for (int pass = 0; pass < NPASS; ++pass) PM_TRY(launch_pass<T>(c, pass, b, gi, shift));
-        PM_CK(cudaEventRecord(c->ev_join[gi], b));
-        PM_CK(cudaStreamWaitEvent(st, c->ev_join[gi], 0));
+        for (int gi : c->lanes[l])
+            for (int pass = 0; pass < NPASS; ++pass) PM_TRY(launch_pass<T>(c, pass, b, gi, shift));
+        PM_CK(cudaEventRecord(c->ev_join[l], b));
+        PM_CK(cudaStreamWaitEvent(st, c->ev_join[l], 0));
     }
     return PM_OK;
+}
+
+// Two lanes of about equal transform volume: chains taken largest first, the
+// first to lane 0, each next one to the lighter lane (lane 1 on ties); lane 0
+// runs largest first, lane 1 smallest first, so lane 1's large chains start
+// after its small ones.
+std::vector<std::vector<int>> plan_lanes(const std::vector<GeoBuf> &geos) {
+    std::vector<std::pair<double, int>> w;
+    for (int gi = 0; gi < (int)geos.size(); ++gi) {
+        const pm_geometry &g = geos[gi].g;
+        w.push_back({8.0 * g.nx * g.ny * g.nz * (double)geos[gi].pairs.size(), gi});
+    }
+    std::sort(w.begin(), w.end(), [](const std::pair<double, int> &a, const std::pair<double, int> &b) {
+        return a.first != b.first ? a.first > b.first : a.second < b.second;
+    });
+    std::vector<std::vector<int>> lanes(2);
+    double tot[2] = {0, 0};
+    for (const auto &x : w) {
+        const int l = lanes[0].empty() ? 0 : (tot[0] < tot[1] ? 0 : 1);
+        lanes[l].push_back(x.second);
+        tot[l] += x.first;
+    }
+    std::reverse(lanes[1].begin(), lanes[1].end());
+    if (lanes[1].empty()) lanes.pop_back();
+    return lanes;
+}
+
+// Times each schedule (one warm-up solve, then five between events, on
+// zeroed densities) and keeps the faster.
+template <typename T> int tune_schedule(pm_ctx *c) {
+    c->sched = 0;
+    if (c->geos.size() < 2) return PM_OK;
+    PM_CK(cudaMemsetAsync(c->rho_all, 0, c->rho_bytes, c->user));
+    cudaEvent_t e0, e1;
+    PM_CK(cudaEventCreate(&e0));
+    PM_CK(cudaEventCreate(&e1));
+    float best = 0.f;
+    int best_s = 0;
+    int rc = PM_OK;
+    for (int sc = 0; sc < 2 && rc == PM_OK; ++sc) {
+        c->sched = sc;
+        rc = enqueue_solve<T>(c, c->user, nullptr);
+        if (rc == PM_OK && cudaEventRecord(e0, c->user) != cudaSuccess) rc = fail(PM_E_CUDA, "event record failed");
+        for (int k = 0; k < 5 && rc == PM_OK; ++k) rc = enqueue_solve<T>(c, c->user, nullptr);
+        if (rc == PM_OK && cudaEventRecord(e1, c->user) != cudaSuccess) rc = fail(PM_E_CUDA, "event record failed");
+        float ms = 0.f;
+        if (rc == PM_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+            rc = fail(PM_E_CUDA, "schedule timing failed");
+        if (rc == PM_OK && (sc == 0 || ms < best)) { best = ms; best_s = sc; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->sched = best_s;
+    if (rc != PM_OK) return rc;
+    return check_device_error(c);
 }
 
 template <typename T> int enqueue_deposit(pm_ctx *c, const pm_particles *p, cudaStream_t st) {
@@ -876,7 +951,8 @@ int pm_create_grids(const pm_system *sys, const pm_galaxy *gals, void *stream, p
         }
     if (cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess)
         return cleanup(fail(PM_E_CUDA, "cudaEventCreate failed"));
-    for (size_t gi = 0; gi < c->geos.size(); ++gi) {
+    c->lanes = plan_lanes(c->geos);
+    for (size_t l = 0; l < std::max<size_t>(c->geos.size(), 2); ++l) {
         cudaStream_t b;
         cudaEvent_t e;
         if (cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking) != cudaSuccess)
@@ -959,6 +1035,7 @@ int pm_create_grids(const pm_system *sys, const pm_galaxy *gals, void *stream, p
         cudaMemsetAsync(c->d_err, 0, sizeof(int), c->user) != cudaSuccess ||
         cudaStreamSynchronize(c->user) != cudaSuccess)
         return cleanup(fail(PM_E_CUDA, "context upload failed: %s", cudaGetErrorString(cudaGetLastError())));
+    if ((rc = (c->prec == PM_FP32 ? tune_schedule<float>(c) : tune_schedule<double>(c)))) return cleanup(rc);
     *out = c;
     return PM_OK;
 }
@@ -1165,6 +1242,7 @@ int pm_info(pm_ctx *c, int64_t *out) {
     out[1] = nsets;
     out[2] = (int64_t)c->geos.size();
     out[3] = (int64_t)c->bytes;
+    out[4] = c->geos.size() < 2 ? -1 : c->sched;
     return PM_OK;
 }
 

@@ -360,6 +360,6 @@ class Context:
         return out.value
 
     def info(self):
-        out = (C.c_int64 * 4)()
+        out = (C.c_int64 * 5)()
         _check(lib().pm_info(self.h, out))
-        return {"shift": out[0], "nsets": out[1], "ngeom": out[2], "bytes": out[3]}
+        return {"shift": out[0], "nsets": out[1], "ngeom": out[2], "bytes": out[3], "solve_schedule": out[4]}
