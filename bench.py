@@ -288,24 +288,32 @@ def run_ours(args):
     span_gbs = sum(pb[p] for p in fft_phases) / (span_ms / 1e3) / 1e9
 
     # ---- end to end through the C ABI with host buffers ----
-    pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in (
-        ("x", host["pos"][0]), ("y", host["pos"][1]), ("z", host["pos"][2]),
-        ("vx", host["vel"][0]), ("vy", host["vel"][1]), ("vz", host["vel"][2]),
-        ("m", m32), ("gal", w["gal"].astype(np.int32)))}
-    pin["flags"] = torch.zeros(n, dtype=torch.int32).pin_memory()
-    out = {k: torch.empty(n, dtype=torch.float32).pin_memory() for k in ("x", "y", "z", "vx", "vy", "vz")}
-    h2d = sum(t.numel() * t.element_size() for t in pin.values())
-    d2h = sum(t.numel() * t.element_size() for t in out.values())
+    # the step's whole particle state (x, y, z, vx, vy, vz, m, galaxy id,
+    # flags) goes up as one pinned block and the updated positions and
+    # velocities come back as one block; the device particle arrays are rows
+    # of the device copy of that block
+    hbuf = torch.empty((9, n), dtype=torch.float32).pin_memory()
+    for k, a in enumerate((host["pos"][0], host["pos"][1], host["pos"][2], host["vel"][0], host["vel"][1],
+                           host["vel"][2], m32)):
+        hbuf[k].copy_(torch.from_numpy(np.ascontiguousarray(a)))
+    hbuf[7].view(torch.int32).copy_(torch.from_numpy(w["gal"].astype(np.int32)))
+    hbuf[8].view(torch.int32).zero_()
+    hout = torch.empty((6, n), dtype=torch.float32).pin_memory()
+    dbuf = torch.empty((9, n), dtype=torch.float32, device="cuda")
+    pe = pm.Particles.from_tensors(dbuf[0:3], dbuf[3:6], dbuf[6], dbuf[7].view(torch.int32), dbuf[8].view(torch.int32))
+    h2d = hbuf.numel() * hbuf.element_size()
+    d2h = hout.numel() * hout.element_size()
     Ke = max(1, min(K, 200))
+    dbuf.copy_(hbuf, non_blocking=True)   # untimed: the step graph for these arrays is captured here
+    ctx.step(pe, dt, 1)
+    hout.copy_(dbuf[0:6], non_blocking=True)
     barrier()
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     f0.record()
     for _ in range(Ke):
-        for k, t in pin.items():
-            getattr(parts, k).copy_(t, non_blocking=True)
-        ctx.step(parts, dt, 1)
-        for k, t in out.items():
-            t.copy_(getattr(parts, k), non_blocking=True)
+        dbuf.copy_(hbuf, non_blocking=True)
+        ctx.step(pe, dt, 1)
+        hout.copy_(dbuf[0:6], non_blocking=True)
     f1.record()
     barrier()
     e2e_ms = f0.elapsed_time(f1)
