@@ -14,32 +14,33 @@ namespace pmk {
 // ---------------------------------------------------------------------------
 // Adds q (two's complement int64) to *addr for every lane with active set.
 // After the spatial sort, lanes that target the same cell are mostly
-// adjacent: each run of adjacent active lanes with one address (found with
-// one shuffle of the address and a ballot) is summed exactly -- mod 2^64,
-// from three chunk sums of 22, 21 and 21 bits, each below 2^32 for 32
-// lanes -- and its first lane issues one atomic.  Lanes with one address
-// that are not adjacent form separate runs (still exact).  Every lane of the
-// warp must call it.
+// adjacent: the runs of adjacent active lanes with one address are found
+// with one shuffle of the address and a ballot, each run is summed by a
+// segmented inclusive scan over shuffles (64-bit adds, exact mod 2^64; it
+// stops as soon as no run in the warp is longer than the distance reached),
+// and the run's last lane issues one atomic.  Lanes with one address that
+// are not adjacent form separate runs (still exact).  Every lane of the warp
+// must call it.
 __device__ __forceinline__ void agg_add(unsigned long long *addr, unsigned long long q, bool active) {
     const unsigned FULL = 0xffffffffu;
     const int lane = (int)(threadIdx.x & 31);
     const unsigned long long key = active ? (unsigned long long)addr : 0ull;   // no cell lives at address 0
-    const unsigned plo = __shfl_up_sync(FULL, (unsigned)key, 1), phi = __shfl_up_sync(FULL, (unsigned)(key >> 32), 1);
-    const bool head = active && (lane == 0 || plo != (unsigned)key || phi != (unsigned)(key >> 32));
-    const unsigned act = __ballot_sync(FULL, active), heads = __ballot_sync(FULL, head);
-    if (!active) return;
+    const unsigned long long prev = __shfl_up_sync(FULL, key, 1);
+    const bool head = active && (lane == 0 || prev != key);
+    // run boundaries: run heads and inactive lanes (an active lane after an
+    // inactive one is a head, since its key is not 0)
+    const unsigned brk = __ballot_sync(FULL, head) | ~__ballot_sync(FULL, active);
     const unsigned upto = lane == 31 ? FULL : ((2u << lane) - 1u);   // lanes 0..lane
-    const int h = 31 - __clz(heads & upto);                          // this run's head
-    const unsigned after = heads & ~upto;
-    const int nx = after ? __ffs(after) - 1 : 32;                     // next run's head
-    const unsigned run = (nx == 32 ? FULL : ((1u << nx) - 1u)) & ~((1u << h) - 1u);
-    const unsigned peers = run & act;
-    if (peers == (1u << lane)) { atomicAdd(addr, q); return; }
-    const unsigned s0 = __reduce_add_sync(peers, (unsigned)(q & 0x3fffffu));
-    const unsigned s1 = __reduce_add_sync(peers, (unsigned)((q >> 22) & 0x1fffffu));
-    const unsigned s2 = __reduce_add_sync(peers, (unsigned)(q >> 43));
-    if (lane == h)
-        atomicAdd(addr, (unsigned long long)s0 + ((unsigned long long)s1 << 22) + ((unsigned long long)s2 << 43));
+    const int h = 31 - __clz(brk & upto);                            // this run's head
+    unsigned long long v = active ? q : 0ull;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const bool take = lane - d >= h;
+        if (!__any_sync(FULL, take)) break;
+        const unsigned long long u = __shfl_up_sync(FULL, v, d);
+        if (take) v += u;
+    }
+    if (active && (lane == 31 || ((brk >> (lane + 1)) & 1u))) atomicAdd(addr, v);
 }
 
 // Steps a2-a3: classification and exact fixed-point mass assignment.  The
@@ -172,22 +173,19 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
     return (unsigned long long)s0 + ((unsigned long long)s1 << 22) + ((unsigned long long)s2 << 43);
 }
 
-// Warp-collective: every lane of the warp calls it (g = -1: no contribution).
-__device__ __forceinline__ void com_warp_add(const SysK &s, unsigned long long (*red)[4], int g, long long M,
-                                             int Dx, int Dy, int Dz) {
+// Warp-collective: every lane of the warp calls it with its sums (M, M Dx,
+// M Dy, M Dz, mod 2^64) for galaxy g (g = -1: no contribution).
+__device__ __forceinline__ void com_warp_add(const SysK &s, unsigned long long (*red)[4], int g,
+                                             const unsigned long long (&S)[4]) {
     for (int h = 0; h < s.ngal; ++h) {
         if (!__any_sync(0xffffffffu, g == h)) continue;
         const bool mine = (g == h);
-        const unsigned long long v0 = warp_sum_u64(mine ? (unsigned long long)M : 0ull);
-        const unsigned long long v1 = warp_sum_u64(mine ? (unsigned long long)(M * Dx) : 0ull);
-        const unsigned long long v2 = warp_sum_u64(mine ? (unsigned long long)(M * Dy) : 0ull);
-        const unsigned long long v3 = warp_sum_u64(mine ? (unsigned long long)(M * Dz) : 0ull);
-        if ((threadIdx.x & 31) == 0) {
-            atomicAdd(&red[h][0], v0);
-            atomicAdd(&red[h][1], v1);
-            atomicAdd(&red[h][2], v2);
-            atomicAdd(&red[h][3], v3);
-        }
+        unsigned long long v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = warp_sum_u64(mine ? S[k] : 0ull);
+        if ((threadIdx.x & 31) == 0)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) atomicAdd(&red[h][k], v[k]);
     }
 }
 
@@ -201,6 +199,17 @@ __device__ __forceinline__ void com_write_partials(const SysK &s, unsigned long 
         const unsigned long long v = (&red[0][0])[threadIdx.x];
         if (v) atomicAdd(reinterpret_cast<unsigned long long *>(part) + (blockIdx.x % COM_SLOTS) * PM_MAX_GALAXIES * 4 +
                              threadIdx.x, v);
+    }
+}
+
+// One thread's running sums for galaxy g straight into its block's row.
+__device__ __forceinline__ void com_flush(long long *part, int g, unsigned long long (&S)[4]) {
+    unsigned long long *row = reinterpret_cast<unsigned long long *>(part) +
+                              (blockIdx.x % COM_SLOTS) * PM_MAX_GALAXIES * 4 + g * 4;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (S[k]) atomicAdd(row + k, S[k]);
+        S[k] = 0;
     }
 }
 
@@ -240,25 +249,39 @@ static __global__ void __launch_bounds__(256) k_com_apply(const __grid_constant_
 }
 
 // Step a1: centre-of-mass sums of the current positions, then k_com_apply.
+// Each thread sums its particles' terms (mod 2^64) for one galaxy ag in
+// registers (a particle of another galaxy first sends the running sums to
+// the block's accumulator row); the warps reduce once, at the end.
 template <typename T>
 __global__ void __launch_bounds__(256) k_recentre(PartK<T> p, const __grid_constant__ SysK s, CenK *cen,
                                                   long long *part) {
     __shared__ unsigned long long red[PM_MAX_GALAXIES][4];
     if (threadIdx.x < PM_MAX_GALAXIES * 4) (&red[0][0])[threadIdx.x] = 0;
-    __syncthreads();
+    int ag = -1;
+    unsigned long long S[4] = {0, 0, 0, 0};
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long b = (long long)blockIdx.x * blockDim.x; b < p.n; b += stride) {
-        const long long i = b + threadIdx.x;
-        int g = -1, Dx = 0, Dy = 0, Dz = 0;
-        long long M = 0;
-        if (i < p.n) {
-            const uint32_t f = p.flags[i];
-            const int gi = p.gal[i];
-            const T x = p.x[i], y = p.y[i], z = p.z[i], m = p.m[i];
-            if (!(f & PM_FLAG_LOST)) g = com_contrib(s, cen, gi, x, y, z, m, M, Dx, Dy, Dz);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += stride) {
+        // every load of the particle issued before the flag test (one memory
+        // latency per particle, not two)
+        const uint32_t f = p.flags[i];
+        const int gi = p.gal[i];
+        const T x = p.x[i], y = p.y[i], z = p.z[i], m = p.m[i];
+        if (f & PM_FLAG_LOST) continue;
+        int Dx, Dy, Dz;
+        long long M;
+        const int g = com_contrib(s, cen, gi, x, y, z, m, M, Dx, Dy, Dz);
+        if (g < 0) continue;
+        if (g != ag) {
+            if (ag >= 0) com_flush(part, ag, S);
+            ag = g;
         }
-        com_warp_add(s, red, g, M, Dx, Dy, Dz);
+        S[0] += (unsigned long long)M;
+        S[1] += (unsigned long long)(M * Dx);
+        S[2] += (unsigned long long)(M * Dy);
+        S[3] += (unsigned long long)(M * Dz);
     }
+    __syncthreads();
+    com_warp_add(s, red, ag, S);
     com_write_partials(s, red, part);
 }
 
@@ -274,10 +297,15 @@ __global__ void __launch_bounds__(256, 3) k_force(PartK<T> p, const __grid_const
     for (long long b = (long long)blockIdx.x * blockDim.x; b < p.n; b += stride) {
         const long long i = b + threadIdx.x;
         if (i < p.n) {
-            if (p.flags[i] & PM_FLAG_LOST) {
+            // the particle's loads (velocities too) issued before the flag
+            // test and the stencil gathers, so their latencies overlap
+            const uint32_t f = p.flags[i];
+            const T xT = p.x[i], yT = p.y[i], zT = p.z[i];
+            T v0[3] = {0, 0, 0};
+            if (MODE == 0 || MODE == 2) { v0[0] = p.vx[i]; v0[1] = p.vy[i]; v0[2] = p.vz[i]; }
+            if (f & PM_FLAG_LOST) {
                 if (MODE == 1) { ax[i] = 0; ay[i] = 0; az[i] = 0; }
             } else {
-                const T xT = p.x[i], yT = p.y[i], zT = p.z[i];
                 const float sx = pm_canon(xT, s.sc[0], s.sc_hi[0], s.sc_lo[0]);
                 const float sy = pm_canon(yT, s.sc[1], s.sc_hi[1], s.sc_lo[1]);
                 const float sz = pm_canon(zT, s.sc[2], s.sc_hi[2], s.sc_lo[2]);
@@ -315,13 +343,13 @@ __global__ void __launch_bounds__(256, 3) k_force(PartK<T> p, const __grid_const
                     }
                 }
                 if (MODE == 0) {
-                    const T vx = p.vx[i] + dt * acc[0], vy = p.vy[i] + dt * acc[1], vz = p.vz[i] + dt * acc[2];
+                    const T vx = v0[0] + dt * acc[0], vy = v0[1] + dt * acc[1], vz = v0[2] + dt * acc[2];
                     p.vx[i] = vx; p.vy[i] = vy; p.vz[i] = vz;
                     p.x[i] = xT + dt * vx; p.y[i] = yT + dt * vy; p.z[i] = zT + dt * vz;
                 } else if (MODE == 1) {
                     ax[i] = acc[0]; ay[i] = acc[1]; az[i] = acc[2];
                 } else if (MODE == 2) {
-                    p.vx[i] += dt * acc[0]; p.vy[i] += dt * acc[1]; p.vz[i] += dt * acc[2];
+                    p.vx[i] = v0[0] + dt * acc[0]; p.vy[i] = v0[1] + dt * acc[1]; p.vz[i] = v0[2] + dt * acc[2];
                 } else {
                     const double x = (double)xT, y = (double)yT, z = (double)zT;
                     const double hdt = 0.5 * (double)dt;
@@ -723,7 +751,10 @@ cudaError_t pm_launch_force(int mode, const PartK<T> &p, const SysK &sk, const C
 template <typename T>
 cudaError_t pm_launch_recentre(const PartK<T> &p, const SysK &sk, CenK *cen, long long *part, cudaStream_t st) {
     if (p.n <= 0) return cudaSuccess;
-    pmk::k_recentre<T><<<pmk_host::particle_grid(p.n), 256, 0, st>>>(p, sk, cen, part);
+    // a full wave (8 blocks of 256 per SM): each thread sums several
+    // particles in registers before the one warp reduction
+    const int g = std::min(pmk_host::particle_grid(p.n), 8 * pmk_host::num_sms());
+    pmk::k_recentre<T><<<g, 256, 0, st>>>(p, sk, cen, part);
     pmk::k_com_apply<<<1, 256, 0, st>>>(sk, part, cen);
     return cudaGetLastError();
 }
