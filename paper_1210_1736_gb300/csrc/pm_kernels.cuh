@@ -567,7 +567,8 @@ __global__ void k_store_hhat(const double *oct, T *out, int nx, int ny, double s
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < ncol * L;
          i += (long long)gridDim.x * blockDim.x) {
         const long long col = i / L;
-        const int w = (int)(i % L), e = w / TPC, t = w % TPC;
+        const int w = (int)(i % L);
+        const int e = hhat_thread_major(L) ? w % E : w / TPC, t = hhat_thread_major(L) ? w / E : w % TPC;
         const int kz = pmfft::in_row<L, NS - 1, false>(t, e / RL, e % RL);
         const int kzr = kz <= L / 2 ? kz : L - kz;
         out[i] = (T)(oct[(long long)kzr * ncol + col] * scale);

@@ -123,7 +123,8 @@ cudaError_t pm_axis_transform(const double *in, double *out, const double *cmat,
 // H-hat table of the z pass from the FP64 octant oct[kzr][kyr][kxr]
 // (scaled by `scale`): for each octant column (kyr, kxr) the L = 2nz values
 // H-hat(kz) in the order the z pass's threads hold the forward transform's
-// outputs (register e of thread t at entry e * L/16 + t), kz > L/2 mirrored.
+// outputs: register e of thread t at entry e * L/16 + t, or at t * 16 + e
+// for L <= 64 (hhat_thread_major); kz > L/2 mirrored.
 inline long long pm_hhat_table_size(int nx, int ny, int nz) { return (long long)(nx + 1) * (ny + 1) * 2 * nz; }
 template <typename T>
 cudaError_t pm_store_hhat(const double *oct, T *out, int nx, int ny, int nz, double scale, cudaStream_t st);

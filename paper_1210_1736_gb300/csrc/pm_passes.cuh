@@ -370,6 +370,14 @@ __global__ void __launch_bounds__(CShape<T, L>::THREADS, 3) k_col(PairArgs a, co
 // the prefetch of the tile two steps ahead.  (The same structure measured
 // slower than k_col for the y passes, so those stay there.)
 // ---------------------------------------------------------------------------
+// Order of the z pass's H-hat table within one octant column (L values).
+// Register order (entry e*TPC + t for register e of thread t) lets the TPC
+// lanes of a column read consecutive values with each load; with TPC <= 4
+// (L <= 64) one such load touches a sector per column and uses half of it,
+// so short transforms take thread-major order (entries t*E .. t*E + E-1,
+// read as 16-byte vectors).
+__host__ __device__ constexpr bool hhat_thread_major(int L) { return L <= 64; }
+
 template <typename T, int L> struct WShape {
     typedef typename cplx_t<T>::type C;
     static constexpr int TPC = L / E;
@@ -493,18 +501,40 @@ __global__ void __launch_bounds__(WShape<T, L>::THREADS, (L >= 512 ? 2 : 3))
 
         pmfft::fft_core<L, false, -1, true, false, true>(v, xch, lay, t, tw);
         {
-            // H-hat of column (kyr, kxr) in register order (pm_store_hhat):
-            // the lanes of a column read consecutive values
+            // H-hat of column (kyr, kxr), stored by pm_store_hhat in the
+            // order hhat_thread_major gives for L
             const long long q = tile * S::COLS + c;
             const int ky = (int)(q / nx2), kx = (int)(q % nx2);
             const int kyr = ky <= a.ny ? ky : ny2 - ky;
             const int kxr = kx <= a.nx ? kx : nx2 - kx;
-            const T *hz = static_cast<const T *>(a.hhat) + ((size_t)kyr * (a.nx + 1) + kxr) * L + t;
+            const T *hcol = static_cast<const T *>(a.hhat) + ((size_t)kyr * (a.nx + 1) + kxr) * L;
+            if constexpr (hhat_thread_major(L)) {
+                const T *hz = hcol + t * E;   // 16-byte aligned: L, E multiples of 16
+                if constexpr (sizeof(T) == 4) {
 #pragma unroll
-            for (int e = 0; e < E; ++e) {
-                const T h = __ldg(hz + e * S::TPC);
-                v[e].x *= h;
-                v[e].y *= h;
+                    for (int e = 0; e < E; e += 4) {
+                        const float4 h = __ldg(reinterpret_cast<const float4 *>(hz + e));
+                        v[e].x *= h.x; v[e].y *= h.x;
+                        v[e + 1].x *= h.y; v[e + 1].y *= h.y;
+                        v[e + 2].x *= h.z; v[e + 2].y *= h.z;
+                        v[e + 3].x *= h.w; v[e + 3].y *= h.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < E; e += 2) {
+                        const double2 h = __ldg(reinterpret_cast<const double2 *>(hz + e));
+                        v[e].x *= h.x; v[e].y *= h.x;
+                        v[e + 1].x *= h.y; v[e + 1].y *= h.y;
+                    }
+                }
+            } else {
+                const T *hz = hcol + t;
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const T h = __ldg(hz + e * S::TPC);
+                    v[e].x *= h;
+                    v[e].y *= h;
+                }
             }
             pmfft::fft_core<L, true, 1, false, true, true>(v, xch, lay, t, tw);
         }
