@@ -289,9 +289,11 @@ __global__ void __launch_bounds__(256) k_recentre(PartK<T> p, const __grid_const
 // rule selects for each galaxy (Sec. 2.1), then
 //   MODE 0: leap-frog kick-drift   MODE 1: write acceleration
 //   MODE 2: kick only              MODE 3: energy / angular momentum sums
+// The FP32 kick-drift fits 64 registers without spilling: four blocks per
+// SM hide more of the stencil gathers' latency.
 template <typename T, int MODE>
-__global__ void __launch_bounds__(256, 3) k_force(PartK<T> p, const __grid_constant__ SysK s, const CenK *cen,
-                                                  T dt, T *ax, T *ay, T *az, double *diag) {
+__global__ void __launch_bounds__(256, (MODE == 0 && sizeof(T) == 4) ? 4 : 3)
+    k_force(PartK<T> p, const __grid_constant__ SysK s, const CenK *cen, T dt, T *ax, T *ay, T *az, double *diag) {
     double dsum[7] = {0, 0, 0, 0, 0, 0, 0};
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long b = (long long)blockIdx.x * blockDim.x; b < p.n; b += stride) {
