@@ -145,6 +145,13 @@ __device__ __forceinline__ int pm_region(const GalK &G, float dx, float dy, floa
 // ----------------------------------------------------------------------------
 template <typename C> __device__ __forceinline__ C cadd(C a, C b) { C r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
 template <typename C> __device__ __forceinline__ C csub(C a, C b) { C r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+// FP32: one packed two-lane instruction (sm_100 family) per complex add or
+// subtract, rounded per component as the scalar operations (bit-identical);
+// the FFT passes are bound by instruction issue.
+template <> __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+template <> __device__ __forceinline__ float2 csub(float2 a, float2 b) {
+    return __fadd2_rn(a, make_float2(-b.x, -b.y));
+}
 template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
     C r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
 }
