@@ -111,9 +111,9 @@ template <int SIGN, typename C> struct Dft<2, SIGN, C> {
 template <int SIGN, typename C> struct Dft<4, SIGN, C> {
     static __device__ __forceinline__ void run(C *v) {
         C t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
-        C t2 = cadd(v[1], v[3]), d = csub(v[1], v[3]);
+        C t2 = cadd(v[1], v[3]), t3 = cmul_i<SIGN>(csub(v[1], v[3]));
         v[0] = cadd(t0, t2); v[2] = csub(t0, t2);
-        v[1] = cadd_i<SIGN>(t1, d); v[3] = cadd_i<-SIGN>(t1, d);
+        v[1] = cadd(t1, t3); v[3] = csub(t1, t3);
     }
 };
 // Cooley-Tukey split R = N1*N2: input n = N2*n1 + n2, output k = k1 + N1*k2.
@@ -157,8 +157,8 @@ __device__ __forceinline__ void dft16(C *v) {
     for (int n2 = 0; n2 < 4; ++n2) {
         C t[4];
         if (ZIN) {
-            const C a = v[n2], b = v[4 + n2];
-            t[0] = cadd(a, b); t[1] = cadd_i<SIGN>(a, b); t[2] = csub(a, b); t[3] = cadd_i<-SIGN>(a, b);
+            const C a = v[n2], b = v[4 + n2], wb = cmul_i<SIGN>(b);
+            t[0] = cadd(a, b); t[1] = cadd(a, wb); t[2] = csub(a, b); t[3] = csub(a, wb);
         } else {
             t[0] = v[n2]; t[1] = v[4 + n2]; t[2] = v[8 + n2]; t[3] = v[12 + n2];
             Dft<4, SIGN, C>::run(t);
@@ -171,7 +171,7 @@ __device__ __forceinline__ void dft16(C *v) {
         const C t0 = y[k1], t1 = y[4 + k1], t2 = y[8 + k1], t3 = y[12 + k1];
         if (HOUT) {
             v[k1] = cadd(cadd(t0, t2), cadd(t1, t3));
-            v[k1 + 4] = cadd_i<SIGN>(csub(t0, t2), csub(t1, t3));
+            v[k1 + 4] = cadd(csub(t0, t2), cmul_i<SIGN>(csub(t1, t3)));
         } else {
             C t[4] = {t0, t1, t2, t3};
             Dft<4, SIGN, C>::run(t);

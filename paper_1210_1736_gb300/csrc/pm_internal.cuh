@@ -165,10 +165,3 @@ template <int SIGN, typename C> __device__ __forceinline__ C cmul_i(C z) {
     if (SIGN > 0) { r.x = -z.y; r.y = z.x; } else { r.x = z.y; r.y = -z.x; }
     return r;
 }
-// a + SIGN*i*b, per component (also for FP32: the swap and sign of b fold
-// into two scalar adds, where a packed add would need b rotated first)
-template <int SIGN, typename C> __device__ __forceinline__ C cadd_i(C a, C b) {
-    C r;
-    if (SIGN > 0) { r.x = a.x - b.y; r.y = a.y + b.x; } else { r.x = a.x + b.y; r.y = a.y - b.x; }
-    return r;
-}

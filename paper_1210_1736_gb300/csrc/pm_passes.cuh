@@ -63,6 +63,7 @@ __global__ void __launch_bounds__(NT) k_xfwd(PairArgs a) {
     __syncthreads();
     const long long nrows = (long long)a.ny * a.nz;
     const long long ngroups = (nrows + S::LINES - 1) / S::LINES;
+    const int lny = __ffs(a.ny) - 1;   // row r = z*ny + y; ny is a power of two
     const T scale = (T)a.scale;
     for (long long grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
         const long long r = grp * S::LINES + line;
@@ -87,7 +88,7 @@ __global__ void __launch_bounds__(NT) k_xfwd(PairArgs a) {
         // exchange row is private: the exchanges synchronise the warp only
         pmfft::fft_core<L, false, -1, true, false, true>(v, sm, pmfft::RowLayout{line * S::LDR}, t, tw);
         if (valid) {
-            const long long z = r / a.ny, y = r % a.ny;
+            const long long z = r >> lny, y = r & (a.ny - 1);
             C *out = static_cast<C *>(a.work) + ((size_t)z * 2 * a.ny + y) * L;
             constexpr int RL = radix(L, NS - 1, false);
 #pragma unroll
@@ -114,11 +115,12 @@ __global__ void __launch_bounds__(NT) k_xinv(PairArgs a) {
     __syncthreads();
     const long long nrows = (long long)a.ny * a.nz;
     const long long ngroups = (nrows + S::LINES - 1) / S::LINES;
+    const int lny = __ffs(a.ny) - 1;   // row r = z*ny + y; ny is a power of two
     T *phi_b = static_cast<T *>(a.phi_b);
     for (long long grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
         const long long r = grp * S::LINES + line;
         const bool valid = r < nrows;
-        const long long z = valid ? r / a.ny : 0, y = valid ? r % a.ny : 0;
+        const long long z = valid ? r >> lny : 0, y = valid ? r & (a.ny - 1) : 0;
         const C *in = static_cast<const C *>(a.work) + ((size_t)z * 2 * a.ny + y) * L;
         C v[E];
         constexpr int R0 = radix(L, 0, true);
@@ -254,12 +256,13 @@ __global__ void __launch_bounds__(CShape<T, L>::THREADS, 3) k_col(PairArgs a, co
     const int c = tid % COLS, t = tid / COLS;
     C *work = static_cast<C *>(a.work);
     const int nx2 = 2 * a.nx, ny2 = 2 * a.ny;
-    const long long tiles_per_z = (nx2 + COLS - 1) / COLS;
+    const long long tiles_per_z = (nx2 + COLS - 1) / COLS;   // a power of two, as nx2 and COLS
+    const int ltpz = __ffs((int)tiles_per_z) - 1;
 
     // tile -> TMA coordinates and the first column it covers
     auto coords = [&](long long tile, int &x, int &y) {
-        x = (int)((tile % tiles_per_z) * COLS * S::EPC);
-        y = (int)((tile / tiles_per_z) * ny2);
+        x = (int)((tile & (tiles_per_z - 1)) * COLS * S::EPC);
+        y = (int)((tile >> ltpz) * ny2);
     };
     auto issue = [&](long long tile, int b) {
         int x, y;
@@ -321,7 +324,7 @@ __global__ void __launch_bounds__(CShape<T, L>::THREADS, 3) k_col(PairArgs a, co
         C *col;
         size_t stride;
         {
-            const long long z = tile / tiles_per_z, kx = (tile % tiles_per_z) * COLS + c;
+            const long long z = tile >> ltpz, kx = (tile & (tiles_per_z - 1)) * COLS + c;
             q = kx;
             valid = kx < nx2;
             col = work + (size_t)z * ny2 * nx2 + kx;
@@ -431,7 +434,7 @@ __global__ void __launch_bounds__(WShape<T, L>::THREADS, (L >= 512 ? 2 : 3))
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int t = lane % S::TPC;
     const int c = warp * (32 / S::TPC) + lane / S::TPC;   // column within the tile
-    const int nx2 = 2 * a.nx, ny2 = 2 * a.ny;
+    const int nx2 = 2 * a.nx, ny2 = 2 * a.ny, lnx2 = __ffs(nx2) - 1;
 
     // tile <-> sub-tiles of the buffer, each NBOXI boxes of BOXI rows
     auto issue_load = [&](long long tile, int b) {
@@ -504,7 +507,7 @@ __global__ void __launch_bounds__(WShape<T, L>::THREADS, (L >= 512 ? 2 : 3))
             // H-hat of column (kyr, kxr), stored by pm_store_hhat in the
             // order hhat_thread_major gives for L
             const long long q = tile * S::COLS + c;
-            const int ky = (int)(q / nx2), kx = (int)(q % nx2);
+            const int ky = (int)(q >> lnx2), kx = (int)(q & (nx2 - 1));   // nx2 is a power of two
             const int kyr = ky <= a.ny ? ky : ny2 - ky;
             const int kxr = kx <= a.nx ? kx : nx2 - kx;
             const T *hcol = static_cast<const T *>(a.hhat) + ((size_t)kyr * (a.nx + 1) + kxr) * L;
