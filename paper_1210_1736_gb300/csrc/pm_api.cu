@@ -107,6 +107,19 @@ CenK make_cenk(const double *c, int ngal) {
     return k;
 }
 
+// Captured steps for one particle set and time step: [0] step, [1] sort +
+// step.  A context keeps a few such sets (e.g. the buffers of a caller that
+// pipelines its copies) and replaces the least recently used.
+struct GraphSet {
+    bool valid = false;
+    pm_particles key;
+    double dt = 0;
+    long long used = 0;
+    cudaGraph_t graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+};
+constexpr int GRAPH_SETS = 4;
+
 // Two mass sets of one geometry transformed together as rho_a + i rho_b
 // (b < 0: no partner), with their work array and tensor maps.
 struct Pair {
@@ -155,11 +168,8 @@ struct pm_ctx {
     int sched = 0;
     std::vector<std::vector<int>> lanes;
     cudaEvent_t ev_fork = nullptr;
-    // captured steps: [0] step, [1] sort + step
-    cudaGraph_t graph[2] = {nullptr, nullptr};
-    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-    pm_particles gkey;
-    double gdt = 0;
+    GraphSet gs[GRAPH_SETS];
+    long long guse = 0;
     // spatial sort
     SortK sortk;
     int sort_interval = 0;
@@ -448,18 +458,24 @@ template <typename T> int enqueue_step(pm_ctx *c, const pm_particles *p, double 
     return PM_OK;
 }
 
-void destroy_graph(pm_ctx *c) {
+void destroy_set(GraphSet &g) {
     for (int k = 0; k < 2; ++k) {
-        if (c->gexec[k]) cudaGraphExecDestroy(c->gexec[k]);
-        if (c->graph[k]) cudaGraphDestroy(c->graph[k]);
-        c->gexec[k] = nullptr;
-        c->graph[k] = nullptr;
+        if (g.gexec[k]) cudaGraphExecDestroy(g.gexec[k]);
+        if (g.graph[k]) cudaGraphDestroy(g.graph[k]);
+        g.gexec[k] = nullptr;
+        g.graph[k] = nullptr;
     }
+    g.valid = false;
+}
+
+void destroy_graph(pm_ctx *c) {
+    for (GraphSet &g : c->gs) destroy_set(g);
 }
 
 // Scratch of the spatial sort for n particles (allocated outside any capture).
 int ensure_sort_scratch(pm_ctx *c, long long n) {
     if (n <= c->sort_cap) return PM_OK;
+    destroy_graph(c);   // captured steps hold the old scratch's addresses
     for (int k = 0; k < 9; ++k)
         PM_TRY(dev_alloc(c, &c->s_arr[k], (size_t)n * (k < 7 ? c->esz : 4)));
     PM_TRY(dev_alloc(c, (void **)&c->s_key, (size_t)n * 4));
@@ -497,21 +513,29 @@ template <typename T> int capture(pm_ctx *c, const pm_particles *p, double dt, b
 
 template <typename T> int step_impl(pm_ctx *c, const pm_particles *p, double dt, int nsteps) {
     const bool sorting = c->sort_interval > 0 && p->n > 0;
-    const bool same = c->gexec[0] && std::memcmp(&c->gkey, p, sizeof(pm_particles)) == 0 && c->gdt == dt;
-    if (!same) {
-        destroy_graph(c);
+    GraphSet *gs = nullptr;
+    for (GraphSet &g : c->gs)
+        if (g.valid && std::memcmp(&g.key, p, sizeof(pm_particles)) == 0 && g.dt == dt) gs = &g;
+    if (!gs) {
         if (sorting) PM_TRY(ensure_sort_scratch(c, p->n));
-        c->gkey = *p;
-        c->gdt = dt;
+        for (GraphSet &g : c->gs) {
+            if (!g.valid) { gs = &g; break; }
+            if (!gs || g.used < gs->used) gs = &g;
+        }
+        destroy_set(*gs);
+        std::memcpy(&gs->key, p, sizeof(pm_particles));
+        gs->dt = dt;
+        gs->valid = true;
     }
+    gs->used = ++c->guse;
     for (int s = 0; s < nsteps; ++s) {
         const bool sort_now = sorting && c->step_count % c->sort_interval == 0;
         const int g = sort_now ? 1 : 0;
-        if (!c->gexec[g]) {
-            const int rc = capture<T>(c, p, dt, sort_now, &c->graph[g], &c->gexec[g]);
-            if (rc != PM_OK) { destroy_graph(c); return rc; }
+        if (!gs->gexec[g]) {
+            const int rc = capture<T>(c, p, dt, sort_now, &gs->graph[g], &gs->gexec[g]);
+            if (rc != PM_OK) { destroy_set(*gs); return rc; }
         }
-        PM_CK(cudaGraphLaunch(c->gexec[g], c->user));
+        PM_CK(cudaGraphLaunch(gs->gexec[g], c->user));
         ++c->step_count;
     }
     return PM_OK;
@@ -873,7 +897,6 @@ int pm_create_grids(const pm_system *sys, const pm_galaxy *gals, void *stream, p
     std::memset(c->set_geo, -1, sizeof(c->set_geo));
     std::memset(c->rho, 0, sizeof(c->rho));
     std::memset(c->phi, 0, sizeof(c->phi));
-    std::memset(&c->gkey, 0, sizeof(c->gkey));
 
     auto cleanup = [&](int rc) { pm_destroy(c); return rc; };
     if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess)
