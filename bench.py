@@ -48,6 +48,25 @@ def env_rank():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
 
 
+def slowest_rank_ms(ms, world, device):
+    """The job's time is its slowest rank's: the maximum over ranks of a
+    per-rank time in ms (all ranks call it; device: where the process group's
+    backend takes tensors, "cuda" for NCCL, "cpu" for gloo)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, n, steps, ms):
+    """Whole-job particle-steps/s: every rank advances its own n particles
+    for `steps` steps (weak scaling) in the job time ms."""
+    return world * n * steps / (ms / 1e3)
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -254,12 +273,8 @@ def run_ours(args):
     e1.record()
     barrier()
     clocks = clk.stop()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * n * K / (ms / 1e3)
+    ms = slowest_rank_ms(e0.elapsed_time(e1), world, "cuda")
+    value = job_rate(world, n, K, ms)
 
     # ---- per-phase device times (same kernels, launched with events between phases) ----
     ph = ctx.step_timed(parts, dt, K)
@@ -350,12 +365,7 @@ def run_ours(args):
             main.wait_event(e)
         f1.record(main)
         barrier()
-        t = f0.elapsed_time(f1)
-        if world > 1:
-            tt = torch.tensor([t], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t = float(tt.item())
-        return world * n * Ke / (t / 1e3)
+        return job_rate(world, n, Ke, slowest_rank_ms(f0.elapsed_time(f1), world, "cuda"))
 
     e2e_serial = e2e_run(False)
     e2e = e2e_run(True)
