@@ -384,6 +384,11 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": ncu_traffic(dom, args.workload)},
+        "step_bound": {"algorithmic_bytes": sum(pb.values()),
+                       "min_ms_per_step": sum(pb.values()) / (peak * 1e9) * 1e3,
+                       "frac": sum(pb.values()) / (peak * 1e9) * 1e3 / (ms / K),
+                       "note": "whole step by the byte model (every phase's algorithmic HBM bytes) at the "
+                               "measured copy bandwidth, against the graph-replayed step"},
         "fft_convolve": {"gbs": conv_gbs, "frac": conv_gbs / peak, "ms_per_step": conv_ms,
                          "span_gbs": span_gbs, "span_frac": span_gbs / peak, "span_ms_per_step": span_ms,
                          "note": "gbs/frac: the five pass phases timed one after another; span: pm_solve as "

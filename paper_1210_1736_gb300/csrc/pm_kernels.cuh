@@ -111,12 +111,12 @@ __global__ void __launch_bounds__(256) k_deposit(PartK<T> p, const __grid_consta
 template <typename T>
 __device__ __forceinline__ void stencil(const GeomK &g, const T *__restrict__ P1, const T *__restrict__ P2,
                                         const Cell &cl, T dx, T dy, T dz, T *acc, T *phi) {
-    const long long sy = g.nx, sz = (long long)g.nx * g.ny;
+    const int sy = g.nx, sz = g.nx * g.ny;   // a grid has at most 256^3 cells: 32-bit offsets
     const size_t base = cell_off(g, cl);
     const T *b1 = P1 + base;
     const T *b2 = P2 ? P2 + base : nullptr;
     auto ld = [&](int di, int dj, int dk) -> T {
-        const long long o = di + dj * sy + dk * sz;
+        const int o = di + dj * sy + dk * sz;
         T v = __ldg(b1 + o);
         if (b2) v += __ldg(b2 + o);
         return v;
