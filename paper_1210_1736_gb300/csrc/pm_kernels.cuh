@@ -46,7 +46,7 @@ __device__ __forceinline__ void agg_add(unsigned long long *addr, unsigned long 
 // Steps a2-a3: classification and exact fixed-point mass assignment.  The
 // loop is warp-uniform so the aggregation can use warp collectives.
 template <typename T>
-__global__ void __launch_bounds__(256) k_deposit(PartK<T> p, const __grid_constant__ SysK s, const CenK *cen,
+__global__ void __launch_bounds__(256, 6) k_deposit(PartK<T> p, const __grid_constant__ SysK s, const CenK *cen,
                                                  int aggregate) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long b = (long long)blockIdx.x * blockDim.x; b < p.n; b += stride) {
@@ -54,10 +54,11 @@ __global__ void __launch_bounds__(256) k_deposit(PartK<T> p, const __grid_consta
         unsigned long long *tgt[3] = {nullptr, nullptr, nullptr};
         unsigned long long q = 0;
         if (i < p.n) {
+            // all loads of the particle before the flag test
             const uint32_t f = p.flags[i];
+            const T x = p.x[i], y = p.y[i], z = p.z[i], mi = p.m[i];
+            const int g = p.gal[i];
             if (!(f & PM_FLAG_LOST)) {
-                const T x = p.x[i], y = p.y[i], z = p.z[i];
-                const int g = p.gal[i];
                 const float sx = pm_canon(x, s.sc[0], s.sc_hi[0], s.sc_lo[0]);
                 const float sy = pm_canon(y, s.sc[1], s.sc_hi[1], s.sc_lo[1]);
                 const float sz = pm_canon(z, s.sc[2], s.sc_hi[2], s.sc_lo[2]);
@@ -80,7 +81,7 @@ __global__ void __launch_bounds__(256) k_deposit(PartK<T> p, const __grid_consta
                     const float dz = pm_canon(z, ce.c[2], ce.hi[2], ce.lo[2]);
                     Cell cf, cm;
                     const int reg = pm_region(G, dx, dy, dz, cf, cm);
-                    q = (unsigned long long)pm_qmass(p.m[i], s.mscale, s.mscale_f);
+                    q = (unsigned long long)pm_qmass(mi, s.mscale, s.mscale_f);
                     if (reg == REG_CORE) {
                         tgt[0] = G.rho[0] + cell_off(G.fine, cf);
                         tgt[1] = G.rho[1] + cell_off(G.med, cm);
