@@ -203,6 +203,14 @@ __device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, int x, int 
                  "r"(x), "r"(y), "r"(smem_addr(src))
                  : "memory");
 }
+// Plain bulk copy global -> shared (16-byte aligned addresses, size a
+// multiple of 16), completing on an mbarrier.
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 // Waits until the committed stores have read their shared-memory source.
 __device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
@@ -431,6 +439,7 @@ __global__ void __launch_bounds__(WShape<T, L>::THREADS, (L >= 512 ? 2 : 3))
     C *tw = xch + S::COLS * S::LDR;
     uint64_t *full = reinterpret_cast<uint64_t *>(tw + pmfft::tw_total(L));   // tile loaded (tx bytes)
     uint64_t *staged = full + 2;                                            // every warp staged (FREE)
+    uint64_t *hfull = staged + 2;                                           // tile's H-hat staged
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int t = lane % S::TPC;
     const int c = warp * (32 / S::TPC) + lane / S::TPC;   // column within the tile
@@ -461,8 +470,17 @@ __global__ void __launch_bounds__(WShape<T, L>::THREADS, (L >= 512 ? 2 : 3))
         mbar_init(&full[1], 1);
         mbar_init(&staged[0], NWARPS);
         mbar_init(&staged[1], NWARPS);
+        mbar_init(&hfull[0], 1);
+        mbar_init(&hfull[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    // H-hat staging: with block barriers and a tile inside one ky row (COLS
+    // <= nx), the tile's H-hat rows (kyr fixed, kxr ascending for kx < nx,
+    // descending from nx for kx >= nx) are one contiguous block of exactly
+    // BUF bytes; it is copied into the tile's input buffer once the inputs
+    // are in registers and read from there for the multiply
+    const bool hstage = !FREE && L >= 128 && S::COLS <= a.nx;
+    bool hpend = false;   // thread 0: an H-hat copy not yet seen complete
     pmfft::expand_twiddles<L>(tw, static_cast<const C *>(a.tw));
     __syncthreads();
     // thread 0 issues every copy; counts per buffer of loads issued and of
@@ -501,9 +519,40 @@ __global__ void __launch_bounds__(WShape<T, L>::THREADS, (L >= 512 ? 2 : 3))
         // overwrite this buffer without a block barrier; the block-synchronous
         // variant keeps the warps in step.
         if (!FREE) __syncthreads();
+        const long long q0 = tile * S::COLS;
+        const int k0 = (int)(q0 & (nx2 - 1));
+        if (hstage && tid == 0) {
+            const int ky0 = (int)(q0 >> lnx2);
+            const int kyr0 = ky0 <= a.ny ? ky0 : ny2 - ky0;
+            const int r0 = k0 < a.nx ? k0 : nx2 - k0 - S::COLS + 1;
+            fence_async_smem();   // the inputs' generic reads before the copy's writes
+            mbar_expect_tx(&hfull[b], S::BUF);
+            bulk_load(in, static_cast<const T *>(a.hhat) + ((size_t)kyr0 * (a.nx + 1) + r0) * L, S::BUF, &hfull[b]);
+            hpend = true;
+        }
 
         pmfft::fft_core<L, false, -1, true, false, true>(v, xch, lay, t, tw);
-        {
+        bool hok = true;
+        if (hstage) {
+            // H-hat of column c from the staged rows (row c, or COLS-1-c
+            // for the mirrored half), register order
+            hok = mbar_wait(&hfull[b], phase);
+            if (hok && tid == 0) hpend = false;
+            const T *hz = reinterpret_cast<const T *>(in) + (k0 < a.nx ? c : S::COLS - 1 - c) * L + t;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const T h = hz[e * S::TPC];
+                v[e].x *= h;
+                v[e].y *= h;
+            }
+            pmfft::fft_core<L, true, 1, false, true, true>(v, xch, lay, t, tw);
+            // every H-hat read done before the outputs overwrite the buffer
+            if (!__syncthreads_and(hok ? 1 : 0)) {
+                failed = true;
+                if (tid == 0 && hpend) mbar_wait(&hfull[b], phase);   // let the copy land (bounded)
+                break;
+            }
+        } else {
             // H-hat of column (kyr, kxr), stored by pm_store_hhat in the
             // order hhat_thread_major gives for L
             const long long q = tile * S::COLS + c;
