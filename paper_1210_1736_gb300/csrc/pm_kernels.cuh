@@ -2,6 +2,8 @@
 // precision T (float or double).  Included once per precision.
 #pragma once
 
+#include <utility>
+
 #include "pm_passes.cuh"
 #include "pm_particle.cuh"
 
@@ -651,19 +653,36 @@ template <typename K> int resident_blocks(K kernel, int threads, size_t smem) {
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, smem) != cudaSuccess || nb < 1) nb = 1;
     return nb;
 }
+// Launch with programmatic stream serialisation (the FFT passes of a chain:
+// each waits for its predecessor with griddepcontrol.wait after its
+// prologue).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*k)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t st,
+                       Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
+}
+
 template <typename T, int L> cudaError_t xfwd_L(const PairArgs &a, cudaStream_t st) {
     static int nb = resident_blocks(pmk::k_xfwd<T, L>, pmk::NT, pmk::xpass_smem<T, L>());
     const long long groups = ((long long)a.ny * a.nz + pmk::XShape<L>::LINES - 1) / pmk::XShape<L>::LINES;
     const long long grid = std::min(groups, (long long)nb * num_sms());
-    pmk::k_xfwd<T, L><<<(unsigned)grid, pmk::NT, pmk::xpass_smem<T, L>(), st>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(pmk::k_xfwd<T, L>, (unsigned)grid, pmk::NT, pmk::xpass_smem<T, L>(), st, a);
 }
 template <typename T, int L> cudaError_t xinv_L(const PairArgs &a, cudaStream_t st) {
     static int nb = resident_blocks(pmk::k_xinv<T, L>, pmk::NT, pmk::xpass_smem<T, L>());
     const long long groups = ((long long)a.ny * a.nz + pmk::XShape<L>::LINES - 1) / pmk::XShape<L>::LINES;
     const long long grid = std::min(groups, (long long)nb * num_sms());
-    pmk::k_xinv<T, L><<<(unsigned)grid, pmk::NT, pmk::xpass_smem<T, L>(), st>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(pmk::k_xinv<T, L>, (unsigned)grid, pmk::NT, pmk::xpass_smem<T, L>(), st, a);
 }
 template <typename T, int L, int MODE> cudaError_t col_LM(const PairArgs &a, const CUtensorMap &map, cudaStream_t st) {
     constexpr int COLS = pmk::CShape<T, L>::COLS;
@@ -671,9 +690,8 @@ template <typename T, int L, int MODE> cudaError_t col_LM(const PairArgs &a, con
     long long grid = (long long)col_blocks_per_sm<T, L, MODE>() * num_sms();
     if (grid > ntiles) grid = ntiles;
     if (grid < 1) grid = 1;
-    pmk::k_col<T, L, MODE><<<(unsigned)grid, pmk::CShape<T, L>::THREADS, pmk::col_smem<T, L, MODE>(), st>>>(a, map,
-                                                                                                          ntiles);
-    return cudaGetLastError();
+    return launch_pdl(pmk::k_col<T, L, MODE>, (unsigned)grid, pmk::CShape<T, L>::THREADS,
+                      pmk::col_smem<T, L, MODE>(), st, a, map, ntiles);
 }
 template <typename T, int L> cudaError_t zconv_L(const PairArgs &a, const CUtensorMap &map, cudaStream_t st) {
     typedef pmk::WShape<T, L> S;
@@ -681,8 +699,7 @@ template <typename T, int L> cudaError_t zconv_L(const PairArgs &a, const CUtens
     long long grid = (long long)colw_blocks_per_sm<T, L>() * num_sms();
     if (grid > ntiles) grid = ntiles;
     if (grid < 1) grid = 1;
-    pmk::k_colw<T, L><<<(unsigned)grid, S::THREADS, pmk::colw_smem<T, L>(), st>>>(a, map, ntiles);
-    return cudaGetLastError();
+    return launch_pdl(pmk::k_colw<T, L>, (unsigned)grid, S::THREADS, pmk::colw_smem<T, L>(), st, a, map, ntiles);
 }
 template <typename T, int L> cudaError_t col_L(const PairArgs &a, const CUtensorMap &map, int mode, cudaStream_t st) {
     if (mode == COL_YFWD) return col_LM<T, L, COL_YFWD>(a, map, st);

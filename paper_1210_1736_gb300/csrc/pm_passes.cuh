@@ -25,6 +25,15 @@
 
 namespace pmk {
 
+// Programmatic dependent launch between the passes of a chain (they are
+// launched with programmatic stream serialisation): a pass runs its
+// prologue (twiddle tables, barriers), then waits until the previous pass
+// has completed and its writes are visible before it touches the work
+// array; each block signals, when it starts its last tile, that the next
+// pass may be scheduled.  Both are no-ops for a plain launch.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 using pmfft::E;
 using pmfft::nstages;
 using pmfft::radix;
@@ -61,11 +70,13 @@ __global__ void __launch_bounds__(NT) k_xfwd(PairArgs a) {
     const int tid = threadIdx.x, line = tid / S::TPC, t = tid % S::TPC;
     pmfft::expand_twiddles<L>(tw, static_cast<const C *>(a.tw));
     __syncthreads();
+    pdl_wait();
     const long long nrows = (long long)a.ny * a.nz;
     const long long ngroups = (nrows + S::LINES - 1) / S::LINES;
     const int lny = __ffs(a.ny) - 1;   // row r = z*ny + y; ny is a power of two
     const T scale = (T)a.scale;
     for (long long grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+        if (grp + gridDim.x >= ngroups) pdl_release();
         const long long r = grp * S::LINES + line;
         const bool valid = r < nrows;
         const long long *ra = a.rho_a + (valid ? r * NX : 0);
@@ -113,11 +124,13 @@ __global__ void __launch_bounds__(NT) k_xinv(PairArgs a) {
     const int tid = threadIdx.x, line = tid / S::TPC, t = tid % S::TPC;
     pmfft::expand_twiddles<L>(tw, static_cast<const C *>(a.tw));
     __syncthreads();
+    pdl_wait();
     const long long nrows = (long long)a.ny * a.nz;
     const long long ngroups = (nrows + S::LINES - 1) / S::LINES;
     const int lny = __ffs(a.ny) - 1;   // row r = z*ny + y; ny is a power of two
     T *phi_b = static_cast<T *>(a.phi_b);
     for (long long grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+        if (grp + gridDim.x >= ngroups) pdl_release();
         const long long r = grp * S::LINES + line;
         const bool valid = r < nrows;
         const long long z = valid ? r >> lny : 0, y = valid ? r & (a.ny - 1) : 0;
@@ -289,6 +302,7 @@ __global__ void __launch_bounds__(CShape<T, L>::THREADS, 3) k_col(PairArgs a, co
     }
     pmfft::expand_twiddles<L>(tw, static_cast<const C *>(a.tw));
     __syncthreads();
+    pdl_wait();
     int issued[2] = {0, 0};   // loads issued per buffer (thread 0's count)
     if (tid == 0) {
         if (blockIdx.x < ntiles) { issue(blockIdx.x, 0); ++issued[0]; }
@@ -297,6 +311,7 @@ __global__ void __launch_bounds__(CShape<T, L>::THREADS, 3) k_col(PairArgs a, co
 
     int it = 0;
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+        if (tile + gridDim.x >= ntiles) pdl_release();
         const int b = it & 1;
         const unsigned phase = (unsigned)((it >> 1) & 1);
         // a tensor copy that never lands: report, wait (bounded) for the other
@@ -483,6 +498,7 @@ __global__ void __launch_bounds__(WShape<T, L>::THREADS, (L >= 512 ? 2 : 3))
     bool hpend = false;   // thread 0: an H-hat copy not yet seen complete
     pmfft::expand_twiddles<L>(tw, static_cast<const C *>(a.tw));
     __syncthreads();
+    pdl_wait();
     // thread 0 issues every copy; counts per buffer of loads issued and of
     // tiles sent (to drain after an expired wait)
     int issued0 = 0, issued1 = 0, done0 = 0, done1 = 0;
@@ -495,6 +511,7 @@ __global__ void __launch_bounds__(WShape<T, L>::THREADS, (L >= 512 ? 2 : 3))
 
     int it = 0;
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+        if (tile + gridDim.x >= ntiles) pdl_release();
         const int b = it & 1;
         const unsigned phase = (unsigned)((it >> 1) & 1);
         if (FREE) {
