@@ -76,11 +76,18 @@ def peaks():
 
 
 def kernel_source_hash():
+    """Hash of the kernel sources' code: comments and whitespace are left
+    out, so that only a change of the compiled code invalidates counters
+    stored against it."""
+    import re
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1210_1736_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
         if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+            text = open(os.path.join(csrc, f), encoding="utf-8").read()
+            text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+            text = re.sub(r"//[^\n]*", " ", text)
+            h.update(f.encode() + b"\0" + " ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -145,8 +145,10 @@ int pm_kick(pm_ctx *ctx, const pm_particles *p, double dt);
 
 /* Steps a1-a9, nsteps times: recentre, deposit, solve, force and leap-frog
  * kick-drift (Sec. 2.1): v(t+dt/2) = v(t-dt/2) + dt a(t);
- * x(t+dt) = x(t) + dt v(t+dt/2).  The step is captured once as a CUDA graph
- * per (particle arrays, n, dt) and replayed. */
+ * x(t+dt) = x(t) + dt v(t+dt/2).  The step is captured as CUDA graphs per
+ * (particle arrays, n, dt) and replayed; the graphs of the four most
+ * recently stepped particle sets are kept (the least recently used is
+ * replaced), so a caller may alternate buffers without recapturing. */
 int pm_step(pm_ctx *ctx, const pm_particles *p, double dt, int32_t nsteps);
 
 /* Step a10 (energy and angular momentum, Sec. 6.4 quantities): recentre is

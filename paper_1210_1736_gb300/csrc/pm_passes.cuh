@@ -419,7 +419,7 @@ template <typename T, int L> struct WShape {
     static constexpr unsigned BUF = (unsigned)(RIN * COLS * sizeof(C));
     // the longest transform runs two blocks per SM with the warps decoupled
     // (thread 0 sends a tile once every warp has arrived on its barrier); the
-    // others measured faster with two block barriers per tile
+    // others measured faster block-synchronous (block barriers per tile)
     static constexpr bool FREE = L >= 512;
 };
 
