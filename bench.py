@@ -134,6 +134,14 @@ def fp64_comparison(w, host, m32, n_steps):
     rms_ref = float(torch.sqrt(f2.mean()))
     rms = float(torch.sqrt(d2.mean())) / rms_ref
     mx = float(torch.sqrt(d2.max())) / rms_ref
+    # where the largest errors sit: per galaxy
+    gal = torch.as_tensor(w["gal"], device=d2.device)[live]
+    by_gal = {}
+    for g in range(len(w["galaxies"])):
+        sel = gal == g
+        if bool(sel.any()):
+            by_gal[str(g)] = {"rms": float(torch.sqrt(d2[sel].mean())) / rms_ref,
+                              "max": float(torch.sqrt(d2[sel].max())) / rms_ref}
     ctx64.kick(p64, -0.5 * dt)
     ctx64.step(p64, dt, 2)
     torch.cuda.synchronize()
@@ -147,8 +155,10 @@ def fp64_comparison(w, host, m32, n_steps):
     del p64, a64, a32
     torch.cuda.empty_cache()
     return {"ms_per_step": ms64, "steps": n_steps, "fp32_force_err_rms": rms, "fp32_force_err_max": mx,
+            "fp32_force_err_by_galaxy": by_gal,
             "note": "FP64 build of the same kernels (graph-replayed steps); force errors relative to the "
-                    "RMS force, over live particles at the initial state"}
+                    "RMS force over live particles at the initial state (by galaxy: the same measure over "
+                    "that galaxy's particles)"}
 
 
 class Clocks:
