@@ -284,6 +284,62 @@ def test_cell_edge_ties_bit_exact():
     _compare_density_and_flags(ctx, parts, system, rho, flags)
 
 
+def _ulp_nudged(x, k, dtype):
+    """x moved by k units in the last place of dtype (elementwise)."""
+    x = np.asarray(x, dtype=dtype)
+    out = x.copy()
+    for step in range(int(np.max(np.abs(k))) if np.size(k) else 0):
+        move = np.abs(k) > step
+        out[move] = np.nextafter(out[move], np.where(k[move] > 0, np.inf, -np.inf).astype(dtype))
+    return out
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_region_and_box_boundaries_bit_exact(precision):
+    """Particles within a few units in the last place of every decision
+    boundary of the nested geometry: the spheres R_core, R_out and R_sys,
+    and both edges of the usable box (cells 2 .. n-3) of each grid on each
+    axis (the cell length is 2R/(n-4); the box spans offsets -R(n-3)/(n-4)
+    .. R(n-5)/(n-4) from its centre).  Region, cell and lost decisions --
+    hence every density and the lost flags -- must be bit-exact with the
+    oracle, which takes them with the same canonical FP32 offsets."""
+    w = W.galaxy_small(precision=precision)
+    g, sysd = w["galaxies"][0], w["system"]
+    dtype = np.float32 if precision == "fp32" else np.float64
+    rng = np.random.default_rng(23)
+    pts = []
+    # spheres about the (initial) galaxy centre, which is the origin
+    for R in (g["r_core"], g["r_out"], sysd["r_sys"]):
+        u = rng.normal(size=(3, 900))
+        u /= np.linalg.norm(u, axis=0)
+        pts.append(_ulp_nudged(u * R, rng.integers(-3, 4, (3, 900)), dtype))
+    # usable-box edges of each grid (all three centred on the origin here)
+    for key in ("coarse", "medium", "fine"):
+        n3 = g[key][:3]
+        R, q = g[key][3], g[key][4]
+        l_xy = 2.0 * R / (n3[0] - 4)
+        for ax in range(3):
+            n = n3[ax]
+            l = l_xy if ax < 2 else q * l_xy
+            for edge in ((1.5 - n / 2) * l, (n / 2 - 2.5) * l):
+                p = rng.uniform(-0.3, 0.3, (3, 300)) * min(R, 0.9 * g["r_core"])
+                p[ax] = edge
+                k = np.zeros((3, 300), dtype=np.int64)
+                k[ax] = rng.integers(-3, 4, 300)
+                pts.append(_ulp_nudged(p, k, dtype))
+    pos = np.concatenate(pts, axis=1).astype(np.float64)
+    n = pos.shape[1]
+    m = np.full(n, 1.0 / n)
+    gal = np.zeros(n, np.int32)
+    ctx, parts = gpu_setup(w, pos=pos, vel=np.zeros_like(pos), m=m, gal=gal)
+    system, state = oracle_setup(w, pos=pos, vel=np.zeros_like(pos), m=m, gal=gal)
+    rho, phi, flags, own, s = oracle_fields(system, state)
+    ctx.deposit(parts)
+    _compare_density_and_flags(ctx, parts, system, rho, flags)
+    lost = flags & 1
+    assert 0 < lost.sum() < n                 # both sides of R_sys are represented
+
+
 def test_deposit_deterministic_repeat():
     w = W.galaxy_small(precision="fp32")
     ctx, parts = gpu_setup(w)
