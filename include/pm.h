@@ -175,6 +175,16 @@ int pm_count_lost(pm_ctx *ctx, const pm_particles *p, int64_t *host_out);
  * other smallest first; -1 = a single geometry (no branches). */
 int pm_info(pm_ctx *ctx, int64_t *host_out);
 
+/* Self-test of failure detection (no counterpart in the paper): launches one
+ * block that waits, with the bounded wait the FFT passes use for their
+ * tensor copies (2 s limit), on a barrier that nothing arrives at.  The wait
+ * gives up, the block sets the context's device error flag, and the call
+ * returns what the next synchronising call reports after an expired wait of
+ * a pass: PM_E_TIMEOUT.  The flag is cleared afterwards, so the context stays
+ * usable.  Takes about two seconds; synchronises.  PM_E_TIMEOUT from this
+ * call is the expected result, not a failure. */
+int pm_selftest_wait_expiry(pm_ctx *ctx);
+
 /* Spatial sort (no counterpart in the paper; a locality optimisation of the
  * NGP assignment of Eq. eqn:cell): permutes every particle array of p in
  * place so that particles are ordered by galaxy, region (core, shell,

@@ -16,7 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libpm.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["pm_fp32.cu", "pm_fp64.cu", "pm_green.cu", "pm_api.cu", "pm_static.cu", "pm_cic.cu", "pm_diag.cu"]
+SOURCES = ["pm_fp32.cu", "pm_fp64.cu", "pm_green.cu", "pm_api.cu", "pm_static.cu", "pm_cic.cu", "pm_diag.cu",
+           "pm_selftest.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1257,6 +1257,16 @@ int pm_count_lost(pm_ctx *c, const pm_particles *p, int64_t *host_out) {
     return check_device_error(c);
 }
 
+int pm_selftest_wait_expiry(pm_ctx *c) {
+    if (!c) return fail(PM_E_ARG, "ctx is NULL");
+    PM_TRY(check_device_error(c));   // starts from a clean flag
+    PM_CK(pm_launch_wait_expiry(c->d_err, c->user));
+    const int rc = check_device_error(c);
+    PM_CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->user));
+    PM_CK(cudaStreamSynchronize(c->user));
+    return rc;
+}
+
 int pm_info(pm_ctx *c, int64_t *out) {
     if (!c || !out) return fail(PM_E_ARG, "ctx or out is NULL");
     int nsets = 0;

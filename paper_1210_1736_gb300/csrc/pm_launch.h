@@ -129,6 +129,10 @@ inline long long pm_hhat_table_size(int nx, int ny, int nz) { return (long long)
 template <typename T>
 cudaError_t pm_store_hhat(const double *oct, T *out, int nx, int ny, int nz, double scale, cudaStream_t st);
 
+// Self-test of the bounded waits: one block waits on an mbarrier nothing
+// arrives at, gives up after the time limit and sets *err to 1.
+cudaError_t pm_launch_wait_expiry(int *err, cudaStream_t st);
+
 // Records a message for pm_last_error() and returns code (C++ linkage; for
 // translation units other than the C ABI file).
 int pm_internal_fail(int code, const char *msg);

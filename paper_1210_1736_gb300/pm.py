@@ -16,6 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpm.so")
 
 PM_OK, PM_E_ARG, PM_E_QCRIT, PM_E_NESTING, PM_E_OVERFLOW, PM_E_CUDA, PM_E_STATE = 0, -1, -2, -3, -4, -5, -6
+PM_E_TIMEOUT = -7
 PM_FP32, PM_FP64 = 1, 2
 PM_FLAG_LOST = 1
 PM_MAX_GALAXIES = 8
@@ -84,6 +85,7 @@ _SIGS.update({
     "pm_cic_force": (C.c_int, [_vp, _P(pm_particles), _vp, _vp, _vp]),
     "pm_cic_kick_drift": (C.c_int, [_vp, _P(pm_particles), C.c_double, C.c_double]),
     "pm_cic_vjp": (C.c_int, [_vp, _P(pm_particles), _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "pm_selftest_wait_expiry": (C.c_int, [_vp]),
 })
 
 _lib = None
@@ -358,6 +360,11 @@ class Context:
         out = C.c_int64()
         _check(lib().pm_count_lost(self.h, C.byref(p.struct()), C.byref(out)))
         return out.value
+
+    def selftest_wait_expiry(self):
+        """Status of the bounded-wait self-test (PM_E_TIMEOUT is the expected
+        result: the wait gave up and the host saw it); see include/pm.h."""
+        return int(lib().pm_selftest_wait_expiry(self.h))
 
     def info(self):
         out = (C.c_int64 * 5)()

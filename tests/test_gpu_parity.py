@@ -340,6 +340,30 @@ def test_region_and_box_boundaries_bit_exact(precision):
     assert 0 < lost.sum() < n                 # both sides of R_sys are represented
 
 
+def test_bounded_wait_expiry_reported():
+    """Failure detection without a GPU fault: one block waits, with the
+    bounded wait the FFT passes use for their tensor copies, on a barrier
+    nothing arrives at.  The wait gives up at its limit (about 2 s), the
+    block sets the device error flag and the host reads PM_E_TIMEOUT.  The
+    flag is cleared again: the same context then deposits and solves without
+    error, with results equal to a fresh context's."""
+    import time
+    from paper_1210_1736_gb300 import pm
+    w = W.galaxy_small(precision="fp32")
+    ctx, parts = gpu_setup(w)
+    t0 = time.perf_counter()
+    assert ctx.selftest_wait_expiry() == pm.PM_E_TIMEOUT
+    assert time.perf_counter() - t0 > 1.5
+    ctx.deposit(parts)
+    ctx.solve()
+    ctx2, p2 = gpu_setup(w)
+    ctx2.deposit(p2)
+    ctx2.solve()
+    for k in range(1, 6):
+        assert np.array_equal(ctx.density(0, k), ctx2.density(0, k))
+        assert np.array_equal(ctx.potential(0, k), ctx2.potential(0, k))
+
+
 def test_deposit_deterministic_repeat():
     w = W.galaxy_small(precision="fp32")
     ctx, parts = gpu_setup(w)
