@@ -240,11 +240,24 @@ def phase_bytes(w, n, esz):
     return b
 
 
-def launches(ctx, steps, sort_every):
+def fft_pairs(w):
+    """FFT launches per pass: one per pair of mass sets sharing a transform
+    (per galaxy: grids 4+5, or 5 alone; grids 2+3; grid 1)."""
+    n = 0
+    for g in w["galaxies"]:
+        n += 1
+        if g.get("medium"):
+            n += 1
+            if g.get("fine"):
+                n += 1
+    return n
+
+
+def launches(w, steps, sort_every):
     """Kernels of `steps` graph steps: recentre and its centre update, deposit,
-    five FFT passes per geometry, force/kick-drift; every sort_every-th step
-    adds the six kernels of the spatial sort."""
-    per_step = 2 + 1 + 5 * ctx.info()["ngeom"] + 1
+    five FFT passes per pair of mass sets, force/kick-drift; every
+    sort_every-th step adds the six kernels of the spatial sort."""
+    per_step = 2 + 1 + 5 * fft_pairs(w) + 1
     sorts = (steps + sort_every - 1) // sort_every if sort_every > 0 else 0
     return per_step * steps + 6 * sorts
 
@@ -415,7 +428,7 @@ def run_ours(args):
                 "steps": Ke, "serial_value": e2e_serial,
                 "pipeline": "one-step requests rotating over three device buffers: upload of k+1 and download "
                             "of k-1 on their own streams overlap the step of k; serial_value without the overlap"},
-        "gpu_launches": launches(ctx, K, args.sort_every),
+        "gpu_launches": launches(w, K, args.sort_every),
         "clocks": clocks,
     }
     if fp64 is not None:
