@@ -166,6 +166,28 @@ __device__ __forceinline__ int com_contrib(const SysK &s, const CenK *cen, int g
     return g;
 }
 
+// Read-only global loads the compiler keeps where they are written.
+__device__ __forceinline__ float ld_early(const float *q) {
+    float v;
+    asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(q));
+    return v;
+}
+__device__ __forceinline__ double ld_early(const double *q) {
+    double v;
+    asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(v) : "l"(q));
+    return v;
+}
+__device__ __forceinline__ int ld_early(const int32_t *q) {
+    int v;
+    asm volatile("ld.global.nc.s32 %0, [%1];" : "=r"(v) : "l"(q));
+    return v;
+}
+__device__ __forceinline__ uint32_t ld_early(const uint32_t *q) {
+    uint32_t v;
+    asm volatile("ld.global.nc.u32 %0, [%1];" : "=r"(v) : "l"(q));
+    return v;
+}
+
 // Exact warp sum of a two's complement int64 (mod 2^64) from three chunk
 // reductions of 22, 21 and 21 bits (each chunk sum stays below 2^32).
 __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
@@ -256,7 +278,7 @@ static __global__ void __launch_bounds__(256) k_com_apply(const __grid_constant_
 // registers (a particle of another galaxy first sends the running sums to
 // the block's accumulator row); the warps reduce once, at the end.
 template <typename T>
-__global__ void __launch_bounds__(256) k_recentre(PartK<T> p, const __grid_constant__ SysK s, CenK *cen,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 1) k_recentre(PartK<T> p, const __grid_constant__ SysK s, CenK *cen,
                                                   long long *part) {
     __shared__ unsigned long long red[PM_MAX_GALAXIES][4];
     if (threadIdx.x < PM_MAX_GALAXIES * 4) (&red[0][0])[threadIdx.x] = 0;
@@ -265,10 +287,11 @@ __global__ void __launch_bounds__(256) k_recentre(PartK<T> p, const __grid_const
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += stride) {
         // every load of the particle issued before the flag test (one memory
-        // latency per particle, not two)
-        const uint32_t f = p.flags[i];
-        const int gi = p.gal[i];
-        const T x = p.x[i], y = p.y[i], z = p.z[i], m = p.m[i];
+        // latency per particle, not two); volatile loads cannot be sunk
+        // into the branch that uses them
+        const uint32_t f = ld_early(p.flags + i);
+        const int gi = ld_early(p.gal + i);
+        const T x = ld_early(p.x + i), y = ld_early(p.y + i), z = ld_early(p.z + i), m = ld_early(p.m + i);
         if (f & PM_FLAG_LOST) continue;
         int Dx, Dy, Dz;
         long long M;
@@ -772,9 +795,13 @@ cudaError_t pm_launch_force(int mode, const PartK<T> &p, const SysK &sk, const C
 template <typename T>
 cudaError_t pm_launch_recentre(const PartK<T> &p, const SysK &sk, CenK *cen, long long *part, cudaStream_t st) {
     if (p.n <= 0) return cudaSuccess;
-    // a full wave (8 blocks of 256 per SM): each thread sums several
-    // particles in registers before the one warp reduction
-    const int g = std::min(pmk_host::particle_grid(p.n), 8 * pmk_host::num_sms());
+    // one full wave of resident blocks (8 per SM in FP32): each thread sums
+    // several particles in registers before the one warp reduction
+    static int bps = 0;
+    if (!bps && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, pmk::k_recentre<T>, 256, 0) != cudaSuccess ||
+                 bps < 1))
+        bps = 1;
+    const int g = std::min(pmk_host::particle_grid(p.n), bps * pmk_host::num_sms());
     pmk::k_recentre<T><<<g, 256, 0, st>>>(p, sk, cen, part);
     pmk::k_com_apply<<<1, 256, 0, st>>>(sk, part, cen);
     return cudaGetLastError();
