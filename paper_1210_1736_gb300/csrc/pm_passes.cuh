@@ -15,7 +15,8 @@
 // The column passes are persistent: each block walks tiles of COLS adjacent
 // columns; a TMA tensor copy brings the next-but-one tile's input rows into
 // shared memory (double buffer, mbarrier completion) while the block
-// transforms the current one; the outputs leave by TMA store.
+// transforms the current one; the y passes store their outputs from
+// registers, the z pass stages them in shared memory for a TMA store.
 #pragma once
 
 #include <cuda.h>
@@ -391,10 +392,12 @@ __global__ void __launch_bounds__(CShape<T, L>::THREADS, 3) k_col(PairArgs a, co
 // kernel's address function agree, so the first-stage reads are free of bank
 // conflicts).  The L/16 threads of a column are consecutive lanes of one
 // warp, so the stage exchanges use a private padded row per column and
-// synchronise the warp only.  The outputs (rows < L/2) are staged into the
-// tile's own, consumed buffer and leave by TMA store; the buffer then takes
-// the prefetch of the tile two steps ahead.  (The same structure measured
-// slower than k_col for the y passes, so those stay there.)
+// synchronise the warp only.  For L = 128, 256 the tile's H-hat rows arrive
+// by one bulk copy into the consumed input buffer during the forward FFT.
+// The outputs (rows < L/2) are staged into the tile's own buffer and leave by
+// TMA store; the buffer then takes the prefetch of the tile two steps ahead.
+// (The same structure measured slower than k_col for the y passes, so those
+// stay there.)
 // ---------------------------------------------------------------------------
 // Order of the z pass's H-hat table within one octant column (L values).
 // Register order (entry e*TPC + t for register e of thread t) lets the TPC
