@@ -262,6 +262,89 @@ def launches(w, steps, sort_every):
     return per_step * steps + 6 * sorts
 
 
+def request_block(host, m32, gal):
+    """One request's particle state as a pinned host block (9, n) float32:
+    x, y, z, vx, vy, vz, m, galaxy id and flags (the last two as int32)."""
+    import torch
+    n = len(m32)
+    hbuf = torch.empty((9, n), dtype=torch.float32).pin_memory()
+    for k, a in enumerate((host["pos"][0], host["pos"][1], host["pos"][2], host["vel"][0], host["vel"][1],
+                           host["vel"][2], m32)):
+        hbuf[k].copy_(torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)))
+    hbuf[7].view(torch.int32).copy_(torch.from_numpy(np.asarray(gal, dtype=np.int32)))
+    hbuf[8].view(torch.int32).zero_()
+    return hbuf
+
+
+class RequestPipeline:
+    """One-step requests whose particle state lives in pinned host memory,
+    through the C ABI: each request's state goes up as one block, one step
+    runs, and the updated positions and velocities (6, n) come back as one
+    block.  With overlap the requests rotate over NB device buffers, so the
+    upload of request k+1 and the download of request k-1 run on their own
+    streams while request k steps (the library keeps the captured step of
+    each buffer); a buffer is refilled only after its previous download has
+    read it.  Without overlap each request's upload, step and download run in
+    sequence on one buffer."""
+    NB = 3
+
+    def __init__(self, ctx, hbuf, dt, nout=NB):
+        """nout: host result blocks (request k lands in hout[k % nout]; at
+        least NB)."""
+        import torch
+        from paper_1210_1736_gb300 import pm
+        self.ctx, self.hbuf, self.dt = ctx, hbuf, dt
+        n = hbuf.shape[1]
+        self.hout = [torch.empty((6, n), dtype=torch.float32).pin_memory() for _ in range(max(nout, self.NB))]
+        self.dbuf = [torch.empty((9, n), dtype=torch.float32, device="cuda") for _ in range(self.NB)]
+        self.pe = [pm.Particles.from_tensors(d[0:3], d[3:6], d[6], d[7].view(torch.int32), d[8].view(torch.int32))
+                   for d in self.dbuf]
+        self.h2d_bytes = hbuf.numel() * hbuf.element_size()
+        self.d2h_bytes = self.hout[0].numel() * self.hout[0].element_size()
+        self.main = torch.cuda.current_stream()
+        self.up, self.down = torch.cuda.Stream(), torch.cuda.Stream()
+        self.ev_up = [torch.cuda.Event() for _ in range(self.NB)]
+        self.ev_step = [torch.cuda.Event() for _ in range(self.NB)]
+        self.ev_down = [torch.cuda.Event() for _ in range(self.NB)]
+        self.reset()
+
+    def reset(self):
+        """Marks every buffer free (its download events as done)."""
+        for e in self.ev_down:
+            e.record(self.main)
+
+    def request(self, k, overlap=True):
+        """Enqueues request k; returns the index o of the host block hout[o]
+        that receives its result (complete once the launching stream has
+        passed join())."""
+        import torch
+        b = k % self.NB if overlap else 0
+        o = k % len(self.hout)
+        if overlap:
+            with torch.cuda.stream(self.up):
+                self.up.wait_event(self.ev_down[b])   # request k-NB's download has read dbuf[b]
+                self.dbuf[b].copy_(self.hbuf, non_blocking=True)
+                self.ev_up[b].record(self.up)
+            self.main.wait_event(self.ev_up[b])
+            self.ctx.step(self.pe[b], self.dt, 1)
+            self.ev_step[b].record(self.main)
+            with torch.cuda.stream(self.down):
+                self.down.wait_event(self.ev_step[b])
+                self.hout[o].copy_(self.dbuf[b][0:6], non_blocking=True)
+                self.ev_down[b].record(self.down)
+        else:
+            self.dbuf[b].copy_(self.hbuf, non_blocking=True)
+            self.ctx.step(self.pe[b], self.dt, 1)
+            self.hout[o].copy_(self.dbuf[b][0:6], non_blocking=True)
+            self.ev_down[b].record(self.main)
+        return o
+
+    def join(self):
+        """The launching stream waits for every download enqueued so far."""
+        for e in self.ev_down:
+            self.main.wait_event(e)
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -332,68 +415,24 @@ def run_ours(args):
     span_ms = s0.elapsed_time(s1) / Ks
     span_gbs = sum(pb[p] for p in fft_phases) / (span_ms / 1e3) / 1e9
 
-    # ---- end to end through the C ABI with host buffers ----
-    # Each iteration is one request: the step's whole particle state (x, y,
-    # z, vx, vy, vz, m, galaxy id, flags) goes up as one pinned block, one
-    # step runs, and the updated positions and velocities come back as one
-    # block.  Requests rotate over three device buffers, so the upload of
-    # request k+1 and the download of request k-1 run on their own streams
-    # while request k steps (the library keeps the captured step of each
-    # buffer); a buffer is refilled only after its previous download.  The
-    # same loop without the overlap is reported as serial_value.
-    NB = 3
-    hbuf = torch.empty((9, n), dtype=torch.float32).pin_memory()
-    for k, a in enumerate((host["pos"][0], host["pos"][1], host["pos"][2], host["vel"][0], host["vel"][1],
-                           host["vel"][2], m32)):
-        hbuf[k].copy_(torch.from_numpy(np.ascontiguousarray(a)))
-    hbuf[7].view(torch.int32).copy_(torch.from_numpy(w["gal"].astype(np.int32)))
-    hbuf[8].view(torch.int32).zero_()
-    hout = [torch.empty((6, n), dtype=torch.float32).pin_memory() for _ in range(NB)]
-    dbuf = [torch.empty((9, n), dtype=torch.float32, device="cuda") for _ in range(NB)]
-    pe = [pm.Particles.from_tensors(d[0:3], d[3:6], d[6], d[7].view(torch.int32), d[8].view(torch.int32))
-          for d in dbuf]
-    h2d = hbuf.numel() * hbuf.element_size()
-    d2h = hout[0].numel() * hout[0].element_size()
+    # ---- end to end through the C ABI with host buffers (RequestPipeline) ----
+    hbuf = request_block(host, m32, w["gal"])
+    pipe = RequestPipeline(ctx, hbuf, dt)
+    h2d, d2h = pipe.h2d_bytes, pipe.d2h_bytes
     Ke = max(1, min(K, 200))
-    main = torch.cuda.current_stream()
-    up, down = torch.cuda.Stream(), torch.cuda.Stream()
-    ev_up = [torch.cuda.Event() for _ in range(NB)]
-    ev_step = [torch.cuda.Event() for _ in range(NB)]
-    ev_down = [torch.cuda.Event() for _ in range(NB)]
-
-    def request(k, overlap=True):
-        b = k % NB if overlap else 0
-        if overlap:
-            with torch.cuda.stream(up):
-                up.wait_event(ev_down[b])      # request k-NB's download has read dbuf[b]
-                dbuf[b].copy_(hbuf, non_blocking=True)
-                ev_up[b].record(up)
-            main.wait_event(ev_up[b])
-            ctx.step(pe[b], dt, 1)
-            ev_step[b].record(main)
-            with torch.cuda.stream(down):
-                down.wait_event(ev_step[b])
-                hout[b].copy_(dbuf[b][0:6], non_blocking=True)
-                ev_down[b].record(down)
-        else:
-            dbuf[b].copy_(hbuf, non_blocking=True)
-            ctx.step(pe[b], dt, 1)
-            hout[b].copy_(dbuf[b][0:6], non_blocking=True)
 
     def e2e_run(overlap):
-        for e in ev_down:
-            e.record(main)
-        for k in range(NB):                   # untimed: every buffer's step is captured here
-            request(k, overlap)
+        pipe.reset()
+        for k in range(pipe.NB):              # untimed: every buffer's step is captured here
+            pipe.request(k, overlap)
         torch.cuda.synchronize()
         barrier()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        f0.record(main)
+        f0.record(pipe.main)
         for k in range(Ke):
-            request(k, overlap)
-        for e in ev_down:
-            main.wait_event(e)
-        f1.record(main)
+            pipe.request(k, overlap)
+        pipe.join()
+        f1.record(pipe.main)
         barrier()
         return job_rate(world, n, Ke, slowest_rank_ms(f0.elapsed_time(f1), world, "cuda"))
 
