@@ -505,6 +505,7 @@ __global__ void __launch_bounds__(WShape<T, L>::THREADS, (L >= 512 ? 2 : 3))
     // thread 0 issues every copy; counts per buffer of loads issued and of
     // tiles sent (to drain after an expired wait)
     int issued0 = 0, issued1 = 0, done0 = 0, done1 = 0;
+    long long deferred = -1;   // thread 0: tile whose buffer awaits its refill
     if (tid == 0) {
         if (blockIdx.x < ntiles) { issue_load(blockIdx.x, 0); ++issued0; }
         if (blockIdx.x + gridDim.x < ntiles) { issue_load(blockIdx.x + gridDim.x, 1); ++issued1; }
@@ -539,6 +540,18 @@ __global__ void __launch_bounds__(WShape<T, L>::THREADS, (L >= 512 ? 2 : 3))
         // overwrite this buffer without a block barrier; the block-synchronous
         // variant keeps the warps in step.
         if (!FREE) __syncthreads();
+        if (!FREE && tid == 0 && deferred >= 0) {
+            // the previous tile's store has long read its buffer by now: the
+            // wait is short, and the refill (the tile after this one) still
+            // lands well before it is needed
+            bulk_wait_read();
+            const int db = b ^ 1;
+            if (deferred + 2 * (long long)gridDim.x < ntiles) {
+                issue_load(deferred + 2 * (long long)gridDim.x, db);
+                if (db) ++issued1; else ++issued0;
+            }
+            deferred = -1;
+        }
         const long long q0 = tile * S::COLS;
         const int k0 = (int)(q0 & (nx2 - 1));
         if (hstage && tid == 0) {
@@ -633,10 +646,14 @@ __global__ void __launch_bounds__(WShape<T, L>::THREADS, (L >= 512 ? 2 : 3))
             issue_store(tile, in);
             bulk_commit();
             if (b) ++done1; else ++done0;
-            bulk_wait_read();   // the staged outputs have been read out
-            if (tile + 2 * (long long)gridDim.x < ntiles) {
-                issue_load(tile + 2 * (long long)gridDim.x, b);
-                if (b) ++issued1; else ++issued0;
+            if (FREE) {
+                bulk_wait_read();   // the staged outputs have been read out
+                if (tile + 2 * (long long)gridDim.x < ntiles) {
+                    issue_load(tile + 2 * (long long)gridDim.x, b);
+                    if (b) ++issued1; else ++issued0;
+                }
+            } else {
+                deferred = tile;    // buffer b is refilled once the store has read it
             }
         }
     }
