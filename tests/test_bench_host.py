@@ -1,0 +1,47 @@
+"""Host logic of bench.py (CPU): the byte model behind the roofline numbers
+and the count of kernel launches it claims.
+
+Byte model per mass set of A = nx ny nz active cells (8-byte complex
+spectra, S1 = (nx+1) ny nz): x forward 8A + 8 S1, y forward 8 S1 + 16 S1,
+z convolve 2 x 16 S1 (+ the H-hat octant once per geometry), y inverse
+16 S1 + 8 S1, x inverse 8 S1 + 4A -- in all 12 A + 96 S1, i.e. about 108 A."""
+import numpy as np
+
+import bench
+from paper_1210_1736_gb300 import workloads as W
+
+
+def _one_set(n):
+    return dict(galaxies=[dict(coarse=(n, n, n, 10.0, 1.0), medium=None, fine=None)])
+
+
+def test_byte_model_of_one_set():
+    for n in (32, 128):
+        A, S1 = n ** 3, (n + 1) * n * n
+        b = bench.phase_bytes(_one_set(n), 0, 4)
+        fft = sum(b[p] for p in ("fft_x_fwd", "fft_y_fwd", "fft_z_conv", "fft_y_inv", "fft_x_inv"))
+        hhat = 4 * (n + 1) ** 3
+        assert fft == 12 * A + 96 * S1 + hhat
+        assert abs(fft - hhat - 108 * A) <= 96 * A / n + 1
+
+
+def test_byte_model_counts_pairs_and_particles():
+    spec = dict(galaxies=[dict(coarse=(128, 128, 128, 32.0, 1.0), medium=(128, 128, 128, 6.0, 0.25),
+                               fine=(128, 128, 32, 1.5, 1.0))])
+    n = 1000
+    b = bench.phase_bytes(spec, n, 4)
+    A2, A1 = 128 ** 3, 128 * 128 * 32
+    # five mass sets: two on each 128^3 geometry, one on the fine grid
+    assert b["deposit"] == n * 24 + 8 * (4 * A2 + A1)
+    assert b["force_kick_drift"] == n * 52
+    assert b["recentre"] == n * 24
+
+
+def test_launch_count_per_pair():
+    assert bench.fft_pairs(_one_set(32)) == 1
+    g = W.galaxy_small()
+    assert bench.fft_pairs(g) == 3
+    # per step: recentre (2), deposit (1), five passes per pair, force (1);
+    # six sort kernels every sort_every-th step
+    assert bench.launches(g, 10, 0) == 10 * (2 + 1 + 15 + 1)
+    assert bench.launches(g, 10, 5) == 10 * 19 + 2 * 6
