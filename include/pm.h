@@ -283,8 +283,8 @@ int pm_disc_diagnostics(pm_ctx *ctx, const pm_particles *p, const uint8_t *selec
 /* Allocation-free potential of one isolated grid.  The paper has no
  * counterpart: this entry point exists for callers that cannot call
  * cudaMalloc (a host application whose device memory is pre-partitioned by
- * its own pool, a plugin that may not allocate after start-up, code issued
- * while another thread captures a CUDA graph in global mode).
+ * its own pool, where a cudaMalloc fails or synchronises the device; a
+ * plugin that may not allocate after start-up).
  *
  * Computes what pm_solve computes for one grid: Phi = G/l_xy * (rho * H) on
  * the nx*ny*nz active region of the doubled grid, with H-hat rebuilt in FP64
@@ -302,12 +302,32 @@ int pm_disc_diagnostics(pm_ctx *ctx, const pm_particles *p, const uint8_t *selec
  * the previous call's contents; each call writes every scratch value before
  * reading it, so nothing needs clearing, but calls whose work overlaps on the
  * GPU (different streams, or other threads) race on it and must be ordered
- * by the caller.  The first call on a device looks up the array's device
- * address and sets kernel attributes, so it should come before any stream
- * capture that includes later calls. */
+ * by the caller.  Every call looks up the array's device address (a host-side
+ * lookup) and the first call on a device and precision also sets kernel
+ * attributes.
+ *
+ * Failure of a bounded wait: a pass whose tensor copy does not complete
+ * within its time limit stops early; the call's last kernel then fills phi
+ * with NaN and raises a status word of the device, which
+ * pm_potential_static_status reports. */
 int pm_potential_static(const int64_t *rho, void *phi, int32_t nx, int32_t ny, int32_t nz,
                         double l_xy, double l_z, double G, double h000, int32_t shift,
                         int32_t precision, void *stream);
+
+/* Status of the allocation-free calls on the current device (no counterpart
+ * in the paper): waits for `stream`, then returns PM_E_TIMEOUT if a
+ * pm_potential_static call since the last status query had an expired wait
+ * (its phi holds NaN), else PM_OK; the status word is cleared by the query.
+ * Allocates nothing; synchronises. */
+int pm_potential_static_status(void *stream);
+
+/* Self-test of that failure report (no counterpart in the paper): one block
+ * waits, with the bounded wait of the passes (2 s), on a barrier nothing
+ * arrives at, and sets the error word of the static scratch; the same last
+ * kernel as pm_potential_static then fills phi (n values, float or double
+ * per precision) with NaN and raises the status word.  Enqueued on `stream`;
+ * pm_potential_static_status then returns PM_E_TIMEOUT. */
+int pm_static_selftest_wait_expiry(void *phi, int64_t n, int32_t precision, void *stream);
 
 #ifdef __cplusplus
 }

@@ -6,7 +6,7 @@ benchmark's CPU-baseline leg; the product path never imports it.
 from .pm_oracle import *  # noqa: F401,F403
 from .pm_cic import *  # noqa: F401,F403
 from .pm_diag import *  # noqa: F401,F403
-from .pm_oracle import Geometry, Galaxy, System, State, cell_length
+from .pm_oracle import Geometry, Galaxy, System, State, cell_length, mass_bound
 import numpy as np
 
 
@@ -19,7 +19,9 @@ def geometry_from_spec(spec):
     return Geometry(nx, ny, nz, l_xy, q * l_xy)
 
 
-def system_from_workload(w):
+def system_from_workload(w, mb=None):
+    """System of a workload dict; mb: the mass bound (default: the oracle's
+    own sum |m| of the workload's masses)."""
     gals = []
     for g in w["galaxies"]:
         gals.append(Galaxy(coarse=geometry_from_spec(g["coarse"]),
@@ -28,9 +30,8 @@ def system_from_workload(w):
                            r_core=g["r_core"], r_out=g["r_out"],
                            centre=tuple(g["centre"]), recentre=bool(g["recentre"])))
     s = w["system"]
-    from paper_1210_1736_gb300.workloads import mass_bound
     return System(galaxies=gals, r_sys=s["r_sys"], sys_centre=tuple(s["sys_centre"]),
-                  G=s["G"], h000=s["h000"], mass_bound=mass_bound(w["m"]),
+                  G=s["G"], h000=s["h000"], mass_bound=mass_bound(w["m"]) if mb is None else float(mb),
                   precision=w.get("precision", "fp64"))
 
 

@@ -51,7 +51,7 @@ from functools import lru_cache
 import numpy as np
 
 __all__ = [
-    "Geometry", "Galaxy", "System", "cell_length", "q_crit", "fixed_shift",
+    "Geometry", "Galaxy", "System", "cell_length", "q_crit", "fixed_shift", "mass_bound",
     "quantize_mass", "offset_f32", "cell_index", "in_box", "region",
     "classify", "deposit", "green_doubled", "green_hat", "potential_fft",
     "potential_direct", "accel_from_grid", "phi_at_particle",
@@ -143,6 +143,12 @@ def fixed_shift(mass_bound: float) -> int:
     f, e = math.frexp(mass_bound)       # mass_bound = f * 2^e, 0.5 <= f < 1
     ceil_log2 = e - 1 if f == 0.5 else e
     return 62 - ceil_log2
+
+
+def mass_bound(m) -> float:
+    """The bound sum |m_i| that fixes the fixed-point scale (1 for no mass)."""
+    b = float(np.sum(np.abs(np.asarray(m, dtype=np.float64))))
+    return b if b > 0 else 1.0
 
 
 def quantize_mass(m, s: int) -> np.ndarray:

@@ -80,6 +80,8 @@ _SIGS.update({
     "pm_set_sort_interval": (C.c_int, [_vp, C.c_int32]),
     "pm_potential_static": (C.c_int, [_vp, _vp, C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_double,
                                       C.c_double, C.c_double, C.c_int32, C.c_int32, _vp]),
+    "pm_potential_static_status": (C.c_int, [_vp]),
+    "pm_static_selftest_wait_expiry": (C.c_int, [_vp, C.c_int64, C.c_int32, _vp]),
     "pm_disc_diagnostics": (C.c_int, [_vp, _P(pm_particles), _vp, _P(pm_disc_query), _P(C.c_double)]),
     "pm_cic_deposit": (C.c_int, [_vp, _P(pm_particles)]),
     "pm_cic_force": (C.c_int, [_vp, _P(pm_particles), _vp, _vp, _vp]),

@@ -6,7 +6,6 @@ import numpy as np
 
 import oracle as O
 from paper_1210_1736_gb300 import pm
-from paper_1210_1736_gb300.workloads import mass_bound
 
 
 def require_cuda():
@@ -27,7 +26,8 @@ def gpu_setup(w, pos=None, vel=None, m=None, gal=None):
     vel = w["vel"] if vel is None else vel
     m = w["m"] if m is None else m
     gal = w["gal"] if gal is None else gal
-    mb = mass_bound(cast(w, m))
+    # the same bound goes to both sides (it fixes the fixed-point scale)
+    mb = O.mass_bound(cast(w, m))
     ctx = pm.Context(w, mb)
     parts = pm.Particles(cast(w, pos), cast(w, vel), cast(w, m), gal, precision=w["precision"])
     return ctx, parts
@@ -41,7 +41,7 @@ def oracle_setup(w, pos=None, vel=None, m=None, gal=None):
     ww["m"] = cast(w, m)
     if gal is not None:
         ww["gal"] = gal
-    system = O.system_from_workload(ww)
+    system = O.system_from_workload(ww, O.mass_bound(ww["m"]))
     state = O.state_from_workload(ww, pos=pos, vel=vel, m=m)
     return system, state
 

@@ -8,7 +8,6 @@ import pytest
 import oracle as O
 from oracle import pm_cic as OC
 from paper_1210_1736_gb300 import pm, workloads as W
-from paper_1210_1736_gb300.workloads import mass_bound
 from tests._harness import gpu_setup, oracle_setup, rel_force_errors
 
 pytestmark = pytest.mark.gpu
@@ -144,7 +143,7 @@ class _Problem:
         w = dict(self.w, precision=precision)
         dt = torch.float32 if precision == "fp32" else torch.float64
         npdt = np.float32 if precision == "fp32" else np.float64
-        ctx = pm.Context(w, 1.25 * mass_bound(np.asarray(w["m"]).astype(npdt)))
+        ctx = pm.Context(w, 1.25 * O.mass_bound(np.asarray(w["m"]).astype(npdt)))
         gal = torch.tensor(np.asarray(w["gal"]), dtype=torch.int32, device="cuda")
         base = [torch.tensor(np.ascontiguousarray(np.asarray(w[k]).astype(npdt)), device="cuda")
                 for k in ("pos", "vel", "m")]

@@ -256,13 +256,12 @@ def test_leapfrog_closed_form_harmonic():
 
 def _nested_plummer(npart=60000, seed=3):
     from paper_1210_1736_gb300 import synth
-    from paper_1210_1736_gb300.workloads import mass_bound
     pos, vel, m = synth.plummer(npart, np.random.default_rng(seed), M=1.0, a=0.4, r_trunc=4.0)
     fine = O.Geometry(32, 32, 32, O.cell_length(0.6, 32), O.cell_length(0.6, 32))
     med = O.Geometry(32, 32, 32, O.cell_length(1.6, 32), 0.5 * O.cell_length(1.6, 32))
     coarse = O.Geometry(32, 32, 32, O.cell_length(6.0, 32), O.cell_length(6.0, 32))
     gal = O.Galaxy(coarse=coarse, medium=med, fine=fine, r_core=0.6, r_out=1.6)
-    system = O.System(galaxies=[gal], r_sys=6.0, mass_bound=mass_bound(m))
+    system = O.System(galaxies=[gal], r_sys=6.0, mass_bound=O.mass_bound(m))
     st = O.State(pos=pos, vel=vel, m=m, gal=np.zeros(npart, np.int64),
                  flags=np.zeros(npart, np.int64), centres=np.zeros((1, 3)))
     return system, st

@@ -1,9 +1,11 @@
 """pm_potential_static, the allocation-free potential solve, against pm_solve.
 
-Callers that cannot allocate device memory (pre-partitioned pools, plugins,
-code issued during another thread's global-mode graph capture) use
-pm_potential_static; its result must be the one the context path gives for
-the same density.  This file is collected last so that a run stopping at the
+Callers that cannot allocate device memory (a host application whose device
+memory is pre-partitioned by its own pool, a plugin that may not allocate
+after start-up) use pm_potential_static; its result must be the one the
+context path gives for the same density, and an expired bounded wait inside
+it must reach the caller (NaN output, PM_E_TIMEOUT from
+pm_potential_static_status).  This file is collected last so that a run stopping at the
 first failure has run every other test first.
 """
 import ctypes as C
@@ -43,8 +45,11 @@ def test_static_potential_matches_context_path(precision):
     torch = require_cuda()
     tol = 2e-6 if precision == "fp32" else 1e-12
     dt = torch.float32 if precision == "fp32" else torch.float64
+    # 64^3: z transforms of length 128, whose tiles stage their H-hat rows by
+    # a bulk copy into the static scratch
     cases = [_single_grid(32, 32, 32, 1.0, precision, seed=1),
              _single_grid(64, 32, 16, 0.5, precision, seed=2),
+             _single_grid(64, 64, 64, 1.0, precision, seed=4),
              W.plummer32() if precision == "fp64" else _single_grid(128, 128, 32, 1.0, precision, seed=3)]
     for w in cases:
         ctx, parts = gpu_setup(w)
@@ -62,6 +67,7 @@ def test_static_potential_matches_context_path(precision):
             got = phi_dev.cpu().numpy().astype(np.float64)
             err = np.max(np.abs(got - ref)) / np.max(np.abs(ref))
             assert err < tol, (w["name"], g.nx, g.ny, g.nz, call, err)
+        assert pm.lib().pm_potential_static_status(C.c_void_p(torch.cuda.current_stream().cuda_stream)) == pm.PM_OK
         ctx.close()
 
 
@@ -73,3 +79,35 @@ def test_static_potential_rejects_oversize_grid():
                                       128, 128, 128, 0.1, 0.1, 1.0, 1.0, 40, pm.PM_FP32, None)
     assert rc == pm.PM_E_ARG
     assert b"static scratch holds" in pm.lib().pm_last_error()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_static_expired_wait_reaches_the_caller(precision):
+    """A bounded wait that expires (one block waits 2 s on a barrier nothing
+    arrives at; no fault) leaves NaN in the output and PM_E_TIMEOUT in the
+    status query, which clears it; the next solve is unaffected."""
+    torch = require_cuda()
+    dt = torch.float32 if precision == "fp32" else torch.float64
+    prec = pm.PM_FP32 if precision == "fp32" else pm.PM_FP64
+    st = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    phi = torch.zeros(4096, dtype=dt, device="cuda")
+    assert pm.lib().pm_potential_static_status(st) == pm.PM_OK
+    assert pm.lib().pm_static_selftest_wait_expiry(C.c_void_p(phi.data_ptr()), phi.numel(), prec, st) == pm.PM_OK
+    assert pm.lib().pm_potential_static_status(st) == pm.PM_E_TIMEOUT
+    assert b"time limit" in pm.lib().pm_last_error()
+    assert bool(torch.isnan(phi).all())
+    assert pm.lib().pm_potential_static_status(st) == pm.PM_OK   # cleared by the query
+
+    w = _single_grid(32, 32, 16, 1.0, precision, seed=5)
+    ctx, parts = gpu_setup(w)
+    ctx.deposit(parts)
+    ctx.solve()
+    rho = ctx.density(0, 5)
+    ref = ctx.potential(0, 5).astype(np.float64)
+    g = ctx.gals[0].coarse
+    out = torch.full(rho.shape, float("nan"), dtype=dt, device="cuda")
+    _static_call(torch, torch.from_numpy(rho).cuda(), out, g, ctx.sys.G, ctx.sys.h000, ctx.info()["shift"], precision)
+    assert pm.lib().pm_potential_static_status(st) == pm.PM_OK
+    got = out.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) < (2e-6 if precision == "fp32" else 1e-12)
+    ctx.close()
