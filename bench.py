@@ -2,9 +2,11 @@
 """Benchmark of the nested-grid particle-mesh step (Superbox-10) on GB300.
 
 One step = recentre + deposit + (x, y, z-convolve, y, x) FFT passes on every
-grid + force/kick-drift, on the 1M-particle disc-bulge-halo galaxy with
-grids 128^3 (coarse), 128^3 flattened q = 1/4 (medium) and 128x128x32 (fine),
-FP32 with int64 fixed-point density.  Prints one JSON line.
+grid + force/kick-drift, FP32 with int64 fixed-point density.  The default
+workload is the largest: a 16M-particle disc-bulge-halo galaxy on 256^3,
+256^3 (q = 1/4) and 256x256x64 grids plus two 250k-particle satellites with
+128^3 grids.  The same line reports the 1M-particle galaxy and the 4M-particle
+merger (extra_workloads).  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -31,7 +33,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "particle-steps/s per nested-grid step; FFT-convolve GB/s vs HBM peak"
 UNIT = "particle-steps/s"
-WORKLOAD = "galaxy_1m"
+WORKLOAD = "large_16m"
+EXTRA_WORKLOADS = ("galaxy_1m", "merger_4m")
 WORKLOAD_DESC = {
     "galaxy_1m": "galaxy_1m: 1M particles (400k exp. disc, 100k Hernquist bulge, 500k truncated NFW halo); "
                  "grids coarse 128^3, medium 128^3 q=1/4, fine 128x128x32; dt=0.01",
@@ -240,6 +243,16 @@ def phase_bytes(w, n, esz):
     return b
 
 
+def bench_config(w, workload, n, world):
+    """The `config` object of the JSON line, identical in both arms."""
+    geoms = {tuple(g[k]) for g in w["galaxies"] for k in ("coarse", "medium", "fine") if g.get(k)}
+    ws = sum(phase_bytes(w, n, 4).values())
+    return {"workload": WORKLOAD_DESC[workload], "particles_per_gpu": n, "galaxies": len(w["galaxies"]),
+            "geometries": len(geoms),
+            "l2": f"algorithmic bytes per step ~{ws / 1e9:.2f} GB > 129 MB L2 (inputs larger than L2, no flush)",
+            "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"}
+
+
 def fft_pairs(w):
     """FFT launches per pass: one per pair of mass sets sharing a transform
     (per galaxy: grids 4+5, or 5 alone; grids 2+3; grid 1)."""
@@ -345,6 +358,80 @@ class RequestPipeline:
             self.main.wait_event(e)
 
 
+def device_phases(ctx, parts, w, n, dt, K):
+    """Per-phase device times (the step's kernels launched with CUDA events
+    between phases on the launching stream, K steps), the algorithmic bytes
+    of each phase, and the convolution span as the step runs it (all
+    geometries' pass chains on their branch streams, overlapping)."""
+    import torch
+    ph = ctx.step_timed(parts, dt, K)
+    phase_ms = {p: ph[i] / K for i, p in enumerate(PHASES)}
+    phase_ms["spatial_sort"] = ph[SORT_PHASE] / K
+    pb = phase_bytes(w, n, 4)
+    fft_phases = PHASES[2:7]
+    dom = max(PHASES, key=lambda p: phase_ms[p])
+    conv_ms = sum(phase_ms[p] for p in fft_phases)
+    conv_gbs = sum(pb[p] for p in fft_phases) / (conv_ms / 1e3) / 1e9
+    ctx.solve()
+    torch.cuda.synchronize()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    Ks = max(10, min(K, 200))
+    s0.record()
+    for _ in range(Ks):
+        ctx.solve()
+    s1.record()
+    torch.cuda.synchronize()
+    span_ms = s0.elapsed_time(s1) / Ks
+    span_gbs = sum(pb[p] for p in fft_phases) / (span_ms / 1e3) / 1e9
+    return {"phase_ms": phase_ms, "pb": pb, "dom": dom, "conv_ms": conv_ms, "conv_gbs": conv_gbs,
+            "span_ms": span_ms, "span_gbs": span_gbs}
+
+
+def extra_workload(name, K, Wm, sort_every, fp64_steps):
+    """Step rate, phase roofline and convolution span of another workload
+    with the same kernels (and, with fp64_steps, the FP64 comparison)."""
+    import torch
+    from paper_1210_1736_gb300 import pm, workloads as W
+    from paper_1210_1736_gb300.workloads import mass_bound
+    w = getattr(W, name)()
+    dt = w["dt"]
+    m32 = w["m"].astype(np.float32)
+    host = dict(pos=w["pos"].astype(np.float32), vel=w["vel"].astype(np.float32), m=m32, gal=w["gal"])
+    fp64 = fp64_comparison(w, host, m32, fp64_steps) if fp64_steps > 0 else None
+    ctx = pm.Context(w, mass_bound(m32))
+    parts = pm.Particles(host["pos"], host["vel"], m32, w["gal"])
+    n = parts.n
+    ctx.deposit(parts)
+    ctx.solve()
+    ctx.kick(parts, -0.5 * dt)
+    ctx.set_sort_interval(sort_every)
+    ctx.step(parts, dt, Wm)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    ctx.step(parts, dt, K)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / K
+    dm = device_phases(ctx, parts, w, n, dt, K)
+    peak, _ = peaks()
+    z = dm["phase_ms"]["fft_z_conv"]
+    out = {"workload": WORKLOAD_DESC[name], "particles": n, "steps": K, "value": n / (ms / 1e3),
+           "unit": UNIT, "ms_per_step": ms,
+           "fft_z_conv": {"ms_per_step": z, "frac": dm["pb"]["fft_z_conv"] / (z / 1e3) / 1e9 / peak},
+           "fft_convolve": {"frac": dm["conv_gbs"] / peak, "span_frac": dm["span_gbs"] / peak,
+                            "span_ms_per_step": dm["span_ms"]},
+           "step_bound_frac": sum(dm["pb"].values()) / (peak * 1e9) * 1e3 / ms,
+           "phase_ms_per_step": dm["phase_ms"]}
+    if fp64 is not None:
+        fp64["speedup_fp32"] = fp64["ms_per_step"] / ms
+        out["fp64_path"] = fp64
+    ctx.close()
+    del parts
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -389,31 +476,11 @@ def run_ours(args):
     ms = slowest_rank_ms(e0.elapsed_time(e1), world, "cuda")
     value = job_rate(world, n, K, ms)
 
-    # ---- per-phase device times (same kernels, launched with events between phases) ----
-    ph = ctx.step_timed(parts, dt, K)
-    phase_ms = {p: ph[i] / K for i, p in enumerate(PHASES)}
-    phase_ms["spatial_sort"] = ph[SORT_PHASE] / K
-    esz = 4
-    pb = phase_bytes(w, n, esz)
-    fft_phases = PHASES[2:7]
-    dom = max(PHASES, key=lambda p: phase_ms[p])
+    # ---- per-phase device times and the convolution span ----
+    dm = device_phases(ctx, parts, w, n, dt, K)
+    phase_ms, pb, dom = dm["phase_ms"], dm["pb"], dm["dom"]
     peak, peak_kind = peaks()
     achieved = pb[dom] / (phase_ms[dom] / 1e3) / 1e9
-    conv_ms = sum(phase_ms[p] for p in fft_phases)
-    conv_gbs = sum(pb[p] for p in fft_phases) / (conv_ms / 1e3) / 1e9
-    # the convolution span as the step runs it: all geometries' pass chains
-    # on their branch streams, overlapping (K solves between two events)
-    ctx.solve()
-    torch.cuda.synchronize()
-    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    Ks = max(10, min(K, 200))
-    s0.record()
-    for _ in range(Ks):
-        ctx.solve()
-    s1.record()
-    torch.cuda.synchronize()
-    span_ms = s0.elapsed_time(s1) / Ks
-    span_gbs = sum(pb[p] for p in fft_phases) / (span_ms / 1e3) / 1e9
 
     # ---- end to end through the C ABI with host buffers (RequestPipeline) ----
     hbuf = request_block(host, m32, w["gal"])
@@ -443,13 +510,11 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": Wm,
         "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic (seeded disc-bulge-halo galaxy, random order)",
-        "config": {"workload": WORKLOAD_DESC[args.workload],
-                   "particles_per_gpu": n, "galaxies": len(w["galaxies"]), "geometries": ctx.info()["ngeom"],
-                   "spatial_sort_every": args.sort_every,
-                   "solve_schedule": {0: "one branch per geometry", 1: "two staggered lanes",
-                                      -1: "single geometry"}[ctx.info()["solve_schedule"]],
-                   "l2": f"working set per step ~{ctx.info()['bytes'] / 1e9:.2f} GB > 129 MB L2 (no flush needed)",
-                   "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"},
+        "config": bench_config(w, args.workload, n, world),
+        "spatial_sort_every": args.sort_every,
+        "solve_schedule": {0: "one branch per geometry", 1: "two staggered lanes",
+                           -1: "single geometry"}[ctx.info()["solve_schedule"]],
+        "device_bytes": ctx.info()["bytes"],
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": ncu_traffic(dom, args.workload)},
@@ -458,8 +523,9 @@ def run_ours(args):
                        "frac": sum(pb.values()) / (peak * 1e9) * 1e3 / (ms / K),
                        "note": "whole step by the byte model (every phase's algorithmic HBM bytes) at the "
                                "measured copy bandwidth, against the graph-replayed step"},
-        "fft_convolve": {"gbs": conv_gbs, "frac": conv_gbs / peak, "ms_per_step": conv_ms,
-                         "span_gbs": span_gbs, "span_frac": span_gbs / peak, "span_ms_per_step": span_ms,
+        "fft_convolve": {"gbs": dm["conv_gbs"], "frac": dm["conv_gbs"] / peak, "ms_per_step": dm["conv_ms"],
+                         "span_gbs": dm["span_gbs"], "span_frac": dm["span_gbs"] / peak,
+                         "span_ms_per_step": dm["span_ms"],
                          "note": "gbs/frac: the five pass phases timed one after another; span: pm_solve as "
                                  "the step runs it (geometry chains overlapping), byte model over time"},
         "phase_ms_per_step": phase_ms,
@@ -473,35 +539,83 @@ def run_ours(args):
     if fp64 is not None:
         fp64["speedup_fp32"] = fp64["ms_per_step"] / (ms / K)
         line["fp64_path"] = fp64
+    ctx.close()
+    del pipe, parts
+    torch.cuda.empty_cache()
+    if rank == 0 and world == 1:
+        extras = [x for x in args.extra_workloads.split(",") if x and x != args.workload]
+        line["extra_workloads"] = {x: extra_workload(x, K, Wm, args.sort_every,
+                                                     args.fp64_steps if x == "galaxy_1m" else 0)
+                                   for x in extras}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = oracle_rate(w, args.workload, budget_s=25.0, max_steps=3)
+        line["cpu_baseline"] = oracle_sampled_rate(w, args.workload, 3)
     if world > 1:
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(line), flush=True)
 
 
-def oracle_rate(w, workload, budget_s, max_steps, warmup=0):
-    """The FP64 oracle, as it stands, on this host: full steps of the same
-    workload until max_steps or the time budget is reached."""
+def oracle_sampled_rate(w, workload, steps):
+    """The FP64 oracle, as it stands, timed on bounded samples of its step.
+
+    With S mass sets, sampled step k runs the per-particle work of one full
+    step (recentre sums, classification, deposit, forces by the combination
+    rule, kick, drift) on particle slice k mod S of S equal slices, plus the
+    doubled-grid convolution of one mass set, taken in an order that visits
+    every distinct geometry first.  A full step's time is estimated as S x
+    the mean slice time plus, for every mass set, the mean time measured for
+    its geometry's convolution (an FFT's cost does not depend on the data).
+    Forces use zero potentials of the right shapes (the gathers cost the
+    same).  At least one step per distinct geometry is run."""
     import oracle as O
     ww = dict(w)
     ww["m"] = w["m"].astype(np.float32)
     system = O.system_from_workload(ww)
     state = O.state_from_workload(ww)
-    for _ in range(warmup):
-        state = O.step(state, system, w["dt"])
-    done, t0 = 0, time.perf_counter()
-    while done < max_steps:
-        state = O.step(state, system, w["dt"])
-        done += 1
-        if time.perf_counter() - t0 > budget_s:
-            break
-    el = time.perf_counter() - t0
+    sets = []
+    for g, gal in enumerate(system.galaxies):
+        for k, geom, _, _ in O.mass_sets(gal):
+            sets.append((g, k, geom))
+            O.green_hat(geom, system.h000)      # H-hat tables: set-up, outside the clock (as the library's)
+    first, rest, seen = [], [], set()
+    for x in sets:
+        (rest if x[2] in seen else first).append(x)
+        seen.add(x[2])
+    order = first + rest
+    S = len(sets)
+    phi0 = [{k: np.zeros(geom.shape) for gg, k, geom in sets if gg == g} for g in range(len(system.galaxies))]
     n = len(state.m)
-    return {"value": n * done / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{done} full FP64 oracle step(s) of {workload} ({n} particles), "
-                      f"{el:.1f} s, single-threaded numpy"}
+    bounds = np.linspace(0, n, S + 1).astype(np.int64)
+    t_part, t_conv = [], {}
+    nrun = max(steps, len(first))
+    for k in range(nrun):
+        a, b = bounds[k % S], bounds[k % S + 1]
+        sub = O.State(state.pos[:, a:b].copy(), state.vel[:, a:b].copy(), state.m[a:b].copy(),
+                      state.gal[a:b].copy(), state.flags[a:b].copy(), state.centres.copy())
+        g, kk, geom = order[k % S]
+        t0 = time.perf_counter()
+        sub.centres = O.recentre(sub, system)
+        flags, own = O.classify(sub, system)
+        rho, flags, sh = O.deposit(sub, system, flags, own)
+        acc = O.accelerations(sub, system, phi0, flags)
+        live = (flags & O.FLAG_LOST) == 0
+        sub.vel = O.kick(sub.vel, acc, w["dt"], live)
+        sub.pos = O.drift(sub.pos, sub.vel, w["dt"], live)
+        t1 = time.perf_counter()
+        O.potential_fft(O.rho_real(rho[g][kk], sh), geom, system.G, system.h000)
+        t2 = time.perf_counter()
+        t_part.append(t1 - t0)
+        t_conv.setdefault(geom, []).append(t2 - t1)
+    tp = S * float(np.mean(t_part))
+    tc = sum(float(np.mean(t_conv[geom])) for _, _, geom in sets)
+    total = tp + tc
+    return {"value": n / total, "unit": UNIT, "cores": 1, "host_nproc": os.cpu_count(), "kind": "oracle",
+            "steps_sampled": nrun, "est_s_per_step": total,
+            "sample": f"{nrun} sampled step(s) of {workload} ({n} particles, {S} mass sets): each the "
+                      f"per-particle work of a step on 1/{S} of the particles plus one mass set's doubled-grid "
+                      f"convolution; full step estimated at {total:.1f} s = {tp:.1f} s particle work + "
+                      f"{tc:.1f} s convolutions; single-threaded numpy FP64 on one of the host's "
+                      f"{os.cpu_count()} cores (H-hat tables built before timing)"}
 
 
 def run_reference(args):
@@ -510,11 +624,14 @@ def run_reference(args):
     if rank != 0:
         return
     w = getattr(W, args.workload)()
-    cb = oracle_rate(w, args.workload, budget_s=90.0, max_steps=max(1, args.steps), warmup=min(args.warmup, 1))
+    cb = oracle_sampled_rate(w, args.workload, max(1, args.steps))
     line = {"metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic (seeded disc-bulge-halo galaxy)", "impl": "reference",
-            "config": {"workload": WORKLOAD_DESC[args.workload]},
+            "config": bench_config(w, args.workload, len(w["m"]), world),
+            "note": "the oracle needs no warm-up (no compilation, no caches beyond the H-hat tables, which "
+                    "are built before timing); each timed step is a bounded sample of a full step (see "
+                    "cpu_baseline.sample)",
             "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -528,6 +645,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOAD_DESC))
+    ap.add_argument("--extra-workloads", default=",".join(EXTRA_WORKLOADS),
+                    help="comma-separated workloads also measured (rank 0, N = 1), reported in extra_workloads")
     ap.add_argument("--fp64-steps", type=int, default=5,
                     help="steps timed on the FP64 instantiation for comparison (0: skip)")
     ap.add_argument("--sort-every", type=int, default=10,
