@@ -211,7 +211,10 @@ class Clocks:
 def phase_bytes(w, n, esz):
     """Algorithmic HBM bytes per step of each phase (byte model): spectra are
     complex of 2*esz bytes; per mass set A = nx ny nz, S1 = (nx+1) ny nz,
-    S2 = (nx+1) 2ny nz; H-hat read once per geometry launch."""
+    S2 = (nx+1) 2ny nz; H-hat read once per geometry launch.  Grid 1 (the
+    fine grid, solved for its difference fields) adds a second z pass that
+    reads the spectrum again and writes a second one, a second y inverse,
+    and x inverse passes that write four real fields (fx, fy, fz, Phi_1)."""
     cz = 2 * esz
     b = dict.fromkeys(PHASES, 0.0)
     geoms = {}
@@ -229,11 +232,12 @@ def phase_bytes(w, n, esz):
             S1 = (nx + 1) * ny * nz
             S2 = 2 * S1
             A_total += A * count
+            diff = key == "fine"
             b["fft_x_fwd"] += count * (8 * A + cz * S1)
             b["fft_y_fwd"] += count * (cz * S1 + cz * S2)
-            b["fft_z_conv"] += count * (2 * cz * S2)
-            b["fft_y_inv"] += count * (cz * S2 + cz * S1)
-            b["fft_x_inv"] += count * (cz * S1 + esz * A)
+            b["fft_z_conv"] += count * (2 * cz * S2) * (2 if diff else 1)
+            b["fft_y_inv"] += count * (cz * S2 + cz * S1) * (2 if diff else 1)
+            b["fft_x_inv"] += count * (cz * S1 * (2 if diff else 1) + esz * A * (4 if diff else 1))
     for nx, ny, nz in geoms.values():
         b["fft_z_conv"] += esz * (nx + 1) * (ny + 1) * (nz + 1)
     b["recentre"] = n * (4 * esz + 8)
@@ -268,9 +272,11 @@ def fft_pairs(w):
 
 def launches(w, steps, sort_every):
     """Kernels of `steps` graph steps: recentre and its centre update, deposit,
-    five FFT passes per pair of mass sets, force/kick-drift; every
+    five FFT passes per pair of mass sets (eight for a fine grid: its z, y
+    inverse and x inverse passes run twice), force/kick-drift; every
     sort_every-th step adds the six kernels of the spatial sort."""
-    per_step = 2 + 1 + 5 * fft_pairs(w) + 1
+    fine = sum(1 for g in w["galaxies"] if g.get("medium") and g.get("fine"))
+    per_step = 2 + 1 + 5 * fft_pairs(w) + 3 * fine + 1
     sorts = (steps + sort_every - 1) // sort_every if sort_every > 0 else 0
     return per_step * steps + 6 * sorts
 

@@ -125,6 +125,29 @@ int pm_set_stream(pm_ctx *ctx, void *stream);
  * accumulation, order independent). */
 int pm_recentre(pm_ctx *ctx, const pm_particles *p);
 
+/* Step a1 split for a step whose particles are sharded across processes
+ * (one GPU each): pm_recentre_sums adds the exact integer centre-of-mass
+ * sums of this process's particles into the context's accumulators (the
+ * csum buffer of pm_exchange_buffers); after the caller has summed that
+ * buffer across processes (integer sums: exact, order independent),
+ * pm_recentre_apply moves the centres from the summed accumulators and
+ * zeroes them.  pm_recentre is both in one call. */
+int pm_recentre_sums(pm_ctx *ctx, const pm_particles *p);
+int pm_recentre_apply(pm_ctx *ctx);
+
+/* Device buffers that a sharded step sums across processes (Sec. 2.1
+ * grids; Sec. 2.2.3 parallelises the paper's own solver): rho = every mass
+ * set's int64 density, one contiguous block of *rho_bytes bytes, filled by
+ * pm_deposit with this process's particles; csum = the centre-of-mass
+ * accumulators (int64, *csum_bytes bytes).  Element-wise int64 sums of
+ * these buffers over the processes give exactly the single-process
+ * densities and centres.  The pointers belong to the context. */
+int pm_exchange_buffers(pm_ctx *ctx, void **rho, int64_t *rho_bytes, void **csum, int64_t *csum_bytes);
+
+/* Steps a8-a9 with the potentials of the last pm_solve (Sec. 2.1 leap-frog):
+ * v += dt a(x); x += dt v, for this process's particles. */
+int pm_kick_drift(pm_ctx *ctx, const pm_particles *p, double dt);
+
 /* Steps a2-a3 (Eq. eqn:cell, Sec. 2.1 grids 1-5, Sec. 2.2.1 individual
  * masses): classify every particle, set lost flags, and add its fixed-point
  * mass to the int64 density of each grid it belongs to.  Densities are

@@ -46,7 +46,8 @@ from .pm_oracle import (FLAG_LOST, REGION_CORE, REGION_OUTER, REGION_SHELL, Stat
                         combination, grid_cells, kick, drift, mass_sets, potential_fft, region)
 
 __all__ = ["cic_cells", "cic_weights", "cic_deposit", "cic_solve", "grid_accel", "cic_interp",
-           "cic_accelerations", "cic_step", "cic_vjp", "cic_half_kick_start"]
+           "cic_accelerations", "cic_step", "cic_vjp", "cic_half_kick_start", "cic_trajectory",
+           "cic_trajectory_vjp"]
 
 
 def cic_cells(pos, centre, g, split=False):
@@ -251,3 +252,65 @@ def cic_vjp(state: State, system: System, phi, flags, own, u):
                 gx[:, sel] += state.m[sel] * dW / _lengths(geom)[:, None] * lc
                 gm[sel] += W * lc
     return gx, gm
+
+
+def _cic_fields(state: State, system: System):
+    flags, own = classify(state, system)
+    rho, flags = cic_deposit(state, system, flags, own)
+    phi = cic_solve(rho, system)
+    return phi, flags, own
+
+
+def cic_trajectory(state: State, system: System, dt: float, steps: int):
+    """The differentiable run's map with positions and velocities
+    synchronised at t = 0 and t = T = steps dt (grid centres fixed):
+        V = v0 - dt/2 a(x0);  V += dt a(x_t), x_{t+1} = x_t + dt V  (t < steps);
+        v_T = V + dt/2 a(x_T),
+    a the CIC acceleration.  Returns (x_T, v_T, tape) with tape[t] =
+    (State at x_t, phi, flags, own) for cic_trajectory_vjp."""
+    st = state.copy()
+    tape = []
+    phi, flags, own = _cic_fields(st, system)
+    live = (flags & FLAG_LOST) == 0
+    V = kick(st.vel, cic_accelerations(st, system, phi, flags), -0.5 * dt, live)
+    for t in range(steps + 1):
+        if t > 0:
+            phi, flags, own = _cic_fields(st, system)
+        st.flags = flags
+        tape.append((st.copy(), phi, flags, own))
+        live = (flags & FLAG_LOST) == 0
+        acc = cic_accelerations(st, system, phi, flags)
+        if t == steps:
+            return st.pos.copy(), kick(V, acc, 0.5 * dt, live), tape
+        V = kick(V, acc, dt, live)
+        st.vel = V
+        st.pos = drift(st.pos, V, dt, live)
+
+
+def cic_trajectory_vjp(tape, system: System, dt: float, lx, lv):
+    """Cotangents (of x0, v0, m) of the map of cic_trajectory for cotangents
+    (lx, lv) of (x_T, v_T): its transpose, newest step first,
+        lV = lv;  lx += J_x(x_T)^T (dt/2 lv);  lm += J_m(x_T)^T (dt/2 lv);
+        per step t = T-1 .. 0:  mu = lV + dt lx;  lx += J_x(x_t)^T (dt mu);
+                                lm += J_m(x_t)^T (dt mu);  lV = mu;
+        v0: lV;  lx += J_x(x_0)^T (-dt/2 lV);  lm += J_m(x_0)^T (-dt/2 lV),
+    with J^T u = cic_vjp at the stored x_t (each the chain rule of one
+    leap-frog step V' = V + dt a(x), x' = x + dt V')."""
+    steps = len(tape) - 1
+    lx = np.array(lx, dtype=np.float64, copy=True)
+    lV = np.array(lv, dtype=np.float64, copy=True)
+    lm = np.zeros(lx.shape[1])
+
+    def add(t, u):
+        st, phi, flags, own = tape[t]
+        gx, gm = cic_vjp(st, system, phi, flags, own, u)
+        lx[...] += gx
+        lm[...] += gm
+
+    add(steps, 0.5 * dt * lV)
+    for t in range(steps - 1, -1, -1):
+        mu = lV + dt * lx
+        add(t, dt * mu)
+        lV = mu
+    add(0, -0.5 * dt * lV)
+    return lx, lV, lm

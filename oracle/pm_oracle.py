@@ -55,10 +55,10 @@ __all__ = [
     "quantize_mass", "offset_f32", "cell_index", "in_box", "region",
     "classify", "deposit", "green_doubled", "green_hat", "potential_fft",
     "potential_direct", "accel_from_grid", "phi_at_particle",
-    "accelerations", "kick", "drift", "recentre", "step", "diagnostics",
+    "accelerations", "kick", "drift", "recentre", "recentre_sums", "recentre_apply", "step", "diagnostics",
     "State", "solve_all", "rho_real", "mass_sets", "combination", "lost_mask",
     "grid_cells", "r2_f32", "half_kick_start", "potential_at", "REGION_CORE", "REGION_SHELL",
-    "REGION_OUTER", "FLAG_LOST",
+    "REGION_OUTER", "FLAG_LOST", "set_fft_workers",
 ]
 
 REGION_CORE, REGION_SHELL, REGION_OUTER = 0, 1, 2
@@ -319,10 +319,36 @@ def green_doubled(g: Geometry, h000: float) -> np.ndarray:
     return H
 
 
+_FFT_WORKERS = None
+
+
+def set_fft_workers(n):
+    """Threads of the library FFT behind potential_fft and green_hat: None
+    (the default) uses numpy's single-threaded FFT, n > 1 scipy.fft with n
+    threads (the same pocketfft algorithm; results agree to rounding).  The
+    arithmetic of the method is unchanged; large test workloads use it."""
+    global _FFT_WORKERS
+    _FFT_WORKERS = n if (n is not None and n > 1) else None
+
+
+def _rfftn(x):
+    if _FFT_WORKERS is None:
+        return np.fft.rfftn(x)
+    import scipy.fft
+    return scipy.fft.rfftn(x, workers=_FFT_WORKERS)
+
+
+def _irfftn(x, shape):
+    if _FFT_WORKERS is None:
+        return np.fft.irfftn(x, s=shape, axes=(0, 1, 2))
+    import scipy.fft
+    return scipy.fft.irfftn(x, s=shape, axes=(0, 1, 2), workers=_FFT_WORKERS)
+
+
 @lru_cache(maxsize=16)
 def green_hat(g: Geometry, h000: float) -> np.ndarray:
     """DFT of the doubled H (real-input half spectrum)."""
-    return np.fft.rfftn(green_doubled(g, h000))
+    return _rfftn(green_doubled(g, h000))
 
 
 def rho_real(rho_int: np.ndarray, s: int) -> np.ndarray:
@@ -338,7 +364,7 @@ def potential_fft(rho: np.ndarray, g: Geometry, G: float, h000: float) -> np.nda
     (Eastwood & Brownrigg 1979).  `rho` is mass per cell (float64)."""
     pad = np.zeros((2 * g.nz, 2 * g.ny, 2 * g.nx))
     pad[: g.nz, : g.ny, : g.nx] = rho
-    conv = np.fft.irfftn(np.fft.rfftn(pad) * green_hat(g, h000), s=pad.shape, axes=(0, 1, 2))
+    conv = _irfftn(_rfftn(pad) * green_hat(g, h000), pad.shape)
     return (G / g.l_xy) * conv[: g.nz, : g.ny, : g.nx]
 
 
@@ -482,32 +508,60 @@ def drift(pos, vel, dt, live):
     return np.where(live, pos + dt * vel, pos)
 
 
-def recentre(state: State, system: System) -> np.ndarray:
-    """New centres of grids 1-3: centre of mass of each recentred galaxy's live
-    particles within R_core of its current centre.  Offsets and masses are
-    taken to integers (offset * 2^sD with |offset| < R_core <= 2^(24 - sD);
-    mass q >> 26 of the deposit's fixed point) so the sums are exact."""
+def recentre_sums(state: State, system: System) -> np.ndarray:
+    """Integer sums of the centre of mass of each recentred galaxy's live
+    particles within R_core of its current centre: per galaxy
+    (sum w, sum w D_x, sum w D_y, sum w D_z) with weights w = q >> 26 (q the
+    deposit's fixed-point mass) and offsets D = rint(d 2^sD), |d| < R_core <=
+    2^(24 - sD).  Integer sums do not depend on order, so the sums of
+    disjoint parts of the particles add up to the sums of all of them.
+    Returns an int64 array (ngal, 4); zeros for galaxies not recentred."""
     s = fixed_shift(system.mass_bound)
     q = quantize_mass(state.m, s) >> 26
-    new = state.centres.copy()
+    out = np.zeros((len(system.galaxies), 4), dtype=np.int64)
     live = (state.flags & FLAG_LOST) == 0
     for g, gal in enumerate(system.galaxies):
         if not gal.recentre or gal.r_core <= 0:
             continue
-        f, e = math.frexp(gal.r_core)
-        sD = 24 - (e - 1 if f == 0.5 else e)
+        sD = _offset_shift(gal.r_core)
         sel = live & (state.gal == g)
         d = [offset_f32(state.pos[k, sel], state.centres[g, k], system.split) for k in range(3)]
         inside = r2_f32(*d) < np.float32(gal.r_core * gal.r_core)
         w = q[sel][inside]
-        M = int(w.sum())
-        if M <= 0:
-            continue
+        out[g, 0] = int(w.sum())
         for k in range(3):
             D = np.rint(np.ldexp(d[k][inside].astype(np.float64), sD)).astype(np.int64)
-            MD = int((w * D).sum())
-            new[g, k] = state.centres[g, k] + math.ldexp(float(MD) / float(M), -sD)
+            out[g, 1 + k] = int((w * D).sum())
+    return out
+
+
+def _offset_shift(r_core: float) -> int:
+    """sD = 24 - ceil(log2 R_core): offsets below R_core times 2^sD stay
+    below 2^24."""
+    f, e = math.frexp(r_core)
+    return 24 - (e - 1 if f == 0.5 else e)
+
+
+def recentre_apply(centres: np.ndarray, sums: np.ndarray, system: System) -> np.ndarray:
+    """New centres c + (sum w D / sum w) 2^-sD for every galaxy whose summed
+    weight is positive; the others keep theirs."""
+    new = np.array(centres, dtype=np.float64, copy=True)
+    for g, gal in enumerate(system.galaxies):
+        M = int(sums[g, 0])
+        if not gal.recentre or gal.r_core <= 0 or M <= 0:
+            continue
+        sD = _offset_shift(gal.r_core)
+        for k in range(3):
+            new[g, k] = centres[g, k] + math.ldexp(float(int(sums[g, 1 + k])) / float(M), -sD)
     return new
+
+
+def recentre(state: State, system: System) -> np.ndarray:
+    """New centres of grids 1-3 (Sec. 2.1, the centre of mass as the stated
+    alternative to the density maximum): centre of mass of each recentred
+    galaxy's live particles within R_core of its current centre, from the
+    exact integer sums of recentre_sums."""
+    return recentre_apply(state.centres, recentre_sums(state, system), system)
 
 
 def step(state: State, system: System, dt: float) -> State:

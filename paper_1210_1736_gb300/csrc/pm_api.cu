@@ -122,10 +122,15 @@ constexpr int GRAPH_SETS = 4;
 
 // Two mass sets of one geometry transformed together as rho_a + i rho_b
 // (b < 0: no partner), with their work array and tensor maps.
+// A grid without partner (grid 1) is solved for its forward-difference
+// fields instead (diff): the z pass runs twice, writing H-hat (D_x + i D_y)
+// rho-hat into a second work array and H-hat (D_z + i) rho-hat in place, so
+// that the inverse passes give fx + i fy and fz + i Phi.
 struct Pair {
     int gi, a, b;
-    void *work = nullptr;
-    CUtensorMap yfwd, yinv, zmap;
+    bool diff = false;
+    void *work = nullptr, *work2 = nullptr;
+    CUtensorMap yfwd, yinv, zmap, yinv2, zmap2;
 };
 
 struct GeoBuf {
@@ -149,6 +154,7 @@ struct pm_ctx {
     int set_geo[PM_MAX_GALAXIES][PM_SETS];
     long long *rho[PM_MAX_GALAXIES][PM_SETS];
     void *phi[PM_MAX_GALAXIES][PM_SETS];
+    void *fd[PM_MAX_GALAXIES][3];   // forward differences of Phi_1: fx, fy, fz (grid 1)
     long long *rho_all = nullptr;
     size_t rho_bytes = 0;
     SysK hs;
@@ -159,6 +165,7 @@ struct pm_ctx {
     double *d_diag = nullptr;
     unsigned long long *d_cnt = nullptr;
     void *d_tw[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    void *d_dt[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};   // exp(2 pi i k / L) - 1
     cudaStream_t user = nullptr;
     cudaStream_t cap = nullptr;
     std::vector<cudaStream_t> branch;   // solve branch streams
@@ -285,6 +292,16 @@ template <typename T> int upload_twiddles(pm_ctx *c) {
         PM_TRY(dev_alloc(c, &c->d_tw[i], L * sizeof(C)));
         PM_CK(cudaMemcpyAsync(c->d_tw[i], tw.data(), L * sizeof(C), cudaMemcpyHostToDevice, c->user));
         PM_CK(cudaStreamSynchronize(c->user));
+        // D(k) = exp(2 pi i k / L) - 1 = -2 sin^2(pi k / L) + i sin(2 pi k / L)
+        // (the half-angle form keeps the real part accurate for small k)
+        for (int m = 0; m < L; ++m) {
+            const double h = std::sin(M_PI * (double)m / (double)L);
+            tw[m].x = (T)(-2.0 * h * h);
+            tw[m].y = (T)std::sin(2.0 * M_PI * (double)m / (double)L);
+        }
+        PM_TRY(dev_alloc(c, &c->d_dt[i], L * sizeof(C)));
+        PM_CK(cudaMemcpyAsync(c->d_dt[i], tw.data(), L * sizeof(C), cudaMemcpyHostToDevice, c->user));
+        PM_CK(cudaStreamSynchronize(c->user));
     }
     return PM_OK;
 }
@@ -311,7 +328,40 @@ template <typename T> int launch_pass(pm_ctx *c, int pass, cudaStream_t st, int 
             a.nx = g.nx; a.ny = g.ny; a.nz = g.nz;
             a.scale = std::ldexp(1.0, -(shift == INT_MIN ? c->shift : shift));
             a.err = c->d_err;
+            a.dtx = c->d_dt[tw_index(2 * g.nx)];
+            a.dty = c->d_dt[tw_index(2 * g.ny)];
+            a.dtz = c->d_dt[tw_index(2 * g.nz)];
             cudaError_t e;
+            if (pr.diff && pass >= PASS_ZCONV) {
+                // difference fields: fx + i fy through work2, fz + i Phi_1 in place
+                if (pass == PASS_ZCONV) {
+                    a.tw = c->d_tw[tw_index(2 * g.nz)];
+                    a.dmode = 1;
+                    e = pm_launch_zconv<T>(a, pr.zmap, pr.zmap2, st);
+                    if (e == cudaSuccess) {
+                        a.dmode = 2;
+                        e = pm_launch_zconv<T>(a, pr.zmap, pr.zmap, st);
+                    }
+                } else if (pass == PASS_YINV) {
+                    a.tw = c->d_tw[tw_index(2 * g.ny)];
+                    e = pm_launch_col<T>(a, pr.yinv, COL_YINV, st);
+                    a.work = pr.work2;
+                    if (e == cudaSuccess) e = pm_launch_col<T>(a, pr.yinv2, COL_YINV, st);
+                } else {
+                    a.tw = c->d_tw[tw_index(2 * g.nx)];
+                    a.split = 1;
+                    a.phi_sum = c->fd[pr.gi][2];
+                    a.phi_b = c->phi[pr.gi][pr.a];
+                    e = pm_launch_xinv<T>(a, st);
+                    a.work = pr.work2;
+                    a.phi_sum = c->fd[pr.gi][0];
+                    a.phi_b = c->fd[pr.gi][1];
+                    if (e == cudaSuccess) e = pm_launch_xinv<T>(a, st);
+                }
+                if (e != cudaSuccess)
+                    return fail(PM_E_CUDA, "FFT pass %d launch failed: %s", pass, cudaGetErrorString(e));
+                continue;
+            }
             switch (pass) {
                 case PASS_XFWD:
                     a.tw = c->d_tw[tw_index(2 * g.nx)];
@@ -439,9 +489,11 @@ template <typename T> int enqueue_deposit(pm_ctx *c, const pm_particles *p, cuda
     return PM_OK;
 }
 
-template <typename T> int enqueue_recentre(pm_ctx *c, const pm_particles *p, cudaStream_t st) {
+// phase: 3 = sums and apply, 1 = sums only, 2 = apply only (a sharded step
+// sums each rank's particles, adds the accumulators across ranks, applies).
+template <typename T> int enqueue_recentre(pm_ctx *c, const pm_particles *p, cudaStream_t st, int phase = 3) {
     if (!c->any_recentre) return PM_OK;
-    PM_CK(pm_launch_recentre<T>(part_k<T>(p), c->hs, c->d_cen, c->d_csum, st));
+    PM_CK(pm_launch_recentre<T>(part_k<T>(p), c->hs, c->d_cen, c->d_csum, phase, st));
     return PM_OK;
 }
 
@@ -897,6 +949,7 @@ int pm_create_grids(const pm_system *sys, const pm_galaxy *gals, void *stream, p
     std::memset(c->set_geo, -1, sizeof(c->set_geo));
     std::memset(c->rho, 0, sizeof(c->rho));
     std::memset(c->phi, 0, sizeof(c->phi));
+    std::memset(c->fd, 0, sizeof(c->fd));
 
     auto cleanup = [&](int rc) { pm_destroy(c); return rc; };
     if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess)
@@ -957,7 +1010,10 @@ int pm_create_grids(const pm_system *sys, const pm_galaxy *gals, void *stream, p
             pr.gi = gi; pr.a = a; pr.b = b;
             gb.pairs.push_back(pr);
         };
-        if (c->set_geo[gi][0] >= 0) add_pair(0, -1);
+        if (c->set_geo[gi][0] >= 0) {
+            add_pair(0, -1);
+            c->geos[c->set_geo[gi][0]].pairs.back().diff = true;
+        }
         if (c->set_geo[gi][1] >= 0) add_pair(1, 2);
         if (c->set_geo[gi][3] >= 0) add_pair(3, 4);
         else add_pair(4, -1);
@@ -971,6 +1027,16 @@ int pm_create_grids(const pm_system *sys, const pm_galaxy *gals, void *stream, p
             if ((rc = pm_encode_col_maps(pr.work, gb.g.nx, gb.g.ny, gb.g.nz, (int)c->esz, &pr.yfwd, &pr.yinv,
                                          &pr.zmap)))
                 return cleanup(rc);
+            if (!pr.diff) continue;
+            CUtensorMap unused;
+            if ((rc = dev_alloc(c, &pr.work2, bytes))) return cleanup(rc);
+            if (cudaMemsetAsync(pr.work2, 0, bytes, c->user) != cudaSuccess)
+                return cleanup(fail(PM_E_CUDA, "memset failed"));
+            if ((rc = pm_encode_col_maps(pr.work2, gb.g.nx, gb.g.ny, gb.g.nz, (int)c->esz, &unused, &pr.yinv2,
+                                         &pr.zmap2)))
+                return cleanup(rc);
+            for (int k = 0; k < 3; ++k)
+                if ((rc = dev_alloc(c, &c->fd[pr.gi][k], gb.A * c->esz))) return cleanup(rc);
         }
     if (cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess)
         return cleanup(fail(PM_E_CUDA, "cudaEventCreate failed"));
@@ -1015,6 +1081,9 @@ int pm_create_grids(const pm_system *sys, const pm_galaxy *gals, void *stream, p
         K.sD = G.r_core > 0 ? 24 - ceil_log2(G.r_core) : 0;
         for (int k = 0; k < PM_SETS; ++k) K.rho[k] = (unsigned long long *)c->rho[gi][k];
         K.phi_fine = c->phi[gi][0];
+        K.fd_x = c->fd[gi][0];
+        K.fd_y = c->fd[gi][1];
+        K.fd_z = c->fd[gi][2];
         K.phi_m23 = c->phi[gi][1];
         K.phi_m3 = c->phi[gi][2];
         K.phi_call = geom_present(G.medium) ? c->phi[gi][3] : c->phi[gi][4];
@@ -1088,6 +1157,35 @@ int pm_recentre(pm_ctx *c, const pm_particles *p) {
     if (!c) return fail(PM_E_ARG, "ctx is NULL");
     PM_TRY(check_particles(p));
     return PM_DISPATCH(c, enqueue_recentre, c, p, c->user);
+}
+
+int pm_recentre_sums(pm_ctx *c, const pm_particles *p) {
+    if (!c) return fail(PM_E_ARG, "ctx is NULL");
+    PM_TRY(check_particles(p));
+    return PM_DISPATCH(c, enqueue_recentre, c, p, c->user, 1);
+}
+
+int pm_recentre_apply(pm_ctx *c) {
+    if (!c) return fail(PM_E_ARG, "ctx is NULL");
+    pm_particles none;
+    std::memset(&none, 0, sizeof(none));
+    return PM_DISPATCH(c, enqueue_recentre, c, &none, c->user, 2);
+}
+
+int pm_exchange_buffers(pm_ctx *c, void **rho, int64_t *rho_bytes, void **csum, int64_t *csum_bytes) {
+    if (!c || !rho || !rho_bytes || !csum || !csum_bytes) return fail(PM_E_ARG, "ctx or an output is NULL");
+    *rho = c->rho_all;
+    *rho_bytes = (int64_t)c->rho_bytes;
+    *csum = c->d_csum;
+    *csum_bytes = (int64_t)(sizeof(long long) * 4 * PM_MAX_GALAXIES * 64);
+    return PM_OK;
+}
+
+int pm_kick_drift(pm_ctx *c, const pm_particles *p, double dt) {
+    if (!c) return fail(PM_E_ARG, "ctx is NULL");
+    PM_TRY(check_particles(p));
+    if (!std::isfinite(dt)) return fail(PM_E_ARG, "dt not finite");
+    return PM_DISPATCH(c, force_impl, c, 0, p, dt, nullptr, nullptr, nullptr, nullptr);
 }
 
 int pm_deposit(pm_ctx *c, const pm_particles *p) {

@@ -46,6 +46,9 @@ struct GalK {
     const void *phi_m23;    // Phi_2 + Phi_3
     const void *phi_c5;     // Phi_5
     const void *phi_call;   // Phi_4 + Phi_5 (Phi_5 when there is no medium grid)
+    // forward differences of Phi_1 (fx[i] = Phi_1[i+1] - Phi_1[i], likewise
+    // fy, fz), from which the fine-grid force is built (null: use Phi_1)
+    const void *fd_x, *fd_y, *fd_z;
 };
 
 struct SysK {

@@ -141,6 +141,46 @@ __device__ __forceinline__ void stencil(const GeomK &g, const T *__restrict__ P1
     if (phi) *phi += p0 + gx * dx + gy * dy + gz * dz;
 }
 
+// Eq. (eqn:diff) on grid 1 from the forward differences of Phi_1,
+// fx[i] = Phi[i+1] - Phi[i] (and fy, fz), which the convolution returns
+// directly; their FP32 rounding is relative to the differences, not to Phi.
+// With f(di, dj, dk) = f at the cell (i+di, j+dj, k+dk):
+//   Phi(1) - Phi(-1)          = fx(0) + fx(-1)
+//   Phi(1) + Phi(-1) - 2Phi(0) = fx(0) - fx(-1)
+//   Phi(1,1) - Phi(-1,1) + Phi(-1,-1) - Phi(1,-1)
+//                             = fx(0,1) + fx(-1,1) - fx(0,-1) - fx(-1,-1)
+// and likewise for the other mixed terms and components (each component's
+// terms from its own difference field).
+template <typename T>
+__device__ __forceinline__ void stencil_diff(const GeomK &g, const T *__restrict__ FX, const T *__restrict__ FY,
+                                             const T *__restrict__ FZ, const Cell &cl, T dx, T dy, T dz, T *acc) {
+    const int sy = g.nx, sz = g.nx * g.ny;
+    const size_t base = cell_off(g, cl);
+    const T *bx = FX + base, *by = FY + base, *bz = FZ + base;
+    auto o = [&](int di, int dj, int dk) { return di + dj * sy + dk * sz; };
+    const T cg = pick<T>(g.c_gx, g.fc_gx), cgz = pick<T>(g.c_gz, g.fc_gz);
+    const T chx = pick<T>(g.c_hxx, g.fc_hxx), chz = pick<T>(g.c_hzz, g.fc_hzz);
+    const T cmxy = pick<T>(g.c_mxy, g.fc_mxy), cmxz = pick<T>(g.c_mxz, g.fc_mxz);
+    const T x0 = __ldg(bx), xm = __ldg(bx + o(-1, 0, 0));
+    const T xyp = __ldg(bx + o(0, 1, 0)) + __ldg(bx + o(-1, 1, 0));
+    const T xym = __ldg(bx + o(0, -1, 0)) + __ldg(bx + o(-1, -1, 0));
+    const T xzp = __ldg(bx + o(0, 0, 1)) + __ldg(bx + o(-1, 0, 1));
+    const T xzm = __ldg(bx + o(0, 0, -1)) + __ldg(bx + o(-1, 0, -1));
+    const T y0 = __ldg(by), ym = __ldg(by + o(0, -1, 0));
+    const T yxp = __ldg(by + o(1, 0, 0)) + __ldg(by + o(1, -1, 0));
+    const T yxm = __ldg(by + o(-1, 0, 0)) + __ldg(by + o(-1, -1, 0));
+    const T yzp = __ldg(by + o(0, 0, 1)) + __ldg(by + o(0, -1, 1));
+    const T yzm = __ldg(by + o(0, 0, -1)) + __ldg(by + o(0, -1, -1));
+    const T z0 = __ldg(bz), zm = __ldg(bz + o(0, 0, -1));
+    const T zxp = __ldg(bz + o(1, 0, 0)) + __ldg(bz + o(1, 0, -1));
+    const T zxm = __ldg(bz + o(-1, 0, 0)) + __ldg(bz + o(-1, 0, -1));
+    const T zyp = __ldg(bz + o(0, 1, 0)) + __ldg(bz + o(0, 1, -1));
+    const T zym = __ldg(bz + o(0, -1, 0)) + __ldg(bz + o(0, -1, -1));
+    acc[0] += (x0 + xm) * cg + (x0 - xm) * chx * dx + (xyp - xym) * cmxy * dy + (xzp - xzm) * cmxz * dz;
+    acc[1] += (y0 + ym) * cg + (y0 - ym) * chx * dy + (yxp - yxm) * cmxy * dx + (yzp - yzm) * cmxz * dz;
+    acc[2] += (z0 + zm) * cgz + (z0 - zm) * chz * dz + (zxp - zxm) * cmxz * dx + (zyp - zym) * cmxz * dy;
+}
+
 // ---------------------------------------------------------------------------
 // Step a1 (recentring).  The centre of mass of each recentring galaxy's live
 // particles within R_core of its centre c is accumulated exactly in integers:
@@ -366,7 +406,12 @@ __global__ void __launch_bounds__(256, (MODE == 0 && sizeof(T) == 4) ? 4 : 3)
                                    cm, dx, dy, dz, acc, php);
                         if (reg == REG_CORE) {
                             cell_delta(G.fine, cf, rx, ry, rz, dx, dy, dz);
-                            stencil<T>(G.fine, static_cast<const T *>(G.phi_fine), nullptr, cf, dx, dy, dz, acc, php);
+                            if (MODE != 3 && G.fd_x)   // forces from the difference fields
+                                stencil_diff<T>(G.fine, static_cast<const T *>(G.fd_x), static_cast<const T *>(G.fd_y),
+                                                static_cast<const T *>(G.fd_z), cf, dx, dy, dz, acc);
+                            else
+                                stencil<T>(G.fine, static_cast<const T *>(G.phi_fine), nullptr, cf, dx, dy, dz, acc,
+                                           php);
                         }
                     }
                 }
@@ -630,11 +675,11 @@ template <typename T, int L, int MODE> int col_blocks_per_sm() {
     return cached;
 }
 
-template <typename T, int L> int colw_blocks_per_sm() {
+template <typename T, int L, int DM> int colw_blocks_per_sm() {
     static int cached = 0;
     if (!cached) {
         int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pmk::k_colw<T, L>, pmk::WShape<T, L>::THREADS,
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pmk::k_colw<T, L, DM>, pmk::WShape<T, L>::THREADS,
                                                           pmk::colw_smem<T, L>()) != cudaSuccess || nb < 1)
             nb = 1;
         cached = nb;
@@ -657,7 +702,10 @@ template <typename T, int L> cudaError_t attrs_L() {
     e = cudaFuncSetAttribute(pmk::k_col<T, L, COL_YFWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)pmk::col_smem<T, L, COL_YFWD>());
     if (e) return e;
-    e = cudaFuncSetAttribute(pmk::k_colw<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(pmk::k_colw<T, L, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)pmk::colw_smem<T, L>());
+    if (e) return e;
+    e = cudaFuncSetAttribute(pmk::k_colw<T, L, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)pmk::colw_smem<T, L>());
     if (e) return e;
     e = cudaFuncSetAttribute(pmk::k_col<T, L, COL_YINV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -716,17 +764,23 @@ template <typename T, int L, int MODE> cudaError_t col_LM(const PairArgs &a, con
     return launch_pdl(pmk::k_col<T, L, MODE>, (unsigned)grid, pmk::CShape<T, L>::THREADS,
                       pmk::col_smem<T, L, MODE>(), st, a, map, ntiles);
 }
-template <typename T, int L> cudaError_t zconv_L(const PairArgs &a, const CUtensorMap &map, cudaStream_t st) {
+template <typename T, int L>
+cudaError_t zconv_L(const PairArgs &a, const CUtensorMap &lmap, const CUtensorMap &smap, cudaStream_t st) {
     typedef pmk::WShape<T, L> S;
     const long long ntiles = ((long long)4 * a.ny * a.nx) / S::COLS;   // COLS divides the 2ny x 2nx columns
-    long long grid = (long long)colw_blocks_per_sm<T, L>() * num_sms();
+    const bool dm = a.dmode != 0;
+    long long grid = (long long)(dm ? colw_blocks_per_sm<T, L, 1>() : colw_blocks_per_sm<T, L, 0>()) * num_sms();
     if (grid > ntiles) grid = ntiles;
     if (grid < 1) grid = 1;
-    return launch_pdl(pmk::k_colw<T, L>, (unsigned)grid, S::THREADS, pmk::colw_smem<T, L>(), st, a, map, ntiles);
+    if (dm)
+        return launch_pdl(pmk::k_colw<T, L, 1>, (unsigned)grid, S::THREADS, pmk::colw_smem<T, L>(), st, a, lmap, smap,
+                          ntiles);
+    return launch_pdl(pmk::k_colw<T, L, 0>, (unsigned)grid, S::THREADS, pmk::colw_smem<T, L>(), st, a, lmap, smap,
+                      ntiles);
 }
 template <typename T, int L> cudaError_t col_L(const PairArgs &a, const CUtensorMap &map, int mode, cudaStream_t st) {
     if (mode == COL_YFWD) return col_LM<T, L, COL_YFWD>(a, map, st);
-    if (mode == COL_ZCONV) return zconv_L<T, L>(a, map, st);
+    if (mode == COL_ZCONV) return zconv_L<T, L>(a, map, map, st);
     return col_LM<T, L, COL_YINV>(a, map, st);
 }
 
@@ -771,6 +825,13 @@ template <typename T> cudaError_t pm_launch_col(const PairArgs &a, const CUtenso
 }
 
 template <typename T>
+cudaError_t pm_launch_zconv(const PairArgs &a, const CUtensorMap &lmap, const CUtensorMap &smap, cudaStream_t st) {
+#define PM_ZC(LL) pmk_host::zconv_L<T, LL>(a, lmap, smap, st)
+    PM_SWITCH_L(2 * a.nz, PM_ZC)
+#undef PM_ZC
+}
+
+template <typename T>
 cudaError_t pm_launch_deposit(const PartK<T> &p, const SysK &sk, const CenK *cen, int aggregate, cudaStream_t st) {
     if (p.n <= 0) return cudaSuccess;
     pmk::k_deposit<T><<<pmk_host::particle_grid(p.n), 256, 0, st>>>(p, sk, cen, aggregate);
@@ -793,17 +854,19 @@ cudaError_t pm_launch_force(int mode, const PartK<T> &p, const SysK &sk, const C
 }
 
 template <typename T>
-cudaError_t pm_launch_recentre(const PartK<T> &p, const SysK &sk, CenK *cen, long long *part, cudaStream_t st) {
-    if (p.n <= 0) return cudaSuccess;
-    // one full wave of resident blocks (8 per SM in FP32): each thread sums
-    // several particles in registers before the one warp reduction
-    static int bps = 0;
-    if (!bps && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, pmk::k_recentre<T>, 256, 0) != cudaSuccess ||
-                 bps < 1))
-        bps = 1;
-    const int g = std::min(pmk_host::particle_grid(p.n), bps * pmk_host::num_sms());
-    pmk::k_recentre<T><<<g, 256, 0, st>>>(p, sk, cen, part);
-    pmk::k_com_apply<<<1, 256, 0, st>>>(sk, part, cen);
+cudaError_t pm_launch_recentre(const PartK<T> &p, const SysK &sk, CenK *cen, long long *part, int phase,
+                               cudaStream_t st) {
+    if ((phase & 1) && p.n > 0) {
+        // one full wave of resident blocks (8 per SM in FP32): each thread
+        // sums several particles in registers before the one warp reduction
+        static int bps = 0;
+        if (!bps && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, pmk::k_recentre<T>, 256, 0) != cudaSuccess ||
+                     bps < 1))
+            bps = 1;
+        const int g = std::min(pmk_host::particle_grid(p.n), bps * pmk_host::num_sms());
+        pmk::k_recentre<T><<<g, 256, 0, st>>>(p, sk, cen, part);
+    }
+    if (phase & 2) pmk::k_com_apply<<<1, 256, 0, st>>>(sk, part, cen);
     return cudaGetLastError();
 }
 
@@ -848,10 +911,12 @@ cudaError_t pm_store_hhat(const double *oct, T *out, int nx, int ny, int nz, dou
     template cudaError_t pm_launch_xfwd<T>(const PairArgs &, cudaStream_t);                                   \
     template cudaError_t pm_launch_xinv<T>(const PairArgs &, cudaStream_t);                                   \
     template cudaError_t pm_launch_col<T>(const PairArgs &, const CUtensorMap &, int, cudaStream_t);          \
+    template cudaError_t pm_launch_zconv<T>(const PairArgs &, const CUtensorMap &, const CUtensorMap &,       \
+                                            cudaStream_t);                                                     \
     template cudaError_t pm_launch_deposit<T>(const PartK<T> &, const SysK &, const CenK *, int, cudaStream_t); \
     template cudaError_t pm_launch_force<T>(int, const PartK<T> &, const SysK &, const CenK *, double, T *, T *, \
                                             T *, double *, cudaStream_t);                                      \
-    template cudaError_t pm_launch_recentre<T>(const PartK<T> &, const SysK &, CenK *, long long *,            \
+    template cudaError_t pm_launch_recentre<T>(const PartK<T> &, const SysK &, CenK *, long long *, int,       \
                                                cudaStream_t);                                                  \
     template cudaError_t pm_launch_count_lost<T>(const PartK<T> &, unsigned long long *, cudaStream_t);       \
     template cudaError_t pm_launch_sort<T>(const PartK<T> &, const PartK<T> &, const SysK &, const CenK *,     \

@@ -18,6 +18,15 @@ struct PairArgs {
     int nx, ny, nz;
     double scale;                         // 2^-s
     int *err;                             // set to 1 if a tensor copy never completes
+    // Difference fields of an unpaired grid (rho_b null).  D_L(k) =
+    // exp(2 pi i k / L) - 1 multiplies the spectrum of a field f into that of
+    // its forward difference f[n+1] - f[n]; dtx, dty, dtz are tables of D for
+    // the x, y and z lengths.  dmode (z pass): 0 multiplies by H-hat,
+    // 1 by H-hat (D_x + i D_y), 2 by H-hat (D_z + i); the inverse of a real
+    // field's spectrum times such a factor is fx + i fy, or fz + i Phi.
+    const void *dtx, *dty, *dtz;
+    int dmode;
+    int split;                            // x inverse: phi_sum = Re, phi_b = Im (no sum)
 };
 
 enum { COL_YFWD = 0, COL_ZCONV = 1, COL_YINV = 2 };
@@ -48,6 +57,10 @@ template <typename T> cudaError_t pm_launch_xfwd(const PairArgs &a, cudaStream_t
 // Column pass `mode` with its tensor map (y forward: yfwd, z: zmap, y
 // inverse: yinv).
 template <typename T> cudaError_t pm_launch_col(const PairArgs &a, const CUtensorMap &map, int mode, cudaStream_t st);
+// z pass reading tiles through lmap and writing them through smap (maps of
+// two work arrays of the same shape; the same map for an in-place pass).
+template <typename T>
+cudaError_t pm_launch_zconv(const PairArgs &a, const CUtensorMap &lmap, const CUtensorMap &smap, cudaStream_t st);
 template <typename T> cudaError_t pm_launch_xinv(const PairArgs &a, cudaStream_t st);
 
 template <typename T>
@@ -57,8 +70,11 @@ template <typename T>
 cudaError_t pm_launch_force(int mode, const PartK<T> &p, const SysK &sk, const CenK *cen, double dt,
                             T *ax, T *ay, T *az, double *diag, cudaStream_t st);
 // Recentring from the current positions (part: zeroed accumulators).
+// phase bit 0: add the particles' integer centre-of-mass sums into part;
+// bit 1: add part's rows, move the centres and zero part again.
 template <typename T>
-cudaError_t pm_launch_recentre(const PartK<T> &p, const SysK &sk, CenK *cen, long long *part, cudaStream_t st);
+cudaError_t pm_launch_recentre(const PartK<T> &p, const SysK &sk, CenK *cen, long long *part, int phase,
+                               cudaStream_t st);
 template <typename T>
 cudaError_t pm_launch_count_lost(const PartK<T> &p, unsigned long long *out, cudaStream_t st);
 // Counting sort by spatial key; permutes p's arrays in place through scratch.

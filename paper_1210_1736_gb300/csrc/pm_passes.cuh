@@ -112,8 +112,8 @@ __global__ void __launch_bounds__(NT) k_xfwd(PairArgs a) {
 }
 
 // x inverse: inverse FFT of length L = 2nx of each row y < ny; x < nx kept:
-// Phi_b = Im, Phi_sum = Re + Im (or Re without partner).  Persistent as
-// k_xfwd.
+// Phi_b = Im, Phi_sum = Re + Im (or Re without partner; with a.split,
+// Phi_sum = Re and Phi_b = Im).  Persistent as k_xfwd.
 template <typename T, int L>
 __global__ void __launch_bounds__(NT) k_xinv(PairArgs a) {
     typedef typename cplx_t<T>::type C;
@@ -153,7 +153,10 @@ __global__ void __launch_bounds__(NT) k_xinv(PairArgs a) {
                 for (int q = 0; q < RL / 2; ++q) {   // outputs x < nx: registers q < 8 of the radix-16 last stage
                     const int x = pmfft::in_row<L, NS - 1, true>(t, kk, q);
                     const C val = v[kk * RL + q];
-                    if (phi_b) {
+                    if (a.split) {
+                        phi_s[x] = val.x;
+                        phi_b[r * NX + x] = val.y;
+                    } else if (phi_b) {
                         phi_b[r * NX + x] = val.y;
                         phi_s[x] = val.x + val.y;
                     } else {
@@ -443,10 +446,16 @@ __device__ __forceinline__ uint32_t woff(int row, int c) {
     return (uint32_t)(c / S::SW) * (uint32_t)(ROWS * S::P) + sw;
 }
 
-// map: boxes (SW*EPC, min(nz, 256)), for the loads and the stores.
-template <typename T, int L>
+// map: boxes (SW*EPC, min(nz, 256)), for the loads; smap: the same boxes
+// for the stores (the same map in place, another work array's for the
+// first difference-field launch).  DM = 0: the spectral factor is H-hat;
+// DM = 1 (difference fields): H-hat (D_x + i D_y) for a.dmode 1, H-hat
+// (D_z + i) for a.dmode 2 (see PairArgs).  The modes are separate
+// instantiations so that the plain pass carries no mode branch.
+template <typename T, int L, int DM>
 __global__ void __launch_bounds__(WShape<T, L>::THREADS, (L >= 512 ? 2 : 3))
-    k_colw(PairArgs a, const __grid_constant__ CUtensorMap map, long long ntiles) {
+    k_colw(PairArgs a, const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap smap,
+           long long ntiles) {
     typedef WShape<T, L> S;
     typedef typename S::C C;
     constexpr int NS = nstages(L), NWARPS = S::THREADS / 32;
@@ -478,12 +487,13 @@ __global__ void __launch_bounds__(WShape<T, L>::THREADS, (L >= 512 ? 2 : 3))
         for (int s = 0; s < S::NSUB; ++s)
 #pragma unroll
             for (int k = 0; k < S::NBOXI; ++k)
-                tma_store_2d(&map, (int)((tile * S::COLS + s * S::SW) * S::EPC), k * S::BOXI,
+                tma_store_2d(&smap, (int)((tile * S::COLS + s * S::SW) * S::EPC), k * S::BOXI,
                              src + s * S::RIN * S::P + k * S::BOXI * S::P);
     };
 
     if (tid == 0) {
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&smap)) : "memory");
         mbar_init(&full[0], 1);
         mbar_init(&full[1], 1);
         mbar_init(&staged[0], NWARPS);
@@ -565,6 +575,34 @@ __global__ void __launch_bounds__(WShape<T, L>::THREADS, (L >= 512 ? 2 : 3))
         }
 
         pmfft::fft_core<L, false, -1, true, false, true>(v, xch, lay, t, tw);
+        // spectral factor of this column: H-hat times 1, D_x + i D_y
+        // (column constant) or D_z + i (per register: kz of register e is
+        // the last forward stage's output row)
+        C dxy = czero<C>();
+        if (DM == 1 && a.dmode == 1) {
+            const long long qc = tile * S::COLS + c;
+            const C ex = static_cast<const C *>(a.dtx)[qc & (nx2 - 1)];
+            const C ey = static_cast<const C *>(a.dty)[qc >> lnx2];
+            dxy.x = ex.x - ey.y;
+            dxy.y = ex.y + ey.x;
+        }
+        auto hmul = [&](int e, T h) {
+            if constexpr (DM == 0) {
+                v[e].x *= h;
+                v[e].y *= h;
+                return;
+            }
+            C f = dxy;
+            if (a.dmode == 2) {
+                constexpr int RLF = radix(L, NS - 1, false);
+                const int kz = pmfft::in_row<L, NS - 1, false>(t, e / RLF, e % RLF);
+                f = static_cast<const C *>(a.dtz)[kz];
+                f.y += (T)1;
+            }
+            f.x *= h;
+            f.y *= h;
+            v[e] = cmul(v[e], f);
+        };
         bool hok = true;
         if (hstage) {
             // H-hat of column c from the staged rows (row c, or COLS-1-c
@@ -573,11 +611,7 @@ __global__ void __launch_bounds__(WShape<T, L>::THREADS, (L >= 512 ? 2 : 3))
             if (hok && tid == 0) hpend = false;
             const T *hz = reinterpret_cast<const T *>(in) + (k0 < a.nx ? c : S::COLS - 1 - c) * L + t;
 #pragma unroll
-            for (int e = 0; e < E; ++e) {
-                const T h = hz[e * S::TPC];
-                v[e].x *= h;
-                v[e].y *= h;
-            }
+            for (int e = 0; e < E; ++e) hmul(e, hz[e * S::TPC]);
             pmfft::fft_core<L, true, 1, false, true, true>(v, xch, lay, t, tw);
             // every H-hat read done before the outputs overwrite the buffer
             if (!__syncthreads_and(hok ? 1 : 0)) {
@@ -599,27 +633,19 @@ __global__ void __launch_bounds__(WShape<T, L>::THREADS, (L >= 512 ? 2 : 3))
 #pragma unroll
                     for (int e = 0; e < E; e += 4) {
                         const float4 h = __ldg(reinterpret_cast<const float4 *>(hz + e));
-                        v[e].x *= h.x; v[e].y *= h.x;
-                        v[e + 1].x *= h.y; v[e + 1].y *= h.y;
-                        v[e + 2].x *= h.z; v[e + 2].y *= h.z;
-                        v[e + 3].x *= h.w; v[e + 3].y *= h.w;
+                        hmul(e, h.x); hmul(e + 1, h.y); hmul(e + 2, h.z); hmul(e + 3, h.w);
                     }
                 } else {
 #pragma unroll
                     for (int e = 0; e < E; e += 2) {
                         const double2 h = __ldg(reinterpret_cast<const double2 *>(hz + e));
-                        v[e].x *= h.x; v[e].y *= h.x;
-                        v[e + 1].x *= h.y; v[e + 1].y *= h.y;
+                        hmul(e, h.x); hmul(e + 1, h.y);
                     }
                 }
             } else {
                 const T *hz = hcol + t;
 #pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    const T h = __ldg(hz + e * S::TPC);
-                    v[e].x *= h;
-                    v[e].y *= h;
-                }
+                for (int e = 0; e < E; ++e) hmul(e, __ldg(hz + e * S::TPC));
             }
             pmfft::fft_core<L, true, 1, false, true, true>(v, xch, lay, t, tw);
         }

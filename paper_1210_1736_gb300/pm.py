@@ -88,6 +88,10 @@ _SIGS.update({
     "pm_cic_kick_drift": (C.c_int, [_vp, _P(pm_particles), C.c_double, C.c_double]),
     "pm_cic_vjp": (C.c_int, [_vp, _P(pm_particles), _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "pm_selftest_wait_expiry": (C.c_int, [_vp]),
+    "pm_recentre_sums": (C.c_int, [_vp, _P(pm_particles)]),
+    "pm_recentre_apply": (C.c_int, [_vp]),
+    "pm_exchange_buffers": (C.c_int, [_vp, _P(_vp), _P(C.c_int64), _P(_vp), _P(C.c_int64)]),
+    "pm_kick_drift": (C.c_int, [_vp, _P(pm_particles), C.c_double]),
 })
 
 _lib = None
@@ -219,6 +223,15 @@ class Particles:
         return pos, vel, self.flags.cpu().numpy().astype(np.int64)
 
 
+class _DeviceArray:
+    """An int64 device buffer owned by the library, exposed to torch through
+    the CUDA array interface (no copy)."""
+
+    def __init__(self, ptr, n):
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": "<i8", "data": (int(ptr), False),
+                                         "version": 3, "strides": None}
+
+
 class Context:
     """One pm_ctx: the grids, H-hat tables and work buffers of a system."""
 
@@ -257,6 +270,25 @@ class Context:
 
     def recentre(self, p):
         _check(lib().pm_recentre(self.h, C.byref(p.struct())))
+
+    def recentre_sums(self, p):
+        _check(lib().pm_recentre_sums(self.h, C.byref(p.struct())))
+
+    def recentre_apply(self):
+        _check(lib().pm_recentre_apply(self.h))
+
+    def exchange_buffers(self):
+        """(rho, csum): int64 device tensors viewing the context's density
+        block and centre-of-mass accumulators, without copying."""
+        import torch
+        rp, rb, cp, cb = _vp(), C.c_int64(), _vp(), C.c_int64()
+        _check(lib().pm_exchange_buffers(self.h, C.byref(rp), C.byref(rb), C.byref(cp), C.byref(cb)))
+        dev = torch.cuda.current_device()
+        return (torch.as_tensor(_DeviceArray(rp.value, rb.value // 8), device=f"cuda:{dev}"),
+                torch.as_tensor(_DeviceArray(cp.value, cb.value // 8), device=f"cuda:{dev}"))
+
+    def kick_drift(self, p, dt):
+        _check(lib().pm_kick_drift(self.h, C.byref(p.struct()), float(dt)))
 
     def deposit(self, p):
         _check(lib().pm_deposit(self.h, C.byref(p.struct())))

@@ -240,6 +240,49 @@ def test_trajectory_gradient_matches_finite_differences_small():
     assert np.all(e32 < 1e-4)
 
 
+def _oracle_theta_grads(w, steps):
+    """The FP64 CPU reference: gradients of both losses with respect to the
+    satellite's (X, V, M) from the oracle's trajectory map and its transpose
+    (cic_trajectory, cic_trajectory_vjp; grid centres fixed)."""
+    system = O.system_from_workload(w, 1.25 * O.mass_bound(w["m"]))
+    st0 = O.state_from_workload(w)
+    xT, vT, tape = OC.cic_trajectory(st0, system, w["dt"], steps)
+    sat = np.asarray(w["comp"]) == W.COMP_SATELLITE
+    disc = np.asarray(w["comp"]) == W.COMP_DISC
+    d = np.array([0.6, -0.48, 0.64])
+    out = np.zeros((2, 7))
+    for which in (0, 1):
+        lx, lv, lm_direct = np.zeros_like(xT), np.zeros_like(vT), np.zeros(len(st0.m))
+        if which == 0:      # L1 = d . mean of the satellite's final positions
+            lx[:, sat] = d[:, None] / sat.sum()
+        else:               # L2 = sum over the disc of m v_z^2 / 2 at t = T
+            lv[2, disc] = st0.m[disc] * vT[2, disc]
+            lm_direct[disc] = 0.5 * vT[2, disc] ** 2
+        gx, gv, gm = OC.cic_trajectory_vjp(tape, system, w["dt"], lx, lv)
+        out[which, 0:3] = gx[:, sat].sum(axis=1)
+        out[which, 3:6] = gv[:, sat].sum(axis=1)
+        out[which, 6] = np.sum(st0.m[sat] * (gm + lm_direct)[sat])
+    return out
+
+
+def test_trajectory_gradient_matches_oracle_reference():
+    """The same small case against the FP64 CPU reference gradient of the
+    whole trajectory (the oracle's per-step vector-Jacobian products chained
+    through the leap-frog map, itself pinned by central differences of the
+    oracle's map): the FP64 adjoint within 1e-9, the FP32 adjoint within
+    1e-4 (per loss, relative to its largest component)."""
+    w = W.merger_small(r_apo=3.0)
+    prob = _Problem(w, steps=20, every=5)
+    ref = _oracle_theta_grads(dict(w, precision="fp64"), 20)
+    g64 = prob.adjoint_grads("fp64")
+    g32 = prob.adjoint_grads("fp32")
+    e64, e32 = _grad_rel_err(g64, ref), _grad_rel_err(g32, ref)
+    print("oracle", ref, "\nadjoint fp64", g64, "\nadjoint fp32", g32)
+    print(f"relative error vs the oracle: fp64 {e64}, fp32 {e32}")
+    assert np.all(e64 < 1e-9)
+    assert np.all(e32 < 1e-4)
+
+
 def test_trajectory_gradient_full_size():
     """The differentiable-run workload at full size: 1M-particle galaxy
     (grids 128^3, 128^3 q = 1/4, 128x128x32) + 20k-particle satellite

@@ -409,3 +409,38 @@ def test_energy_angular_momentum_drift_100_steps(precision):
     assert abs(g0["E"] - d0["E"]) < (1e-12 if precision == "fp64" else 1e-5) * abs(d0["E"])
     assert abs(dE_gpu - dE_ref) < tol, (dE_gpu, dE_ref)
     assert abs(dL_gpu - dL_ref) < tol, (dL_gpu, dL_ref)
+
+
+def test_energy_angular_momentum_drift_100_steps_galaxy_1m():
+    """The 1M-particle galaxy (128^3, 128^3 q = 1/4, 128x128x32), FP32,
+    100 steps: the relative drifts of E and |L| match the oracle's within
+    1e-6 (the oracle's FFTs on all host cores)."""
+    import os
+    O.set_fft_workers(os.cpu_count())
+    try:
+        w = W.galaxy_1m(precision="fp32")
+        dt = w["dt"]
+        ctx, parts = gpu_setup(w)
+        ctx.deposit(parts)
+        ctx.solve()
+        ctx.kick(parts, -0.5 * dt)
+        g0 = ctx.diagnostics(parts, dt)
+        ctx.step(parts, dt, 100)
+        g1 = ctx.diagnostics(parts, dt)
+        ctx.close()
+        system, state = oracle_setup(w)
+        state = O.half_kick_start(state, system, dt)
+        d0 = O.diagnostics(state, system, dt)
+        for _ in range(100):
+            state = O.step(state, system, dt)
+        d1 = O.diagnostics(state, system, dt)
+    finally:
+        O.set_fft_workers(None)
+    dE_ref = (d1["E"] - d0["E"]) / abs(d0["E"])
+    dE_gpu = (g1["E"] - g0["E"]) / abs(g0["E"])
+    dL_ref = (np.linalg.norm(d1["L"]) - np.linalg.norm(d0["L"])) / np.linalg.norm(d0["L"])
+    dL_gpu = (np.linalg.norm(g1["L"]) - np.linalg.norm(g0["L"])) / np.linalg.norm(g0["L"])
+    print(f"galaxy_1m: dE oracle {dE_ref:.3e} gpu {dE_gpu:.3e}; dL oracle {dL_ref:.3e} gpu {dL_gpu:.3e}")
+    assert abs(g0["E"] - d0["E"]) < 1e-5 * abs(d0["E"])
+    assert abs(dE_gpu - dE_ref) < 1e-6, (dE_gpu, dE_ref)
+    assert abs(dL_gpu - dL_ref) < 1e-6, (dL_gpu, dL_ref)

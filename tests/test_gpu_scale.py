@@ -1,7 +1,11 @@
 """Parity at the workloads' structure and size limits: two galaxies with their
-own nested grids (the merger layout), and the largest grids (256^3, every
+own nested grids (the merger layout), the largest grids (256^3, every
 transform of length 512) checked on every density cell and on sampled
-potential cells that the oracle sums directly (Eq. eq:poisson)."""
+potential cells that the oracle sums directly (Eq. eq:poisson), and the FP32
+forces of the full-size merger (4.1M particles) and large (16.5M particles)
+workloads on sampled particles."""
+import os
+
 import numpy as np
 import pytest
 
@@ -110,3 +114,51 @@ def test_galaxy_256_nested_largest_grids():
     ctx.solve()
     _compare_density_and_flags(ctx, parts, system, rho, flags)
     _sampled_potential_check(ctx, system, rho, s, 24, 2e-6, 2)
+
+
+@pytest.mark.parametrize("name", ["merger_4m", "large_16m"])
+def test_fp32_forces_full_size(name):
+    """The full-size workloads in FP32: every density cell bit-exact and
+    every lost flag equal; forces (Eq. eqn:diff by the combination rule) on
+    every satellite particle and a uniform sample of 400k particles against
+    the oracle: RMS error < 2e-5 and largest error < 1e-4 of the RMS force
+    (reading r14; the RMS force and the RMS error from the uniform sample)."""
+    import torch
+    require_cuda()
+    O.set_fft_workers(os.cpu_count())
+    try:
+        w = getattr(W, name)()
+        ctx, parts = gpu_setup(w)
+        ctx.deposit(parts)
+        ctx.solve()
+        acc = ctx.force(parts)
+        torch.cuda.synchronize()
+        a_gpu = np.stack([a.cpu().numpy().astype(np.float64) for a in acc])
+        system, state = oracle_setup(w)
+        flags, own = O.classify(state, system)
+        rho, flags, s = O.deposit(state, system, flags, own)
+        _compare_density_and_flags(ctx, parts, system, rho, flags)
+        ctx.close()
+        del parts
+        phi = O.solve_all(rho, system, s)
+        n = len(state.m)
+        rng = np.random.default_rng(7)
+        uni = rng.choice(n, 400_000, replace=False)
+        sat = np.nonzero(np.asarray(w["comp"]) == W.COMP_SATELLITE)[0]
+        idx = np.union1d(uni, sat)
+        sub = O.State(state.pos[:, idx], state.vel[:, idx], state.m[idx], state.gal[idx], flags[idx],
+                      state.centres)
+        a_ref = O.accelerations(sub, system, phi, flags[idx])
+        live = (flags[idx] & 1) == 0
+        in_uni = np.isin(idx, uni)
+        d = np.sqrt(np.sum((a_gpu[:, idx] - a_ref) ** 2, axis=0))
+        f = np.sqrt(np.sum(a_ref ** 2, axis=0))
+        rms_ref = np.sqrt(np.mean(f[live & in_uni] ** 2))
+        rms = np.sqrt(np.mean(d[live & in_uni] ** 2)) / rms_ref
+        mx = np.max(d[live]) / rms_ref
+        mx_sat = np.max(d[live & ~in_uni], initial=0.0) / rms_ref
+        print(f"{name}: force error rms {rms:.3e} max {mx:.3e} (satellites {mx_sat:.3e}), "
+              f"{int(live.sum())} particles")
+        assert rms < 2e-5 and mx < 1e-4, (rms, mx)
+    finally:
+        O.set_fft_workers(None)

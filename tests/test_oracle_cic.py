@@ -179,3 +179,38 @@ def test_step_matches_kick_drift_of_accelerations():
     nxt = C.cic_step(st, sysm, 0.01)
     assert np.allclose(nxt.vel, st.vel + 0.01 * a, rtol=0, atol=1e-15)
     assert np.allclose(nxt.pos, st.pos + 0.01 * nxt.vel, rtol=0, atol=1e-15)
+
+
+def test_trajectory_vjp_matches_central_differences():
+    """The transpose of the whole leap-frog map (cic_trajectory_vjp, the
+    per-step vector-Jacobian products chained newest first) against central
+    differences of the oracle's own forward map (cic_trajectory), 4 steps of
+    the two-galaxy system with the satellite inside the disc: directional
+    derivatives along the satellite's positions, velocities and masses for a
+    random cotangent of (x_T, v_T)."""
+    from paper_1210_1736_gb300 import workloads as W
+    w = W.merger_small(precision="fp64", r_apo=3.0)
+    system = O.system_from_workload(w, 1.25 * O.mass_bound(w["m"]))
+    st0 = O.state_from_workload(w)
+    steps, dt = 4, w["dt"]
+    xT, vT, tape = C.cic_trajectory(st0, system, dt, steps)
+    rng = np.random.default_rng(1)
+    lx, lv = rng.normal(size=xT.shape), rng.normal(size=vT.shape)
+    gx, gv, gm = C.cic_trajectory_vjp(tape, system, dt, lx, lv)
+
+    def J(dx=0.0, dv=0.0, dm=0.0):
+        s = st0.copy()
+        s.pos, s.vel, s.m = s.pos + dx, s.vel + dv, s.m + dm
+        x, v, _ = C.cic_trajectory(s, system, dt, steps)
+        return np.sum(lx * x) + np.sum(lv * v)
+
+    sat = np.asarray(w["comp"]) == W.COMP_SATELLITE
+    d = np.array([0.3, -0.5, 0.2])[:, None] * sat[None, :]
+    h = 1e-8
+    fx = (J(dx=h * d) - J(dx=-h * d)) / (2 * h)
+    fv = (J(dv=h * d) - J(dv=-h * d)) / (2 * h)
+    dm = st0.m * sat
+    fm = (J(dm=1e-6 * dm) - J(dm=-1e-6 * dm)) / 2e-6
+    assert np.sum(gx * d) == pytest.approx(fx, rel=1e-5)
+    assert np.sum(gv * d) == pytest.approx(fv, rel=1e-5)
+    assert np.sum(gm * dm) == pytest.approx(fm, rel=1e-5)
