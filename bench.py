@@ -42,6 +42,8 @@ WORKLOAD_DESC = {
                  "256x256x32; satellite grids 64^3 x 3; dt=0.01",
     "large_16m": "large_16m: 16M-particle galaxy + two 250k Plummer satellites; galaxy grids 256^3, 256^3 q=1/4, "
                  "256x256x64; satellite grids 128^3 x 3 each; dt=0.01",
+    "galaxy_256": "galaxy_256: 2M-particle galaxy on the large run's grids 256^3, 256^3 q=1/4, 256x256x64; dt=0.01 "
+                  "(profiling size)",
 }
 PHASES = ["recentre", "deposit", "fft_x_fwd", "fft_y_fwd", "fft_z_conv", "fft_y_inv", "fft_x_inv", "force_kick_drift"]
 SORT_PHASE = 9
