@@ -551,7 +551,7 @@ def run_ours(args):
     del pipe, parts
     torch.cuda.empty_cache()
     if rank == 0 and world == 1:
-        extras = [x for x in args.extra_workloads.split(",") if x and x != args.workload]
+        extras = [x for x in args.extra_workloads.split(",") if x and x != "none" and x != args.workload]
         line["extra_workloads"] = {x: extra_workload(x, K, Wm, args.sort_every,
                                                      args.fp64_steps if x == "galaxy_1m" else 0)
                                    for x in extras}
@@ -654,7 +654,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOAD_DESC))
     ap.add_argument("--extra-workloads", default=",".join(EXTRA_WORKLOADS),
-                    help="comma-separated workloads also measured (rank 0, N = 1), reported in extra_workloads")
+                    help="comma-separated workloads also measured (rank 0, N = 1), reported in extra_workloads "
+                         "('none' or '': no others)")
     ap.add_argument("--fp64-steps", type=int, default=5,
                     help="steps timed on the FP64 instantiation for comparison (0: skip)")
     ap.add_argument("--sort-every", type=int, default=10,
