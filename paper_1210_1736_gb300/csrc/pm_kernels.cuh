@@ -635,16 +635,21 @@ __global__ void k_count_lost(PartK<T> p, unsigned long long *out) {
 
 template <typename T, int L>
 __global__ void k_store_hhat(const double *oct, T *out, int nx, int ny, double scale) {
-    constexpr int TPC = L / E, NS = nstages(L), RL = radix(L, NS - 1, false);
+    constexpr int NS = nstages(L), RL = radix(L, NS - 1, false), HS = pm_hhat_stride(L);
     const long long ncol = (long long)(nx + 1) * (ny + 1);
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < ncol * L;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < ncol * HS;
          i += (long long)gridDim.x * blockDim.x) {
-        const long long col = i / L;
-        const int w = (int)(i % L);
-        const int e = hhat_thread_major(L) ? w % E : w / TPC, t = hhat_thread_major(L) ? w / E : w % TPC;
-        const int kz = pmfft::in_row<L, NS - 1, false>(t, e / RL, e % RL);
-        const int kzr = kz <= L / 2 ? kz : L - kz;
-        out[i] = (T)(oct[(long long)kzr * ncol + col] * scale);
+        const long long col = i / HS;
+        const int w = (int)(i % HS);
+        int kzr;
+        if (hhat_thread_major(L)) {   // register w % 16 of thread w / 16
+            const int e = w % E, t = w / E;
+            const int kz = pmfft::in_row<L, NS - 1, false>(t, e / RL, e % RL);
+            kzr = kz <= L / 2 ? kz : L - kz;
+        } else {
+            kzr = w;                  // padding beyond nz = L/2
+        }
+        out[i] = kzr <= L / 2 ? (T)(oct[(long long)kzr * ncol + col] * scale) : (T)0;
     }
 }
 

@@ -137,11 +137,22 @@ cudaError_t pm_green_octant(double *h, int nx, int ny, int nz, double q, double 
 cudaError_t pm_axis_transform(const double *in, double *out, const double *cmat, int n1,
                               long long outer, long long inner, cudaStream_t st);
 // H-hat table of the z pass from the FP64 octant oct[kzr][kyr][kxr]
-// (scaled by `scale`): for each octant column (kyr, kxr) the L = 2nz values
-// H-hat(kz) in the order the z pass's threads hold the forward transform's
-// outputs: register e of thread t at entry e * L/16 + t, or at t * 16 + e
-// for L <= 64 (hhat_thread_major); kz > L/2 mirrored.
-inline long long pm_hhat_table_size(int nx, int ny, int nz) { return (long long)(nx + 1) * (ny + 1) * 2 * nz; }
+// (scaled by `scale`): for each octant column (kyr, kxr), for L = 2nz >= 128
+// the nz + 1 values H-hat(kzr) padded with zeros to pm_hhat_stride(L); for
+// L <= 64 the L values H-hat(kz) (kz > L/2 mirrored) in thread-major order,
+// register e of thread t at entry t * 16 + e (hhat_thread_major).
+// For L = 2nz >= 128 each octant column holds only H-hat(kzr), kzr = 0..nz,
+// padded to pm_hhat_stride(L) values: the smallest h >= nz + 1 with
+// h = TPC (mod 2 TPC), TPC = L/16 threads per column, so that the columns of
+// a warp (32/TPC of them) read disjoint shared-memory banks; each lane
+// mirrors its kz itself.  Shorter transforms keep the full L values per
+// column in thread-major order.
+__host__ __device__ constexpr int pm_hhat_stride(int L) {
+    return L < 128 ? L : (L / 16) + (L / 8) * ((L / 2 + 1 - L / 16 + L / 8 - 1) / (L / 8));
+}
+inline long long pm_hhat_table_size(int nx, int ny, int nz) {
+    return (long long)(nx + 1) * (ny + 1) * pm_hhat_stride(2 * nz);
+}
 template <typename T>
 cudaError_t pm_store_hhat(const double *oct, T *out, int nx, int ny, int nz, double scale, cudaStream_t st);
 

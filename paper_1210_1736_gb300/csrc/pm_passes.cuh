@@ -423,17 +423,32 @@ template <typename T, int L> struct WShape {
     static constexpr int LDR = L + L / 16;
     static constexpr int EPC = (int)sizeof(C) / 8;
     static constexpr unsigned BUF = (unsigned)(RIN * COLS * sizeof(C));
+    static constexpr int HS = pm_hhat_stride(L);                       // H-hat values per octant column
+    static constexpr unsigned HBYTES = (unsigned)(COLS * HS * sizeof(T));   // a tile's staged H-hat rows
+    static_assert(HBYTES <= BUF, "a tile's H-hat rows fit its input buffer");
     // the longest transform runs two blocks per SM with the warps decoupled
     // (thread 0 sends a tile once every warp has arrived on its barrier); the
     // others measured faster block-synchronous (block barriers per tile)
     static constexpr bool FREE = L >= 512;
 };
 
+// Shared memory of the z pass: two tile buffers, the exchange rows, the
+// stage twiddles, six mbarriers, and (decoupled warps, L >= 512) one H-hat
+// column per warp, prefetched with cp.async while the forward FFT runs.
 template <typename T, int L> constexpr size_t colw_smem() {
     typedef WShape<T, L> S;
     return 1024 + 2 * (size_t)S::BUF + (size_t)S::COLS * S::LDR * sizeof(typename S::C) +
-           (size_t)pmfft::tw_total(L) * sizeof(typename S::C) + 64;
+           (size_t)pmfft::tw_total(L) * sizeof(typename S::C) + 64 +
+           (S::FREE ? (size_t)(S::THREADS / 32) * S::HS * sizeof(T) : 0);
 }
+
+// Asynchronous global -> shared copies of 16 bytes (both addresses 16-byte
+// aligned), completed by cp_async_wait_all in the issuing thread.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // Byte offset of element (row, column c) of a tile buffer whose sub-tiles
 // hold ROWS rows (swizzle of the tensor map: the 16-byte chunk index XOR the
@@ -467,13 +482,14 @@ __global__ void __launch_bounds__(WShape<T, L>::THREADS, (L >= 512 ? 2 : 3))
     uint64_t *full = reinterpret_cast<uint64_t *>(tw + pmfft::tw_total(L));   // tile loaded (tx bytes)
     uint64_t *staged = full + 2;                                            // every warp staged (FREE)
     uint64_t *hfull = staged + 2;                                           // tile's H-hat staged
+    T *hpre = reinterpret_cast<T *>(hfull + 2);   // FREE: one prefetched H-hat column per warp (16-byte aligned)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int t = lane % S::TPC;
     const int c = warp * (32 / S::TPC) + lane / S::TPC;   // column within the tile
     const int nx2 = 2 * a.nx, ny2 = 2 * a.ny, lnx2 = __ffs(nx2) - 1;
 
     // tile <-> sub-tiles of the buffer, each NBOXI boxes of BOXI rows
-    auto issue_load = [&](long long tile, int b) {
+    auto issue_load = [&](int tile, int b) {
         mbar_expect_tx(&full[b], S::BUF);
 #pragma unroll
         for (int s = 0; s < S::NSUB; ++s)
@@ -482,7 +498,7 @@ __global__ void __launch_bounds__(WShape<T, L>::THREADS, (L >= 512 ? 2 : 3))
                 tma_load_2d(base + b * S::BUF + s * S::RIN * S::P + k * S::BOXI * S::P, &map,
                             (int)((tile * S::COLS + s * S::SW) * S::EPC), k * S::BOXI, &full[b]);
     };
-    auto issue_store = [&](long long tile, const unsigned char *src) {
+    auto issue_store = [&](int tile, const unsigned char *src) {
 #pragma unroll
         for (int s = 0; s < S::NSUB; ++s)
 #pragma unroll
@@ -515,17 +531,20 @@ __global__ void __launch_bounds__(WShape<T, L>::THREADS, (L >= 512 ? 2 : 3))
     // thread 0 issues every copy; counts per buffer of loads issued and of
     // tiles sent (to drain after an expired wait)
     int issued0 = 0, issued1 = 0, done0 = 0, done1 = 0;
-    long long deferred = -1;   // thread 0: tile whose buffer awaits its refill
+    const int nt0 = (int)ntiles;
+    int deferred = -1;   // thread 0: tile whose buffer awaits its refill
     if (tid == 0) {
-        if (blockIdx.x < ntiles) { issue_load(blockIdx.x, 0); ++issued0; }
-        if (blockIdx.x + gridDim.x < ntiles) { issue_load(blockIdx.x + gridDim.x, 1); ++issued1; }
+        if ((int)blockIdx.x < nt0) { issue_load(blockIdx.x, 0); ++issued0; }
+        if ((int)(blockIdx.x + gridDim.x) < nt0) { issue_load(blockIdx.x + gridDim.x, 1); ++issued1; }
     }
     const pmfft::RowLayout lay{c * S::LDR};
     bool failed = false;
 
     int it = 0;
-    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
-        if (tile + gridDim.x >= ntiles) pdl_release();
+    // tile indices fit in 32 bits: at most (2 * 256)^2 / COLS tiles
+    const int nt = (int)ntiles;
+    for (int tile = blockIdx.x; tile < nt; tile += gridDim.x, ++it) {
+        if (tile + (int)gridDim.x >= nt) pdl_release();
         const int b = it & 1;
         const unsigned phase = (unsigned)((it >> 1) & 1);
         if (FREE) {
@@ -535,6 +554,18 @@ __global__ void __launch_bounds__(WShape<T, L>::THREADS, (L >= 512 ? 2 : 3))
             break;
         }
         unsigned char *in = base + b * S::BUF;
+        if constexpr (FREE) {
+            // this warp's column (one per warp): its H-hat column lands in
+            // shared memory while the forward FFT runs
+            const int qc = tile * S::COLS + c;
+            const int ky = qc >> lnx2, kx = qc & (nx2 - 1);
+            const int kyr = ky <= a.ny ? ky : ny2 - ky, kxr = kx <= a.nx ? kx : nx2 - kx;
+            const unsigned char *src = reinterpret_cast<const unsigned char *>(
+                static_cast<const T *>(a.hhat) + ((size_t)kyr * (a.nx + 1) + kxr) * S::HS);
+            unsigned char *dst = reinterpret_cast<unsigned char *>(hpre + warp * S::HS);
+            for (int ch = lane; ch < (int)(S::HS * sizeof(T) / 16); ch += 32) cp_async16(dst + 16 * ch, src + 16 * ch);
+            cp_async_commit();
+        }
         C v[E];
         constexpr int R0 = radix(L, 0, false);
 #pragma unroll
@@ -556,21 +587,22 @@ __global__ void __launch_bounds__(WShape<T, L>::THREADS, (L >= 512 ? 2 : 3))
             // lands well before it is needed
             bulk_wait_read();
             const int db = b ^ 1;
-            if (deferred + 2 * (long long)gridDim.x < ntiles) {
-                issue_load(deferred + 2 * (long long)gridDim.x, db);
+            if (deferred + 2 * (int)gridDim.x < nt) {
+                issue_load(deferred + 2 * (int)gridDim.x, db);
                 if (db) ++issued1; else ++issued0;
             }
             deferred = -1;
         }
-        const long long q0 = tile * S::COLS;
+        const int q0 = tile * S::COLS;
         const int k0 = (int)(q0 & (nx2 - 1));
         if (hstage && tid == 0) {
             const int ky0 = (int)(q0 >> lnx2);
             const int kyr0 = ky0 <= a.ny ? ky0 : ny2 - ky0;
             const int r0 = k0 < a.nx ? k0 : nx2 - k0 - S::COLS + 1;
             fence_async_smem();   // the inputs' generic reads before the copy's writes
-            mbar_expect_tx(&hfull[b], S::BUF);
-            bulk_load(in, static_cast<const T *>(a.hhat) + ((size_t)kyr0 * (a.nx + 1) + r0) * L, S::BUF, &hfull[b]);
+            mbar_expect_tx(&hfull[b], S::HBYTES);
+            bulk_load(in, static_cast<const T *>(a.hhat) + ((size_t)kyr0 * (a.nx + 1) + r0) * S::HS, S::HBYTES,
+                      &hfull[b]);
             hpend = true;
         }
 
@@ -580,12 +612,18 @@ __global__ void __launch_bounds__(WShape<T, L>::THREADS, (L >= 512 ? 2 : 3))
         // the last forward stage's output row)
         C dxy = czero<C>();
         if (DM == 1 && a.dmode == 1) {
-            const long long qc = tile * S::COLS + c;
+            const int qc = tile * S::COLS + c;
             const C ex = static_cast<const C *>(a.dtx)[qc & (nx2 - 1)];
             const C ey = static_cast<const C *>(a.dty)[qc >> lnx2];
             dxy.x = ex.x - ey.y;
             dxy.y = ex.y + ey.x;
         }
+        // mirrored kz (0..L/2) of register e: the last forward stage's row
+        auto kz_mirror = [&](int e) {
+            constexpr int RLF = radix(L, NS - 1, false);
+            const int kz = pmfft::in_row<L, NS - 1, false>(t, e / RLF, e % RLF);
+            return kz <= L / 2 ? kz : L - kz;
+        };
         auto hmul = [&](int e, T h) {
             if constexpr (DM == 0) {
                 v[e].x *= h;
@@ -606,12 +644,12 @@ __global__ void __launch_bounds__(WShape<T, L>::THREADS, (L >= 512 ? 2 : 3))
         bool hok = true;
         if (hstage) {
             // H-hat of column c from the staged rows (row c, or COLS-1-c
-            // for the mirrored half), register order
+            // for the mirrored half), indexed by the register's mirrored kz
             hok = mbar_wait(&hfull[b], phase);
             if (hok && tid == 0) hpend = false;
-            const T *hz = reinterpret_cast<const T *>(in) + (k0 < a.nx ? c : S::COLS - 1 - c) * L + t;
+            const T *hz = reinterpret_cast<const T *>(in) + (k0 < a.nx ? c : S::COLS - 1 - c) * S::HS;
 #pragma unroll
-            for (int e = 0; e < E; ++e) hmul(e, hz[e * S::TPC]);
+            for (int e = 0; e < E; ++e) hmul(e, hz[kz_mirror(e)]);
             pmfft::fft_core<L, true, 1, false, true, true>(v, xch, lay, t, tw);
             // every H-hat read done before the outputs overwrite the buffer
             if (!__syncthreads_and(hok ? 1 : 0)) {
@@ -622,11 +660,11 @@ __global__ void __launch_bounds__(WShape<T, L>::THREADS, (L >= 512 ? 2 : 3))
         } else {
             // H-hat of column (kyr, kxr), stored by pm_store_hhat in the
             // order hhat_thread_major gives for L
-            const long long q = tile * S::COLS + c;
-            const int ky = (int)(q >> lnx2), kx = (int)(q & (nx2 - 1));   // nx2 is a power of two
+            const int q = tile * S::COLS + c;
+            const int ky = q >> lnx2, kx = q & (nx2 - 1);   // nx2 is a power of two
             const int kyr = ky <= a.ny ? ky : ny2 - ky;
             const int kxr = kx <= a.nx ? kx : nx2 - kx;
-            const T *hcol = static_cast<const T *>(a.hhat) + ((size_t)kyr * (a.nx + 1) + kxr) * L;
+            const T *hcol = static_cast<const T *>(a.hhat) + ((size_t)kyr * (a.nx + 1) + kxr) * S::HS;
             if constexpr (hhat_thread_major(L)) {
                 const T *hz = hcol + t * E;   // 16-byte aligned: L, E multiples of 16
                 if constexpr (sizeof(T) == 4) {
@@ -642,10 +680,16 @@ __global__ void __launch_bounds__(WShape<T, L>::THREADS, (L >= 512 ? 2 : 3))
                         hmul(e, h.x); hmul(e + 1, h.y);
                     }
                 }
-            } else {
-                const T *hz = hcol + t;
+            } else if constexpr (FREE) {
+                cp_async_wait_all();
+                __syncwarp();
+                const T *hz = hpre + warp * S::HS;
 #pragma unroll
-                for (int e = 0; e < E; ++e) hmul(e, __ldg(hz + e * S::TPC));
+                for (int e = 0; e < E; ++e) hmul(e, hz[kz_mirror(e)]);
+                __syncwarp();   // every lane's reads done before the next tile's prefetch
+            } else {
+#pragma unroll
+                for (int e = 0; e < E; ++e) hmul(e, __ldg(hcol + kz_mirror(e)));
             }
             pmfft::fft_core<L, true, 1, false, true, true>(v, xch, lay, t, tw);
         }
@@ -674,8 +718,8 @@ __global__ void __launch_bounds__(WShape<T, L>::THREADS, (L >= 512 ? 2 : 3))
             if (b) ++done1; else ++done0;
             if (FREE) {
                 bulk_wait_read();   // the staged outputs have been read out
-                if (tile + 2 * (long long)gridDim.x < ntiles) {
-                    issue_load(tile + 2 * (long long)gridDim.x, b);
+                if (tile + 2 * (int)gridDim.x < nt) {
+                    issue_load(tile + 2 * (int)gridDim.x, b);
                     if (b) ++issued1; else ++issued0;
                 }
             } else {
