@@ -272,13 +272,39 @@ def fft_pairs(w):
     return n
 
 
-def launches(w, steps, sort_every):
+def fft_launches(w, batched=True):
+    """FFT launches per step: the pairs of mass sets of all galaxies are
+    grouped by grid shape (nx, ny, nz) and each pass of a shape is one launch
+    per 8 pairs; a fine grid (grid 1, solved for its difference fields) adds
+    a second work array to the y and x inverse passes and two z passes of
+    its own."""
+    shapes = {}
+    for g in w["galaxies"]:
+        pairs = [(g["coarse"], False)]
+        if g.get("medium"):
+            pairs.append((g["medium"], False))
+            if g.get("fine"):
+                pairs.append((g["fine"], True))
+        for spec, diff in pairs:
+            p, d = shapes.get(tuple(spec[:3]), (0, 0))
+            shapes[tuple(spec[:3])] = (p + 1, d + int(diff))
+    if not batched:   # a launch per pair: five passes, three more for a fine grid
+        return sum(5 * p + 3 * d for p, d in shapes.values())
+    up = lambda k: (k + 7) // 8  # noqa: E731
+    n = 0
+    for p, d in shapes.values():
+        n += 2 * up(p)                                   # x and y forward
+        n += up(p - d) + (2 * up(d) if d else 0)         # z: plain, then the two difference passes
+        n += 2 * up(p + d)                               # y and x inverse over both work arrays
+    return n
+
+
+def launches(w, steps, sort_every, batched=True):
     """Kernels of `steps` graph steps: recentre and its centre update, deposit,
-    five FFT passes per pair of mass sets (eight for a fine grid: its z, y
-    inverse and x inverse passes run twice), force/kick-drift; every
-    sort_every-th step adds the six kernels of the spatial sort."""
-    fine = sum(1 for g in w["galaxies"] if g.get("medium") and g.get("fine"))
-    per_step = 2 + 1 + 5 * fft_pairs(w) + 3 * fine + 1
+    the FFT passes (batched or per pair, as the context chose), force/
+    kick-drift; every sort_every-th step adds the six kernels of the spatial
+    sort."""
+    per_step = 2 + 1 + fft_launches(w, batched) + 1
     sorts = (steps + sort_every - 1) // sort_every if sort_every > 0 else 0
     return per_step * steps + 6 * sorts
 
@@ -430,6 +456,7 @@ def extra_workload(name, K, Wm, sort_every, fp64_steps):
            "fft_convolve": {"frac": dm["conv_gbs"] / peak, "span_frac": dm["span_gbs"] / peak,
                             "span_ms_per_step": dm["span_ms"]},
            "step_bound_frac": sum(dm["pb"].values()) / (peak * 1e9) * 1e3 / ms,
+           "solve_schedule": ctx.info()["solve_schedule"], "batched": ctx.info()["batched"],
            "phase_ms_per_step": dm["phase_ms"]}
     if fp64 is not None:
         fp64["speedup_fp32"] = fp64["ms_per_step"] / ms
@@ -520,8 +547,10 @@ def run_ours(args):
         "dtype": "f32", "data": "synthetic (seeded disc-bulge-halo galaxy, random order)",
         "config": bench_config(w, args.workload, n, world),
         "spatial_sort_every": args.sort_every,
-        "solve_schedule": {0: "one branch per geometry", 1: "two staggered lanes",
-                           -1: "single geometry"}[ctx.info()["solve_schedule"]],
+        "solve_schedule": ({0: "one branch per unit", 1: "two staggered lanes",
+                            -1: "single unit"}[ctx.info()["solve_schedule"]] +
+                           ("; units: grid shapes, same-shape pairs batched per launch" if ctx.info()["batched"]
+                            else "; units: geometries, one launch per pair")),
         "device_bytes": ctx.info()["bytes"],
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
@@ -541,7 +570,7 @@ def run_ours(args):
                 "steps": Ke, "serial_value": e2e_serial,
                 "pipeline": "one-step requests rotating over three device buffers: upload of k+1 and download "
                             "of k-1 on their own streams overlap the step of k; serial_value without the overlap"},
-        "gpu_launches": launches(w, K, args.sort_every),
+        "gpu_launches": launches(w, K, args.sort_every, bool(ctx.info()["batched"])),
         "clocks": clocks,
     }
     if fp64 is not None:

@@ -190,12 +190,16 @@ int pm_get_potential(pm_ctx *ctx, int32_t gal, int32_t set, void *host_out);
 int pm_get_centres(pm_ctx *ctx, double *host_out);          /* ngal*3 */
 int pm_set_centres(pm_ctx *ctx, const double *host_in);     /* ngal*3 */
 int pm_count_lost(pm_ctx *ctx, const pm_particles *p, int64_t *host_out);
-/* host_out[5] = [fixed-point shift, mass sets, distinct geometries, device
- * bytes, solve schedule].  The schedule of the geometries' FFT chains is
- * chosen when the context is created by timing both on the device: 0 = one
- * branch stream per geometry, all chains starting together; 1 = two branch
- * streams of about equal work, one running its chains largest first and the
- * other smallest first; -1 = a single geometry (no branches). */
+/* host_out[6] = [fixed-point shift, mass sets, distinct geometries, device
+ * bytes, solve schedule, batched].  The solve's schedule is chosen when the
+ * context is created by timing each on the device.  Its units are either the
+ * grid shapes (batched = 1: the pairs of mass sets of every geometry of one
+ * shape, e.g. the same-size grids of several galaxies, share each FFT pass's
+ * launches) or the single geometries (batched = 0: a launch per pair); their
+ * chains of passes run as 0 = one branch stream per unit, all starting
+ * together; 1 = two branch streams of about equal work, one running its
+ * chains largest first and the other smallest first; -1 = a single unit (no
+ * branches). */
 int pm_info(pm_ctx *ctx, int64_t *host_out);
 
 /* Self-test of failure detection (no counterpart in the paper): launches one

@@ -141,6 +141,13 @@ struct GeoBuf {
     std::vector<Pair> pairs;
 };
 
+// Geometries of one shape (nx, ny, nz), e.g. the same-size grids of several
+// galaxies: their pairs share each pass's launches (up to PM_BATCH pairs).
+struct ShapeGroup {
+    int nx, ny, nz;
+    std::vector<int> geos;
+};
+
 }  // namespace
 
 struct pm_ctx {
@@ -151,6 +158,12 @@ struct pm_ctx {
     int shift = 0;
     double mscale = 1.0;
     std::vector<GeoBuf> geos;
+    std::vector<ShapeGroup> shapes;
+    // units of the solve's launches and branch streams: with `batched`, one
+    // unit per shape whose pairs share each pass's launches; without, one
+    // unit per geometry, each pair launched on its own (chosen by timing)
+    bool batched = true;
+    std::vector<std::vector<int>> units;   // geometry indices per unit
     int set_geo[PM_MAX_GALAXIES][PM_SETS];
     long long *rho[PM_MAX_GALAXIES][PM_SETS];
     void *phi[PM_MAX_GALAXIES][PM_SETS];
@@ -309,97 +322,142 @@ template <typename T> int upload_twiddles(pm_ctx *c) {
 // ---- the passes of pm_solve --------------------------------------------------
 enum { PASS_XFWD = 0, PASS_YFWD, PASS_ZCONV, PASS_YINV, PASS_XINV, NPASS };
 
-// shift: fixed-point scale of the input densities (2^-shift); the mass scale
-// unless an adjoint solve passes its own.
-template <typename T> int launch_pass(pm_ctx *c, int pass, cudaStream_t st, int only = -1, int shift = INT_MIN) {
-    for (int gi = 0; gi < (int)c->geos.size(); ++gi) {
-        if (only >= 0 && gi != only) continue;
-        const GeoBuf &gb = c->geos[gi];
-        const pm_geometry &g = gb.g;
-        for (const Pair &pr : gb.pairs) {
-            PairArgs a;
-            std::memset(&a, 0, sizeof(a));
-            a.rho_a = c->rho[pr.gi][pr.a];
-            a.rho_b = pr.b >= 0 ? c->rho[pr.gi][pr.b] : nullptr;
-            a.work = pr.work;
-            a.phi_b = pr.b >= 0 ? c->phi[pr.gi][pr.b] : nullptr;
-            a.phi_sum = c->phi[pr.gi][pr.a];
-            a.hhat = gb.hhat;
-            a.nx = g.nx; a.ny = g.ny; a.nz = g.nz;
-            a.scale = std::ldexp(1.0, -(shift == INT_MIN ? c->shift : shift));
-            a.err = c->d_err;
-            a.dtx = c->d_dt[tw_index(2 * g.nx)];
-            a.dty = c->d_dt[tw_index(2 * g.ny)];
-            a.dtz = c->d_dt[tw_index(2 * g.nz)];
-            cudaError_t e;
-            if (pr.diff && pass >= PASS_ZCONV) {
-                // difference fields: fx + i fy through work2, fz + i Phi_1 in place
-                if (pass == PASS_ZCONV) {
-                    a.tw = c->d_tw[tw_index(2 * g.nz)];
-                    a.dmode = 1;
-                    e = pm_launch_zconv<T>(a, pr.zmap, pr.zmap2, st);
-                    if (e == cudaSuccess) {
-                        a.dmode = 2;
-                        e = pm_launch_zconv<T>(a, pr.zmap, pr.zmap, st);
-                    }
-                } else if (pass == PASS_YINV) {
-                    a.tw = c->d_tw[tw_index(2 * g.ny)];
-                    e = pm_launch_col<T>(a, pr.yinv, COL_YINV, st);
-                    a.work = pr.work2;
-                    if (e == cudaSuccess) e = pm_launch_col<T>(a, pr.yinv2, COL_YINV, st);
-                } else {
-                    a.tw = c->d_tw[tw_index(2 * g.nx)];
-                    a.split = 1;
-                    a.phi_sum = c->fd[pr.gi][2];
-                    a.phi_b = c->phi[pr.gi][pr.a];
-                    e = pm_launch_xinv<T>(a, st);
-                    a.work = pr.work2;
-                    a.phi_sum = c->fd[pr.gi][0];
-                    a.phi_b = c->fd[pr.gi][1];
-                    if (e == cudaSuccess) e = pm_launch_xinv<T>(a, st);
-                }
-                if (e != cudaSuccess)
-                    return fail(PM_E_CUDA, "FFT pass %d launch failed: %s", pass, cudaGetErrorString(e));
-                continue;
-            }
-            switch (pass) {
-                case PASS_XFWD:
-                    a.tw = c->d_tw[tw_index(2 * g.nx)];
-                    e = pm_launch_xfwd<T>(a, st);
-                    break;
-                case PASS_YFWD:
-                    a.tw = c->d_tw[tw_index(2 * g.ny)];
-                    e = pm_launch_col<T>(a, pr.yfwd, COL_YFWD, st);
-                    break;
-                case PASS_ZCONV:
-                    a.tw = c->d_tw[tw_index(2 * g.nz)];
-                    e = pm_launch_col<T>(a, pr.zmap, COL_ZCONV, st);
-                    break;
-                case PASS_YINV:
-                    a.tw = c->d_tw[tw_index(2 * g.ny)];
-                    e = pm_launch_col<T>(a, pr.yinv, COL_YINV, st);
-                    break;
-                default:
-                    a.tw = c->d_tw[tw_index(2 * g.nx)];
-                    e = pm_launch_xinv<T>(a, st);
-                    break;
-            }
-            if (e != cudaSuccess) return fail(PM_E_CUDA, "FFT pass %d launch failed: %s", pass, cudaGetErrorString(e));
+// The arguments of one pair's passes.  shift: fixed-point scale of the
+// input densities (2^-shift); the mass scale unless an adjoint solve passes
+// its own.
+PairArgs pair_args(const pm_ctx *c, const GeoBuf &gb, const Pair &pr, int shift) {
+    const pm_geometry &g = gb.g;
+    PairArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.rho_a = c->rho[pr.gi][pr.a];
+    a.rho_b = pr.b >= 0 ? c->rho[pr.gi][pr.b] : nullptr;
+    a.work = pr.work;
+    a.phi_b = pr.b >= 0 ? c->phi[pr.gi][pr.b] : nullptr;
+    a.phi_sum = c->phi[pr.gi][pr.a];
+    a.hhat = gb.hhat;
+    a.nx = g.nx; a.ny = g.ny; a.nz = g.nz;
+    a.scale = std::ldexp(1.0, -(shift == INT_MIN ? c->shift : shift));
+    a.err = c->d_err;
+    a.dtx = c->d_dt[tw_index(2 * g.nx)];
+    a.dty = c->d_dt[tw_index(2 * g.ny)];
+    a.dtz = c->d_dt[tw_index(2 * g.nz)];
+    return a;
+}
+
+// Items of one batched pass launch (PairArgs and tensor maps).
+struct BatchItems {
+    std::vector<PairArgs> a;
+    std::vector<const CUtensorMap *> l, s;
+    void add(const PairArgs &x, const CUtensorMap *lm = nullptr, const CUtensorMap *sm = nullptr) {
+        a.push_back(x);
+        l.push_back(lm);
+        s.push_back(sm ? sm : lm);
+    }
+};
+
+// Launches `pass` of every item in chunks of `chunk` (<= PM_BATCH) items.
+template <typename T> cudaError_t launch_items(int pass, const BatchItems &it, size_t chunk, cudaStream_t st) {
+    for (size_t i0 = 0; i0 < it.a.size(); i0 += chunk) {
+        PassBatch b;
+        std::memset(&b, 0, sizeof(b));
+        b.n = (int)std::min<size_t>(chunk, it.a.size() - i0);
+        for (int k = 0; k < b.n; ++k) {
+            b.a[k] = it.a[i0 + k];
+            if (it.l[i0 + k]) b.lmap[k] = *it.l[i0 + k];
+            if (it.s[i0 + k]) b.smap[k] = *it.s[i0 + k];
         }
+        cudaError_t e;
+        switch (pass) {
+            case PASS_XFWD: e = pm_launch_xfwd<T>(b, st); break;
+            case PASS_YFWD: e = pm_launch_col<T>(b, COL_YFWD, st); break;
+            case PASS_ZCONV: e = pm_launch_col<T>(b, COL_ZCONV, st); break;
+            case PASS_YINV: e = pm_launch_col<T>(b, COL_YINV, st); break;
+            default: e = pm_launch_xinv<T>(b, st); break;
+        }
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// One pass of every pair of the units (only >= 0: of unit `only`); a
+// unit's pairs share each pass's launches when the context batches (the
+// pairs of a unit then have one shape).  A grid 1 pair (diff) takes part in
+// the forward passes like any other; its z pass runs twice (H-hat
+// (D_x + i D_y) into work2, then H-hat (D_z + i) in place), and its inverse
+// passes run on both work arrays: fx + i fy -> fx, fy; fz + i Phi_1 -> fz,
+// Phi_1.
+template <typename T> int launch_pass(pm_ctx *c, int pass, cudaStream_t st, int only = -1, int shift = INT_MIN) {
+    const size_t chunk = c->batched ? PM_BATCH : 1;
+    for (int ui = 0; ui < (int)c->units.size(); ++ui) {
+        if (only >= 0 && ui != only) continue;
+        BatchItems main, d1, d2;
+        for (int gi : c->units[ui]) {
+            const GeoBuf &gb = c->geos[gi];
+            const pm_geometry &sg = gb.g;
+            for (const Pair &pr : gb.pairs) {
+                PairArgs a = pair_args(c, gb, pr, shift);
+                switch (pass) {
+                    case PASS_XFWD:
+                        a.tw = c->d_tw[tw_index(2 * sg.nx)];
+                        main.add(a);
+                        break;
+                    case PASS_YFWD:
+                        a.tw = c->d_tw[tw_index(2 * sg.ny)];
+                        main.add(a, &pr.yfwd);
+                        break;
+                    case PASS_ZCONV:
+                        a.tw = c->d_tw[tw_index(2 * sg.nz)];
+                        if (!pr.diff) {
+                            main.add(a, &pr.zmap);
+                        } else {
+                            a.dmode = 1;
+                            d1.add(a, &pr.zmap, &pr.zmap2);
+                            a.dmode = 2;
+                            d2.add(a, &pr.zmap);
+                        }
+                        break;
+                    case PASS_YINV:
+                        a.tw = c->d_tw[tw_index(2 * sg.ny)];
+                        main.add(a, &pr.yinv);
+                        if (pr.diff) {
+                            a.work = pr.work2;
+                            main.add(a, &pr.yinv2);
+                        }
+                        break;
+                    default:
+                        a.tw = c->d_tw[tw_index(2 * sg.nx)];
+                        if (pr.diff) {
+                            a.split = 1;
+                            a.phi_sum = c->fd[pr.gi][2];
+                            a.phi_b = c->phi[pr.gi][pr.a];
+                            main.add(a);
+                            a.work = pr.work2;
+                            a.phi_sum = c->fd[pr.gi][0];
+                            a.phi_b = c->fd[pr.gi][1];
+                        }
+                        main.add(a);
+                        break;
+                }
+            }
+        }
+        cudaError_t e = launch_items<T>(pass, main, chunk, st);
+        if (e == cudaSuccess) e = launch_items<T>(pass, d1, chunk, st);
+        if (e == cudaSuccess) e = launch_items<T>(pass, d2, chunk, st);
+        if (e != cudaSuccess) return fail(PM_E_CUDA, "FFT pass %d launch failed: %s", pass, cudaGetErrorString(e));
     }
     return PM_OK;
 }
 
 // With ev (phase timing) the passes run pass by pass on st.  Otherwise the
-// geometries' chains of five passes run on branch streams forked from and
-// joined back to st, by one of two schedules (timed at creation, the faster
-// kept): one branch per geometry, all chains starting together; or two
-// lanes of about equal work, one taking its chains largest first and the
-// other smallest first, so that the compute-bound z pass of one large chain
-// meets the bandwidth-bound x and y passes of another rather than its own z
-// pass.
+// units' chains of five passes run on branch streams forked from and joined
+// back to st, by one of two schedules (timed at creation with and without
+// batching, the fastest kept): one branch per unit, all chains starting
+// together; or two lanes of about equal work, one taking its chains largest
+// first and the other smallest first, so that the compute-bound z pass of
+// one large chain meets the bandwidth-bound x and y passes of another rather
+// than its own z pass.
 template <typename T> int enqueue_solve(pm_ctx *c, cudaStream_t st, cudaEvent_t *ev, int shift = INT_MIN) {
-    if (ev || c->geos.size() < 2) {
+    if (ev || c->units.size() < 2) {
         for (int pass = 0; pass < NPASS; ++pass) {
             PM_TRY(launch_pass<T>(c, pass, st, -1, shift));
             if (ev) PM_CK(cudaEventRecord(ev[pass], st));
@@ -408,7 +466,7 @@ template <typename T> int enqueue_solve(pm_ctx *c, cudaStream_t st, cudaEvent_t 
     }
     PM_CK(cudaEventRecord(c->ev_fork, st));
     if (c->sched == 0) {
-        for (int gi = 0; gi < (int)c->geos.size(); ++gi) {
+        for (int gi = 0; gi < (int)c->units.size(); ++gi) {
             cudaStream_t b = c->branch[gi];
             PM_CK(cudaStreamWaitEvent(b, c->ev_fork, 0));
             for (int pass = 0; pass < NPASS; ++pass) PM_TRY(launch_pass<T>(c, pass, b, gi, shift));
@@ -428,15 +486,19 @@ template <typename T> int enqueue_solve(pm_ctx *c, cudaStream_t st, cudaEvent_t 
     return PM_OK;
 }
 
-// Two lanes of about equal transform volume: chains taken largest first, the
-// first to lane 0, each next one to the lighter lane (lane 1 on ties); lane 0
-// runs largest first, lane 1 smallest first, so lane 1's large chains start
-// after its small ones.
-std::vector<std::vector<int>> plan_lanes(const std::vector<GeoBuf> &geos) {
+// Two lanes of about equal transform volume: the units' chains taken
+// largest first, the first to lane 0, each next one to the lighter lane
+// (lane 1 on ties); lane 0 runs largest first, lane 1 smallest first, so
+// lane 1's large chains start after its small ones.
+std::vector<std::vector<int>> plan_lanes(const std::vector<std::vector<int>> &units, const std::vector<GeoBuf> &geos) {
     std::vector<std::pair<double, int>> w;
-    for (int gi = 0; gi < (int)geos.size(); ++gi) {
-        const pm_geometry &g = geos[gi].g;
-        w.push_back({8.0 * g.nx * g.ny * g.nz * (double)geos[gi].pairs.size(), gi});
+    for (int ui = 0; ui < (int)units.size(); ++ui) {
+        double vol = 0;
+        for (int gi : units[ui]) {
+            const pm_geometry &g = geos[gi].g;
+            vol += 8.0 * g.nx * g.ny * g.nz * (double)geos[gi].pairs.size();
+        }
+        w.push_back({vol, ui});
     }
     std::sort(w.begin(), w.end(), [](const std::pair<double, int> &a, const std::pair<double, int> &b) {
         return a.first != b.first ? a.first > b.first : a.second < b.second;
@@ -453,9 +515,22 @@ std::vector<std::vector<int>> plan_lanes(const std::vector<GeoBuf> &geos) {
     return lanes;
 }
 
-// Times each schedule (one warm-up solve, then five between events, on
-// zeroed densities) and keeps the faster.
+// Units of the solve: shapes (batched) or single geometries.
+void set_units(pm_ctx *c, bool batched) {
+    c->batched = batched;
+    c->units.clear();
+    if (batched) {
+        for (const ShapeGroup &sg : c->shapes) c->units.push_back(sg.geos);
+    } else {
+        for (int gi = 0; gi < (int)c->geos.size(); ++gi) c->units.push_back({gi});
+    }
+    c->lanes = plan_lanes(c->units, c->geos);
+}
+
+// Times each solve schedule (one warm-up solve, then five between events,
+// on zeroed densities) with and without batching, and keeps the fastest.
 template <typename T> int tune_schedule(pm_ctx *c) {
+    set_units(c, true);
     c->sched = 0;
     if (c->geos.size() < 2) return PM_OK;
     PM_CK(cudaMemsetAsync(c->rho_all, 0, c->rho_bytes, c->user));
@@ -463,21 +538,32 @@ template <typename T> int tune_schedule(pm_ctx *c) {
     PM_CK(cudaEventCreate(&e0));
     PM_CK(cudaEventCreate(&e1));
     float best = 0.f;
-    int best_s = 0;
+    int best_s = 0, best_b = 1;
+    bool first = true;
     int rc = PM_OK;
-    for (int sc = 0; sc < 2 && rc == PM_OK; ++sc) {
-        c->sched = sc;
-        rc = enqueue_solve<T>(c, c->user, nullptr);
-        if (rc == PM_OK && cudaEventRecord(e0, c->user) != cudaSuccess) rc = fail(PM_E_CUDA, "event record failed");
-        for (int k = 0; k < 5 && rc == PM_OK; ++k) rc = enqueue_solve<T>(c, c->user, nullptr);
-        if (rc == PM_OK && cudaEventRecord(e1, c->user) != cudaSuccess) rc = fail(PM_E_CUDA, "event record failed");
-        float ms = 0.f;
-        if (rc == PM_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
-            rc = fail(PM_E_CUDA, "schedule timing failed");
-        if (rc == PM_OK && (sc == 0 || ms < best)) { best = ms; best_s = sc; }
+    for (int bt = 1; bt >= 0 && rc == PM_OK; --bt) {
+        set_units(c, bt != 0);
+        for (int sc = 0; sc < (c->units.size() < 2 ? 1 : 2) && rc == PM_OK; ++sc) {
+            c->sched = sc;
+            rc = enqueue_solve<T>(c, c->user, nullptr);
+            if (rc == PM_OK && cudaEventRecord(e0, c->user) != cudaSuccess) rc = fail(PM_E_CUDA, "event record failed");
+            for (int k = 0; k < 5 && rc == PM_OK; ++k) rc = enqueue_solve<T>(c, c->user, nullptr);
+            if (rc == PM_OK && cudaEventRecord(e1, c->user) != cudaSuccess) rc = fail(PM_E_CUDA, "event record failed");
+            float ms = 0.f;
+            if (rc == PM_OK &&
+                (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                rc = fail(PM_E_CUDA, "schedule timing failed");
+            if (rc == PM_OK && (first || ms < best)) {
+                best = ms;
+                best_s = sc;
+                best_b = bt;
+                first = false;
+            }
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    set_units(c, best_b != 0);
     c->sched = best_s;
     if (rc != PM_OK) return rc;
     return check_device_error(c);
@@ -875,6 +961,16 @@ int pm_encode_col_maps(void *work, int nx, int ny, int nz, int esz, CUtensorMap 
     return PM_OK;
 }
 
+PassBatch pm_single_batch(const PairArgs &a, const CUtensorMap *lmap, const CUtensorMap *smap) {
+    PassBatch b;
+    std::memset(&b, 0, sizeof(b));
+    b.n = 1;
+    b.a[0] = a;
+    if (lmap) b.lmap[0] = *lmap;
+    if (smap || lmap) b.smap[0] = smap ? *smap : *lmap;
+    return b;
+}
+
 int pm_internal_fail(int code, const char *msg) {
     g_err = msg;
     return code;
@@ -1040,7 +1136,18 @@ int pm_create_grids(const pm_system *sys, const pm_galaxy *gals, void *stream, p
         }
     if (cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess)
         return cleanup(fail(PM_E_CUDA, "cudaEventCreate failed"));
-    c->lanes = plan_lanes(c->geos);
+    for (int gi = 0; gi < (int)c->geos.size(); ++gi) {   // shapes: geometries of equal cell counts
+        const pm_geometry &g = c->geos[gi].g;
+        int si = -1;
+        for (int k = 0; k < (int)c->shapes.size(); ++k)
+            if (c->shapes[k].nx == g.nx && c->shapes[k].ny == g.ny && c->shapes[k].nz == g.nz) si = k;
+        if (si < 0) {
+            c->shapes.push_back(ShapeGroup{g.nx, g.ny, g.nz, {}});
+            si = (int)c->shapes.size() - 1;
+        }
+        c->shapes[si].geos.push_back(gi);
+    }
+    set_units(c, true);
     for (size_t l = 0; l < std::max<size_t>(c->geos.size(), 2); ++l) {
         cudaStream_t b;
         cudaEvent_t e;
@@ -1373,7 +1480,8 @@ int pm_info(pm_ctx *c, int64_t *out) {
     out[1] = nsets;
     out[2] = (int64_t)c->geos.size();
     out[3] = (int64_t)c->bytes;
-    out[4] = c->geos.size() < 2 ? -1 : c->sched;
+    out[4] = c->units.size() < 2 ? -1 : c->sched;
+    out[5] = c->batched ? 1 : 0;
     return PM_OK;
 }
 

@@ -748,45 +748,50 @@ cudaError_t launch_pdl(void (*k)(KArgs...), unsigned grid, unsigned block, size_
     return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
 }
 
-template <typename T, int L> cudaError_t xfwd_L(const PairArgs &a, cudaStream_t st) {
+inline int ilog2(long long v) {
+    int l = 0;
+    while ((1LL << l) < v) ++l;
+    return l;
+}
+template <typename T, int L> cudaError_t xfwd_L(PassBatch b, cudaStream_t st) {
     static int nb = resident_blocks(pmk::k_xfwd<T, L>, pmk::NT, pmk::xpass_smem<T, L>());
-    const long long groups = ((long long)a.ny * a.nz + pmk::XShape<L>::LINES - 1) / pmk::XShape<L>::LINES;
-    const long long grid = std::min(groups, (long long)nb * num_sms());
-    return launch_pdl(pmk::k_xfwd<T, L>, (unsigned)grid, pmk::NT, pmk::xpass_smem<T, L>(), st, a);
+    const long long gpi = std::max(1LL, (long long)b.a[0].ny * b.a[0].nz / pmk::XShape<L>::LINES);
+    b.lgi = ilog2(gpi);
+    const long long grid = std::min((long long)b.n << b.lgi, (long long)nb * num_sms());
+    return launch_pdl(pmk::k_xfwd<T, L>, (unsigned)grid, pmk::NT, pmk::xpass_smem<T, L>(), st, b);
 }
-template <typename T, int L> cudaError_t xinv_L(const PairArgs &a, cudaStream_t st) {
+template <typename T, int L> cudaError_t xinv_L(PassBatch b, cudaStream_t st) {
     static int nb = resident_blocks(pmk::k_xinv<T, L>, pmk::NT, pmk::xpass_smem<T, L>());
-    const long long groups = ((long long)a.ny * a.nz + pmk::XShape<L>::LINES - 1) / pmk::XShape<L>::LINES;
-    const long long grid = std::min(groups, (long long)nb * num_sms());
-    return launch_pdl(pmk::k_xinv<T, L>, (unsigned)grid, pmk::NT, pmk::xpass_smem<T, L>(), st, a);
+    const long long gpi = std::max(1LL, (long long)b.a[0].ny * b.a[0].nz / pmk::XShape<L>::LINES);
+    b.lgi = ilog2(gpi);
+    const long long grid = std::min((long long)b.n << b.lgi, (long long)nb * num_sms());
+    return launch_pdl(pmk::k_xinv<T, L>, (unsigned)grid, pmk::NT, pmk::xpass_smem<T, L>(), st, b);
 }
-template <typename T, int L, int MODE> cudaError_t col_LM(const PairArgs &a, const CUtensorMap &map, cudaStream_t st) {
+template <typename T, int L, int MODE> cudaError_t col_LM(PassBatch b, cudaStream_t st) {
     constexpr int COLS = pmk::CShape<T, L>::COLS;
-    const long long ntiles = (long long)a.nz * ((2 * a.nx + COLS - 1) / COLS);
+    b.lgi = ilog2((long long)b.a[0].nz * ((2 * b.a[0].nx + COLS - 1) / COLS));
+    const long long ntiles = (long long)b.n << b.lgi;
     long long grid = (long long)col_blocks_per_sm<T, L, MODE>() * num_sms();
     if (grid > ntiles) grid = ntiles;
     if (grid < 1) grid = 1;
     return launch_pdl(pmk::k_col<T, L, MODE>, (unsigned)grid, pmk::CShape<T, L>::THREADS,
-                      pmk::col_smem<T, L, MODE>(), st, a, map, ntiles);
+                      pmk::col_smem<T, L, MODE>(), st, b);
 }
-template <typename T, int L>
-cudaError_t zconv_L(const PairArgs &a, const CUtensorMap &lmap, const CUtensorMap &smap, cudaStream_t st) {
+template <typename T, int L> cudaError_t zconv_L(PassBatch b, cudaStream_t st) {
     typedef pmk::WShape<T, L> S;
-    const long long ntiles = ((long long)4 * a.ny * a.nx) / S::COLS;   // COLS divides the 2ny x 2nx columns
-    const bool dm = a.dmode != 0;
+    b.lgi = ilog2(((long long)4 * b.a[0].ny * b.a[0].nx) / S::COLS);   // COLS divides the 2ny x 2nx columns
+    const long long ntiles = (long long)b.n << b.lgi;
+    const bool dm = b.a[0].dmode != 0;
     long long grid = (long long)(dm ? colw_blocks_per_sm<T, L, 1>() : colw_blocks_per_sm<T, L, 0>()) * num_sms();
     if (grid > ntiles) grid = ntiles;
     if (grid < 1) grid = 1;
-    if (dm)
-        return launch_pdl(pmk::k_colw<T, L, 1>, (unsigned)grid, S::THREADS, pmk::colw_smem<T, L>(), st, a, lmap, smap,
-                          ntiles);
-    return launch_pdl(pmk::k_colw<T, L, 0>, (unsigned)grid, S::THREADS, pmk::colw_smem<T, L>(), st, a, lmap, smap,
-                      ntiles);
+    if (dm) return launch_pdl(pmk::k_colw<T, L, 1>, (unsigned)grid, S::THREADS, pmk::colw_smem<T, L>(), st, b);
+    return launch_pdl(pmk::k_colw<T, L, 0>, (unsigned)grid, S::THREADS, pmk::colw_smem<T, L>(), st, b);
 }
-template <typename T, int L> cudaError_t col_L(const PairArgs &a, const CUtensorMap &map, int mode, cudaStream_t st) {
-    if (mode == COL_YFWD) return col_LM<T, L, COL_YFWD>(a, map, st);
-    if (mode == COL_ZCONV) return zconv_L<T, L>(a, map, map, st);
-    return col_LM<T, L, COL_YINV>(a, map, st);
+template <typename T, int L> cudaError_t col_L(const PassBatch &b, int mode, cudaStream_t st) {
+    if (mode == COL_YFWD) return col_LM<T, L, COL_YFWD>(b, st);
+    if (mode == COL_ZCONV) return zconv_L<T, L>(b, st);
+    return col_LM<T, L, COL_YINV>(b, st);
 }
 
 #define PM_SWITCH_L(L, CALL)                          \
@@ -812,28 +817,24 @@ template <typename T> cudaError_t pm_set_attrs() {
     return pmk_host::attrs_L<T, 512>();
 }
 
-template <typename T> cudaError_t pm_launch_xfwd(const PairArgs &a, cudaStream_t st) {
-#define PM_XF(LL) pmk_host::xfwd_L<T, LL>(a, st)
-    PM_SWITCH_L(2 * a.nx, PM_XF)
+template <typename T> cudaError_t pm_launch_xfwd(PassBatch b, cudaStream_t st) {
+    if (b.n < 1 || b.n > PM_BATCH) return cudaErrorInvalidValue;
+#define PM_XF(LL) pmk_host::xfwd_L<T, LL>(b, st)
+    PM_SWITCH_L(2 * b.a[0].nx, PM_XF)
 #undef PM_XF
 }
-template <typename T> cudaError_t pm_launch_xinv(const PairArgs &a, cudaStream_t st) {
-#define PM_XI(LL) pmk_host::xinv_L<T, LL>(a, st)
-    PM_SWITCH_L(2 * a.nx, PM_XI)
+template <typename T> cudaError_t pm_launch_xinv(PassBatch b, cudaStream_t st) {
+    if (b.n < 1 || b.n > PM_BATCH) return cudaErrorInvalidValue;
+#define PM_XI(LL) pmk_host::xinv_L<T, LL>(b, st)
+    PM_SWITCH_L(2 * b.a[0].nx, PM_XI)
 #undef PM_XI
 }
-template <typename T> cudaError_t pm_launch_col(const PairArgs &a, const CUtensorMap &map, int mode, cudaStream_t st) {
-    const int L = (mode == COL_ZCONV) ? 2 * a.nz : 2 * a.ny;
-#define PM_CO(LL) pmk_host::col_L<T, LL>(a, map, mode, st)
+template <typename T> cudaError_t pm_launch_col(PassBatch b, int mode, cudaStream_t st) {
+    if (b.n < 1 || b.n > PM_BATCH) return cudaErrorInvalidValue;
+    const int L = (mode == COL_ZCONV) ? 2 * b.a[0].nz : 2 * b.a[0].ny;
+#define PM_CO(LL) pmk_host::col_L<T, LL>(b, mode, st)
     PM_SWITCH_L(L, PM_CO)
 #undef PM_CO
-}
-
-template <typename T>
-cudaError_t pm_launch_zconv(const PairArgs &a, const CUtensorMap &lmap, const CUtensorMap &smap, cudaStream_t st) {
-#define PM_ZC(LL) pmk_host::zconv_L<T, LL>(a, lmap, smap, st)
-    PM_SWITCH_L(2 * a.nz, PM_ZC)
-#undef PM_ZC
 }
 
 template <typename T>
@@ -913,11 +914,9 @@ cudaError_t pm_store_hhat(const double *oct, T *out, int nx, int ny, int nz, dou
 
 #define PM_INSTANTIATE(T)                                                                                       \
     template cudaError_t pm_set_attrs<T>();                                                                    \
-    template cudaError_t pm_launch_xfwd<T>(const PairArgs &, cudaStream_t);                                   \
-    template cudaError_t pm_launch_xinv<T>(const PairArgs &, cudaStream_t);                                   \
-    template cudaError_t pm_launch_col<T>(const PairArgs &, const CUtensorMap &, int, cudaStream_t);          \
-    template cudaError_t pm_launch_zconv<T>(const PairArgs &, const CUtensorMap &, const CUtensorMap &,       \
-                                            cudaStream_t);                                                     \
+    template cudaError_t pm_launch_xfwd<T>(PassBatch, cudaStream_t);                                          \
+    template cudaError_t pm_launch_xinv<T>(PassBatch, cudaStream_t);                                          \
+    template cudaError_t pm_launch_col<T>(PassBatch, int, cudaStream_t);                                      \
     template cudaError_t pm_launch_deposit<T>(const PartK<T> &, const SysK &, const CenK *, int, cudaStream_t); \
     template cudaError_t pm_launch_force<T>(int, const PartK<T> &, const SysK &, const CenK *, double, T *, T *, \
                                             T *, double *, cudaStream_t);                                      \

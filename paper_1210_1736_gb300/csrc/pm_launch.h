@@ -31,6 +31,23 @@ struct PairArgs {
 
 enum { COL_YFWD = 0, COL_ZCONV = 1, COL_YINV = 2 };
 
+// One launch of an FFT pass over up to PM_BATCH items: work arrays of the
+// same shape (nx, ny, nz), e.g. the grids of the same size of every galaxy
+// (Sec. 2.1: all galaxies use the same kinds of grid).  Each item has its own
+// arrays, H-hat table and tensor maps (lmap: the column passes' loads; smap:
+// the z pass's stores); the launch walks the items' tiles (or x-pass row
+// groups) as one index space, 2^lgi per item (set by the launcher).
+#ifndef PM_BATCH
+#define PM_BATCH 8
+#endif
+struct PassBatch {
+    CUtensorMap lmap[PM_BATCH];
+    CUtensorMap smap[PM_BATCH];
+    PairArgs a[PM_BATCH];
+    int n;
+    int lgi;
+};
+
 // Columns per tile of the column passes for transform length L and real
 // size esz: 16 threads per column, 256 threads per block, and a tensor-map
 // box row of at most 256 eight-byte elements.
@@ -53,15 +70,16 @@ int pm_encode_col_maps(void *work, int nx, int ny, int nz, int esz, CUtensorMap 
                        CUtensorMap *zmap);
 
 template <typename T> cudaError_t pm_set_attrs();
-template <typename T> cudaError_t pm_launch_xfwd(const PairArgs &a, cudaStream_t st);
-// Column pass `mode` with its tensor map (y forward: yfwd, z: zmap, y
-// inverse: yinv).
-template <typename T> cudaError_t pm_launch_col(const PairArgs &a, const CUtensorMap &map, int mode, cudaStream_t st);
-// z pass reading tiles through lmap and writing them through smap (maps of
-// two work arrays of the same shape; the same map for an in-place pass).
-template <typename T>
-cudaError_t pm_launch_zconv(const PairArgs &a, const CUtensorMap &lmap, const CUtensorMap &smap, cudaStream_t st);
-template <typename T> cudaError_t pm_launch_xinv(const PairArgs &a, cudaStream_t st);
+// Batched passes: x forward, column pass `mode` (y forward through lmap =
+// the items' yfwd maps, y inverse through their yinv maps, z through lmap
+// for loads and smap for stores: the same map in place, another work
+// array's for the first difference-field pass), x inverse.  Every item of a
+// batch has the same shape, precision and, in the z pass, dmode.
+template <typename T> cudaError_t pm_launch_xfwd(PassBatch b, cudaStream_t st);
+template <typename T> cudaError_t pm_launch_col(PassBatch b, int mode, cudaStream_t st);
+template <typename T> cudaError_t pm_launch_xinv(PassBatch b, cudaStream_t st);
+// A batch of one item (a pair's arrays and its maps; smap = lmap if null).
+PassBatch pm_single_batch(const PairArgs &a, const CUtensorMap *lmap, const CUtensorMap *smap);
 
 template <typename T>
 cudaError_t pm_launch_deposit(const PartK<T> &p, const SysK &sk, const CenK *cen, int aggregate, cudaStream_t st);

@@ -61,7 +61,7 @@ template <typename T, int L> constexpr size_t xpass_smem() {
 // L = 2nx, all L outputs written to the row of the work array.  Persistent:
 // each block walks groups of LINES rows (the twiddle tables are built once).
 template <typename T, int L>
-__global__ void __launch_bounds__(NT) k_xfwd(PairArgs a) {
+__global__ void __launch_bounds__(NT) k_xfwd(const __grid_constant__ PassBatch B) {
     typedef typename cplx_t<T>::type C;
     typedef XShape<L> S;
     constexpr int NX = L / 2, NS = nstages(L);
@@ -69,19 +69,35 @@ __global__ void __launch_bounds__(NT) k_xfwd(PairArgs a) {
     C *tw = reinterpret_cast<C *>(smraw);
     C *sm = tw + pmfft::tw_total(L);
     const int tid = threadIdx.x, line = tid / S::TPC, t = tid % S::TPC;
-    pmfft::expand_twiddles<L>(tw, static_cast<const C *>(a.tw));
+    // the shape, twiddles and scale are the items' common ones; every field
+    // is read into a register once (the stores below could otherwise make
+    // the compiler reload them)
+    const int ny = B.a[0].ny, lgi = B.lgi;
+    // the items' arrays, copied once into shared memory (a parameter array
+    // indexed at run time is read through slow generic loads)
+    __shared__ const void *ip[PM_BATCH][3];
+    if (tid < B.n) {
+        ip[tid][0] = B.a[tid].rho_a;
+        ip[tid][1] = B.a[tid].rho_b;
+        ip[tid][2] = B.a[tid].work;
+    }
+    pmfft::expand_twiddles<L>(tw, static_cast<const C *>(B.a[0].tw));
     __syncthreads();
     pdl_wait();
-    const long long nrows = (long long)a.ny * a.nz;
-    const long long ngroups = (nrows + S::LINES - 1) / S::LINES;
-    const int lny = __ffs(a.ny) - 1;   // row r = z*ny + y; ny is a power of two
-    const T scale = (T)a.scale;
+    const long long nrows = (long long)ny * B.a[0].nz;
+    const long long ngroups = (long long)B.n << lgi;   // row groups of every item
+    const int lny = __ffs(ny) - 1;   // row r = z*ny + y; ny is a power of two
+    const T scale = (T)B.a[0].scale;
     for (long long grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
         if (grp + gridDim.x >= ngroups) pdl_release();
-        const long long r = grp * S::LINES + line;
+        const int item = (int)(grp >> lgi);
+        const long long *rho_a = static_cast<const long long *>(ip[item][0]);
+        const long long *rho_b = static_cast<const long long *>(ip[item][1]);
+        C *work = static_cast<C *>(const_cast<void *>(ip[item][2]));
+        const long long r = (grp & ((1LL << lgi) - 1)) * S::LINES + line;
         const bool valid = r < nrows;
-        const long long *ra = a.rho_a + (valid ? r * NX : 0);
-        const long long *rb = a.rho_b ? a.rho_b + (valid ? r * NX : 0) : nullptr;
+        const long long *ra = rho_a + (valid ? r * NX : 0);
+        const long long *rb = rho_b ? rho_b + (valid ? r * NX : 0) : nullptr;
         C v[E];
         constexpr int R0 = radix(L, 0, false);
 #pragma unroll
@@ -91,8 +107,8 @@ __global__ void __launch_bounds__(NT) k_xfwd(PairArgs a) {
                 C val = czero<C>();
                 if (valid && q < R0 / 2) {   // inputs x >= nx are the zero padding
                     const int x = pmfft::in_row<L, 0, false>(t, kk, q);
-                    val.x = (T)ra[x] * scale;
-                    if (rb) val.y = (T)rb[x] * scale;
+                    val.x = (T)__ldg(ra + x) * scale;
+                    if (rb) val.y = (T)__ldg(rb + x) * scale;
                 }
                 v[kk * R0 + q] = val;
             }
@@ -100,13 +116,13 @@ __global__ void __launch_bounds__(NT) k_xfwd(PairArgs a) {
         // exchange row is private: the exchanges synchronise the warp only
         pmfft::fft_core<L, false, -1, true, false, true>(v, sm, pmfft::RowLayout{line * S::LDR}, t, tw);
         if (valid) {
-            const long long z = r >> lny, y = r & (a.ny - 1);
-            C *out = static_cast<C *>(a.work) + ((size_t)z * 2 * a.ny + y) * L;
+            const long long z = r >> lny, y = r & (ny - 1);
+            C *out = work + ((size_t)z * 2 * ny + y) * L;
             constexpr int RL = radix(L, NS - 1, false);
 #pragma unroll
             for (int kk = 0; kk < E / RL; ++kk)
 #pragma unroll
-                for (int q = 0; q < RL; ++q) out[pmfft::in_row<L, NS - 1, false>(t, kk, q)] = v[kk * RL + q];
+                for (int q = 0; q < RL; ++q) __stcg(out + pmfft::in_row<L, NS - 1, false>(t, kk, q), v[kk * RL + q]);
         }
     }
 }
@@ -115,7 +131,7 @@ __global__ void __launch_bounds__(NT) k_xfwd(PairArgs a) {
 // Phi_b = Im, Phi_sum = Re + Im (or Re without partner; with a.split,
 // Phi_sum = Re and Phi_b = Im).  Persistent as k_xfwd.
 template <typename T, int L>
-__global__ void __launch_bounds__(NT) k_xinv(PairArgs a) {
+__global__ void __launch_bounds__(NT) k_xinv(const __grid_constant__ PassBatch B) {
     typedef typename cplx_t<T>::type C;
     typedef XShape<L> S;
     constexpr int NX = L / 2, NS = nstages(L);
@@ -123,29 +139,42 @@ __global__ void __launch_bounds__(NT) k_xinv(PairArgs a) {
     C *tw = reinterpret_cast<C *>(smraw);
     C *sm = tw + pmfft::tw_total(L);
     const int tid = threadIdx.x, line = tid / S::TPC, t = tid % S::TPC;
-    pmfft::expand_twiddles<L>(tw, static_cast<const C *>(a.tw));
+    const int ny = B.a[0].ny, lgi = B.lgi;   // common to the items; read once (see k_xfwd)
+    __shared__ void *ip[PM_BATCH][3];
+    __shared__ int isplit[PM_BATCH];
+    if (tid < B.n) {
+        ip[tid][0] = B.a[tid].phi_b;
+        ip[tid][1] = B.a[tid].phi_sum;
+        ip[tid][2] = B.a[tid].work;
+        isplit[tid] = B.a[tid].split;
+    }
+    pmfft::expand_twiddles<L>(tw, static_cast<const C *>(B.a[0].tw));
     __syncthreads();
     pdl_wait();
-    const long long nrows = (long long)a.ny * a.nz;
-    const long long ngroups = (nrows + S::LINES - 1) / S::LINES;
-    const int lny = __ffs(a.ny) - 1;   // row r = z*ny + y; ny is a power of two
-    T *phi_b = static_cast<T *>(a.phi_b);
+    const long long nrows = (long long)ny * B.a[0].nz;
+    const long long ngroups = (long long)B.n << lgi;
+    const int lny = __ffs(ny) - 1;   // row r = z*ny + y; ny is a power of two
     for (long long grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
         if (grp + gridDim.x >= ngroups) pdl_release();
-        const long long r = grp * S::LINES + line;
+        const int item = (int)(grp >> lgi);
+        T *phi_b = static_cast<T *>(ip[item][0]);
+        T *phi_sum = static_cast<T *>(ip[item][1]);
+        const bool split = isplit[item] != 0;
+        const C *work = static_cast<const C *>(ip[item][2]);
+        const long long r = (grp & ((1LL << lgi) - 1)) * S::LINES + line;
         const bool valid = r < nrows;
-        const long long z = valid ? r >> lny : 0, y = valid ? r & (a.ny - 1) : 0;
-        const C *in = static_cast<const C *>(a.work) + ((size_t)z * 2 * a.ny + y) * L;
+        const long long z = valid ? r >> lny : 0, y = valid ? r & (ny - 1) : 0;
+        const C *in = work + ((size_t)z * 2 * ny + y) * L;
         C v[E];
         constexpr int R0 = radix(L, 0, true);
 #pragma unroll
         for (int kk = 0; kk < E / R0; ++kk)
 #pragma unroll
             for (int q = 0; q < R0; ++q)
-                v[kk * R0 + q] = valid ? in[pmfft::in_row<L, 0, true>(t, kk, q)] : czero<C>();
+                v[kk * R0 + q] = valid ? __ldg(in + pmfft::in_row<L, 0, true>(t, kk, q)) : czero<C>();
         pmfft::fft_core<L, true, 1, false, true, true>(v, sm, pmfft::RowLayout{line * S::LDR}, t, tw);
         if (valid) {
-            T *phi_s = static_cast<T *>(a.phi_sum) + r * NX;
+            T *phi_s = phi_sum + r * NX;
             constexpr int RL = radix(L, NS - 1, true);
 #pragma unroll
             for (int kk = 0; kk < E / RL; ++kk)
@@ -153,14 +182,15 @@ __global__ void __launch_bounds__(NT) k_xinv(PairArgs a) {
                 for (int q = 0; q < RL / 2; ++q) {   // outputs x < nx: registers q < 8 of the radix-16 last stage
                     const int x = pmfft::in_row<L, NS - 1, true>(t, kk, q);
                     const C val = v[kk * RL + q];
-                    if (a.split) {
-                        phi_s[x] = val.x;
-                        phi_b[r * NX + x] = val.y;
+                    // the arrays are global memory (pointers read from shared memory: say so)
+                    if (split) {
+                        __stcg(phi_s + x, val.x);
+                        __stcg(phi_b + r * NX + x, val.y);
                     } else if (phi_b) {
-                        phi_b[r * NX + x] = val.y;
-                        phi_s[x] = val.x + val.y;
+                        __stcg(phi_b + r * NX + x, val.y);
+                        __stcg(phi_s + x, val.x + val.y);
                     } else {
-                        phi_s[x] = val.x;
+                        __stcg(phi_s + x, val.x);
                     }
                 }
         }
@@ -256,12 +286,12 @@ template <typename T, int L, int MODE> constexpr size_t col_smem() {
            2 * (size_t)ColRows<MODE>::of(L) * COLS * sizeof(C) + 3 * 128;
 }
 
-// Persistent y pass (forward or inverse).  map: 2D tensor map over 8-byte
-// elements whose box is (COLS * EPC, min(rows, 256)); tile t covers COLS
-// columns of one z plane.
+// Persistent y pass (forward or inverse) over a batch: the items' maps
+// B.lmap are 2D tensor maps over 8-byte elements whose box is
+// (COLS * EPC, min(rows, 256)); an item's tile covers COLS columns of one z
+// plane.
 template <typename T, int L, int MODE>
-__global__ void __launch_bounds__(CShape<T, L>::THREADS, 3) k_col(PairArgs a, const __grid_constant__ CUtensorMap map,
-                                                               long long ntiles) {
+__global__ void __launch_bounds__(CShape<T, L>::THREADS, 3) k_col(const __grid_constant__ PassBatch B) {
     typedef typename cplx_t<T>::type C;
     typedef CShape<T, L> S;
     constexpr int COLS = S::COLS, NS = nstages(L), ROWS = ColRows<MODE>::of(L);
@@ -279,32 +309,38 @@ __global__ void __launch_bounds__(CShape<T, L>::THREADS, 3) k_col(PairArgs a, co
     C *tw = sm + L * COLS;
     const int tid = threadIdx.x;
     const int c = tid % COLS, t = tid / COLS;
-    C *work = static_cast<C *>(a.work);
-    const int nx2 = 2 * a.nx, ny2 = 2 * a.ny;
+    const int nx2 = 2 * B.a[0].nx, ny2 = 2 * B.a[0].ny;   // the items' common shape, read once
+    int *const err = B.a[0].err;
     const long long tiles_per_z = (nx2 + COLS - 1) / COLS;   // a power of two, as nx2 and COLS
     const int ltpz = __ffs((int)tiles_per_z) - 1;
+    const long long ntiles = (long long)B.n << B.lgi;
+    const long long lmask = (1LL << B.lgi) - 1;
 
-    // tile -> TMA coordinates and the first column it covers
-    auto coords = [&](long long tile, int &x, int &y) {
-        x = (int)((tile & (tiles_per_z - 1)) * COLS * S::EPC);
-        y = (int)((tile >> ltpz) * ny2);
+    // an item's tile -> TMA coordinates and the first column it covers
+    auto coords = [&](long long lt, int &x, int &y) {
+        x = (int)((lt & (tiles_per_z - 1)) * COLS * S::EPC);
+        y = (int)((lt >> ltpz) * ny2);
     };
     auto issue = [&](long long tile, int b) {
         int x, y;
-        coords(tile, x, y);
+        coords(tile & lmask, x, y);
+        const CUtensorMap *map = &B.lmap[tile >> B.lgi];
         C *dst = b ? buf1 : buf0;
         mbar_expect_tx(&bar[b], TILE_BYTES);
 #pragma unroll
-        for (int k = 0; k < NBOX; ++k) tma_load_2d(dst + k * BOXR * COLS, &map, x, y + k * BOXR, &bar[b]);
+        for (int k = 0; k < NBOX; ++k) tma_load_2d(dst + k * BOXR * COLS, map, x, y + k * BOXR, &bar[b]);
     };
 
+    __shared__ C *iwork[PM_BATCH];   // the items' work arrays (read once; see k_xfwd)
+    if (tid < B.n) iwork[tid] = static_cast<C *>(B.a[tid].work);
     if (tid == 0) {
-        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map)) : "memory");
+        for (int i = 0; i < B.n; ++i)
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&B.lmap[i])) : "memory");
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    pmfft::expand_twiddles<L>(tw, static_cast<const C *>(a.tw));
+    pmfft::expand_twiddles<L>(tw, static_cast<const C *>(B.a[0].tw));
     __syncthreads();
     pdl_wait();
     int issued[2] = {0, 0};   // loads issued per buffer (thread 0's count)
@@ -322,7 +358,7 @@ __global__ void __launch_bounds__(CShape<T, L>::THREADS, 3) k_col(PairArgs a, co
         // copy in flight, stop; the decision is the same for the whole block
         if (!__syncthreads_and(mbar_wait(&bar[b], phase) ? 1 : 0)) {
             if (tid == 0) {
-                atomicExch(a.err, 1);
+                atomicExch(err, 1);
                 const int o = b ^ 1, used_o = it >> 1;   // uses of buffer o completed so far
                 if (issued[o] > used_o) mbar_wait(&bar[o], (unsigned)(used_o & 1));
             }
@@ -351,10 +387,11 @@ __global__ void __launch_bounds__(CShape<T, L>::THREADS, 3) k_col(PairArgs a, co
         C *col;
         size_t stride;
         {
-            const long long z = tile >> ltpz, kx = (tile & (tiles_per_z - 1)) * COLS + c;
+            const long long lt = tile & lmask;
+            const long long z = lt >> ltpz, kx = (lt & (tiles_per_z - 1)) * COLS + c;
             q = kx;
             valid = kx < nx2;
-            col = work + (size_t)z * ny2 * nx2 + kx;
+            col = iwork[tile >> B.lgi] + (size_t)z * ny2 * nx2 + kx;
             stride = (size_t)nx2;
         }
 
@@ -368,7 +405,7 @@ __global__ void __launch_bounds__(CShape<T, L>::THREADS, 3) k_col(PairArgs a, co
                 for (int kk = 0; kk < E / RL; ++kk)
 #pragma unroll
                     for (int r = 0; r < RL; ++r)
-                        colt[(size_t)pmfft::in_row<L, NS - 1, false>(0, kk, r) * stride] = v[kk * RL + r];
+                        __stcg(colt + (size_t)pmfft::in_row<L, NS - 1, false>(0, kk, r) * stride, v[kk * RL + r]);
             }
             continue;
         }
@@ -381,7 +418,7 @@ __global__ void __launch_bounds__(CShape<T, L>::THREADS, 3) k_col(PairArgs a, co
             for (int kk = 0; kk < E / RL; ++kk)
 #pragma unroll
                 for (int r = 0; r < RL / 2; ++r)
-                    colt[(size_t)pmfft::in_row<L, NS - 1, true>(0, kk, r) * stride] = v[kk * RL + r];
+                    __stcg(colt + (size_t)pmfft::in_row<L, NS - 1, true>(0, kk, r) * stride, v[kk * RL + r]);
         }
     }
 }
@@ -461,16 +498,16 @@ __device__ __forceinline__ uint32_t woff(int row, int c) {
     return (uint32_t)(c / S::SW) * (uint32_t)(ROWS * S::P) + sw;
 }
 
-// map: boxes (SW*EPC, min(nz, 256)), for the loads; smap: the same boxes
-// for the stores (the same map in place, another work array's for the
-// first difference-field launch).  DM = 0: the spectral factor is H-hat;
-// DM = 1 (difference fields): H-hat (D_x + i D_y) for a.dmode 1, H-hat
-// (D_z + i) for a.dmode 2 (see PairArgs).  The modes are separate
-// instantiations so that the plain pass carries no mode branch.
+// Over a batch: B.lmap, the items' maps with boxes (SW*EPC, min(nz, 256)),
+// for the loads; B.smap, the same boxes, for the stores (the same map in
+// place, another work array's for the first difference-field pass).  DM = 0:
+// the spectral factor is H-hat; DM = 1 (difference fields): H-hat
+// (D_x + i D_y) for dmode 1, H-hat (D_z + i) for dmode 2 (see PairArgs).
+// The modes are separate instantiations so that the plain pass carries no
+// mode branch.
 template <typename T, int L, int DM>
 __global__ void __launch_bounds__(WShape<T, L>::THREADS, (L >= 512 ? 2 : 3))
-    k_colw(PairArgs a, const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap smap,
-           long long ntiles) {
+    k_colw(const __grid_constant__ PassBatch B) {
     typedef WShape<T, L> S;
     typedef typename S::C C;
     constexpr int NS = nstages(L), NWARPS = S::THREADS / 32;
@@ -486,30 +523,41 @@ __global__ void __launch_bounds__(WShape<T, L>::THREADS, (L >= 512 ? 2 : 3))
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int t = lane % S::TPC;
     const int c = warp * (32 / S::TPC) + lane / S::TPC;   // column within the tile
+    const PairArgs &a = B.a[0];   // the shape, tables and mode are the items' common ones
     const int nx2 = 2 * a.nx, ny2 = 2 * a.ny, lnx2 = __ffs(nx2) - 1;
+    // tile indices fit in 32 bits: at most 8 items of (2 * 256)^2 / COLS tiles
+    const int lgi = B.lgi, lmask = (1 << lgi) - 1;
 
-    // tile <-> sub-tiles of the buffer, each NBOXI boxes of BOXI rows
+    // an item's tile <-> sub-tiles of the buffer, each NBOXI boxes of BOXI rows
     auto issue_load = [&](int tile, int b) {
+        const CUtensorMap *map = &B.lmap[tile >> lgi];
+        const int lt = tile & lmask;
         mbar_expect_tx(&full[b], S::BUF);
 #pragma unroll
         for (int s = 0; s < S::NSUB; ++s)
 #pragma unroll
             for (int k = 0; k < S::NBOXI; ++k)
-                tma_load_2d(base + b * S::BUF + s * S::RIN * S::P + k * S::BOXI * S::P, &map,
-                            (int)((tile * S::COLS + s * S::SW) * S::EPC), k * S::BOXI, &full[b]);
+                tma_load_2d(base + b * S::BUF + s * S::RIN * S::P + k * S::BOXI * S::P, map,
+                            (int)((lt * S::COLS + s * S::SW) * S::EPC), k * S::BOXI, &full[b]);
     };
     auto issue_store = [&](int tile, const unsigned char *src) {
+        const CUtensorMap *smap = &B.smap[tile >> lgi];
+        const int lt = tile & lmask;
 #pragma unroll
         for (int s = 0; s < S::NSUB; ++s)
 #pragma unroll
             for (int k = 0; k < S::NBOXI; ++k)
-                tma_store_2d(&smap, (int)((tile * S::COLS + s * S::SW) * S::EPC), k * S::BOXI,
+                tma_store_2d(smap, (int)((lt * S::COLS + s * S::SW) * S::EPC), k * S::BOXI,
                              src + s * S::RIN * S::P + k * S::BOXI * S::P);
     };
 
+    __shared__ const T *ihhat[PM_BATCH];   // the items' H-hat tables (read once; see k_xfwd)
+    if (tid < B.n) ihhat[tid] = static_cast<const T *>(B.a[tid].hhat);
     if (tid == 0) {
-        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map)) : "memory");
-        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&smap)) : "memory");
+        for (int i = 0; i < B.n; ++i) {
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&B.lmap[i])) : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&B.smap[i])) : "memory");
+        }
         mbar_init(&full[0], 1);
         mbar_init(&full[1], 1);
         mbar_init(&staged[0], NWARPS);
@@ -531,7 +579,7 @@ __global__ void __launch_bounds__(WShape<T, L>::THREADS, (L >= 512 ? 2 : 3))
     // thread 0 issues every copy; counts per buffer of loads issued and of
     // tiles sent (to drain after an expired wait)
     int issued0 = 0, issued1 = 0, done0 = 0, done1 = 0;
-    const int nt0 = (int)ntiles;
+    const int nt0 = B.n << lgi;
     int deferred = -1;   // thread 0: tile whose buffer awaits its refill
     if (tid == 0) {
         if ((int)blockIdx.x < nt0) { issue_load(blockIdx.x, 0); ++issued0; }
@@ -541,8 +589,7 @@ __global__ void __launch_bounds__(WShape<T, L>::THREADS, (L >= 512 ? 2 : 3))
     bool failed = false;
 
     int it = 0;
-    // tile indices fit in 32 bits: at most (2 * 256)^2 / COLS tiles
-    const int nt = (int)ntiles;
+    const int nt = nt0;
     for (int tile = blockIdx.x; tile < nt; tile += gridDim.x, ++it) {
         if (tile + (int)gridDim.x >= nt) pdl_release();
         const int b = it & 1;
@@ -554,14 +601,16 @@ __global__ void __launch_bounds__(WShape<T, L>::THREADS, (L >= 512 ? 2 : 3))
             break;
         }
         unsigned char *in = base + b * S::BUF;
+        const int lt = tile & lmask;                       // the tile within its item
+        const T *hhat = ihhat[tile >> lgi];
         if constexpr (FREE) {
             // this warp's column (one per warp): its H-hat column lands in
             // shared memory while the forward FFT runs
-            const int qc = tile * S::COLS + c;
+            const int qc = lt * S::COLS + c;
             const int ky = qc >> lnx2, kx = qc & (nx2 - 1);
             const int kyr = ky <= a.ny ? ky : ny2 - ky, kxr = kx <= a.nx ? kx : nx2 - kx;
-            const unsigned char *src = reinterpret_cast<const unsigned char *>(
-                static_cast<const T *>(a.hhat) + ((size_t)kyr * (a.nx + 1) + kxr) * S::HS);
+            const unsigned char *src =
+                reinterpret_cast<const unsigned char *>(hhat + ((size_t)kyr * (a.nx + 1) + kxr) * S::HS);
             unsigned char *dst = reinterpret_cast<unsigned char *>(hpre + warp * S::HS);
             for (int ch = lane; ch < (int)(S::HS * sizeof(T) / 16); ch += 32) cp_async16(dst + 16 * ch, src + 16 * ch);
             cp_async_commit();
@@ -593,7 +642,7 @@ __global__ void __launch_bounds__(WShape<T, L>::THREADS, (L >= 512 ? 2 : 3))
             }
             deferred = -1;
         }
-        const int q0 = tile * S::COLS;
+        const int q0 = lt * S::COLS;
         const int k0 = (int)(q0 & (nx2 - 1));
         if (hstage && tid == 0) {
             const int ky0 = (int)(q0 >> lnx2);
@@ -601,8 +650,7 @@ __global__ void __launch_bounds__(WShape<T, L>::THREADS, (L >= 512 ? 2 : 3))
             const int r0 = k0 < a.nx ? k0 : nx2 - k0 - S::COLS + 1;
             fence_async_smem();   // the inputs' generic reads before the copy's writes
             mbar_expect_tx(&hfull[b], S::HBYTES);
-            bulk_load(in, static_cast<const T *>(a.hhat) + ((size_t)kyr0 * (a.nx + 1) + r0) * S::HS, S::HBYTES,
-                      &hfull[b]);
+            bulk_load(in, hhat + ((size_t)kyr0 * (a.nx + 1) + r0) * S::HS, S::HBYTES, &hfull[b]);
             hpend = true;
         }
 
@@ -612,7 +660,7 @@ __global__ void __launch_bounds__(WShape<T, L>::THREADS, (L >= 512 ? 2 : 3))
         // the last forward stage's output row)
         C dxy = czero<C>();
         if (DM == 1 && a.dmode == 1) {
-            const int qc = tile * S::COLS + c;
+            const int qc = lt * S::COLS + c;
             const C ex = static_cast<const C *>(a.dtx)[qc & (nx2 - 1)];
             const C ey = static_cast<const C *>(a.dty)[qc >> lnx2];
             dxy.x = ex.x - ey.y;
@@ -660,11 +708,11 @@ __global__ void __launch_bounds__(WShape<T, L>::THREADS, (L >= 512 ? 2 : 3))
         } else {
             // H-hat of column (kyr, kxr), stored by pm_store_hhat in the
             // order hhat_thread_major gives for L
-            const int q = tile * S::COLS + c;
+            const int q = lt * S::COLS + c;
             const int ky = q >> lnx2, kx = q & (nx2 - 1);   // nx2 is a power of two
             const int kyr = ky <= a.ny ? ky : ny2 - ky;
             const int kxr = kx <= a.nx ? kx : nx2 - kx;
-            const T *hcol = static_cast<const T *>(a.hhat) + ((size_t)kyr * (a.nx + 1) + kxr) * S::HS;
+            const T *hcol = hhat + ((size_t)kyr * (a.nx + 1) + kxr) * S::HS;
             if constexpr (hhat_thread_major(L)) {
                 const T *hz = hcol + t * E;   // 16-byte aligned: L, E multiples of 16
                 if constexpr (sizeof(T) == 4) {

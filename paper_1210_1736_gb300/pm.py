@@ -401,6 +401,7 @@ class Context:
         return int(lib().pm_selftest_wait_expiry(self.h))
 
     def info(self):
-        out = (C.c_int64 * 5)()
+        out = (C.c_int64 * 6)()
         _check(lib().pm_info(self.h, out))
-        return {"shift": out[0], "nsets": out[1], "ngeom": out[2], "bytes": out[3], "solve_schedule": out[4]}
+        return {"shift": out[0], "nsets": out[1], "ngeom": out[2], "bytes": out[3], "solve_schedule": out[4],
+                "batched": out[5]}

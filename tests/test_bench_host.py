@@ -41,8 +41,19 @@ def test_launch_count_per_pair():
     assert bench.fft_pairs(_one_set(32)) == 1
     g = W.galaxy_small()
     assert bench.fft_pairs(g) == 3
-    # per step: recentre (2), deposit (1), five passes per pair and three
-    # more for the fine grid's difference fields, force (1); six sort kernels
+    # galaxy_small: shapes 32^3 (coarse and medium pairs) and 32x32x8 (the
+    # fine grid): x, y forward 2 + 2, z 1 + 2, y, x inverse 2 + 2 -> 11;
+    # per step also recentre (2), deposit (1), force (1); six sort kernels
     # every sort_every-th step
-    assert bench.launches(g, 10, 0) == 10 * (2 + 1 + 15 + 3 + 1)
-    assert bench.launches(g, 10, 5) == 10 * 22 + 2 * 6
+    assert bench.fft_launches(g) == 11
+    assert bench.launches(g, 10, 0) == 10 * (2 + 1 + 11 + 1)
+    assert bench.launches(g, 10, 5) == 10 * 15 + 2 * 6
+    # large_16m: the satellites' six 128^3 pairs (two of them fine grids)
+    # share launches: x 1, y 1, z 1 + 2, y inverse 1, x inverse 1
+    spec = dict(galaxies=[
+        dict(coarse=(256, 256, 256, 32, 1), medium=(256, 256, 256, 6, 0.25), fine=(256, 256, 64, 1.5, 1)),
+        dict(coarse=(128, 128, 128, 32, 1), medium=(128, 128, 128, 0.5, 1), fine=(128, 128, 128, 0.125, 1)),
+        dict(coarse=(128, 128, 128, 32, 1), medium=(128, 128, 128, 0.5, 1), fine=(128, 128, 128, 0.125, 1))])
+    assert bench.fft_launches(spec) == (2 + 1 + 2) + (2 + 2 + 2) + (2 + 3 + 2)
+    # unbatched: five launches per pair and three more per fine grid
+    assert bench.fft_launches(spec, batched=False) == 5 * 9 + 3 * 3
