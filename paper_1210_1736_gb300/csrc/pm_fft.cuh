@@ -20,8 +20,8 @@ __host__ __device__ constexpr int fwd_radix(int L, int s) {
     return s == 0 ? 16 : (L == 512 ? (s == 1 ? 16 : 2) : L / 16);
 }
 // A plan is the forward plan or its reverse; reversing lets the first stage
-// of the inverse transform reuse the registers of the forward transform's
-// last stage.
+// of an inverse transform take the forward transform's last-stage registers
+// as they are (see also inv_fwd_plan).
 __host__ __device__ constexpr int radix(int L, int s, bool rev) {
     return rev ? fwd_radix(L, nstages(L) - 1 - s) : fwd_radix(L, s);
 }
@@ -190,19 +190,34 @@ __device__ __forceinline__ void dft16(C *v) {
 template <int L, int S, bool REV, int SIGN, bool ZIN = false, bool HOUT = false, typename C>
 __device__ __forceinline__ void stage_butterflies(C *v, int t, const C *tw) {
     constexpr int R = radix(L, S, REV), Ns = stride_before(L, S, REV), TPC = L / E;
+    if constexpr (R == 2 && Ns == L / 2) {
+        // a closing radix-2 stage: item j = t + kk TPC has the twiddle
+        // w^j = w^t exp(-2 pi i kk / 16) (w^TPC = exp(-2 pi i / 16)): one
+        // table entry per thread, the rest constant rotations.  HOUT keeps
+        // the output rows < L/2 only (register kk*2).
+        const C wt = tw[tw_offset(L, S, REV) + Ns + t];
 #pragma unroll
-    for (int kk = 0; kk < E / R; ++kk) {
-        const int j = t + kk * TPC;
-        if (Ns > 1) {
-            const C *tws = tw + tw_offset(L, S, REV) + (j % Ns);
-#pragma unroll
-            for (int r = 1; r < R; ++r) {
-                C w = tws[r * Ns];
-                v[kk * R + r] = (SIGN < 0) ? cmul(v[kk * R + r], w) : cconjmul(v[kk * R + r], w);
-            }
+        for (int kk = 0; kk < E / 2; ++kk) {
+            const C b = rot16<SIGN>(kk, (SIGN < 0) ? cmul(v[2 * kk + 1], wt) : cconjmul(v[2 * kk + 1], wt));
+            const C a = v[2 * kk];
+            v[2 * kk] = cadd(a, b);
+            if (!HOUT) v[2 * kk + 1] = csub(a, b);
         }
-        if (R == 16 && (ZIN || HOUT)) dft16<SIGN, ZIN, HOUT>(v + kk * R);
-        else Dft<R, SIGN, C>::run(v + kk * R);
+    } else {
+#pragma unroll
+        for (int kk = 0; kk < E / R; ++kk) {
+            const int j = t + kk * TPC;
+            if (Ns > 1) {
+                const C *tws = tw + tw_offset(L, S, REV) + (j % Ns);
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    C w = tws[r * Ns];
+                    v[kk * R + r] = (SIGN < 0) ? cmul(v[kk * R + r], w) : cconjmul(v[kk * R + r], w);
+                }
+            }
+            if (R == 16 && (ZIN || HOUT)) dft16<SIGN, ZIN, HOUT>(v + kk * R);
+            else Dft<R, SIGN, C>::run(v + kk * R);
+        }
     }
 }
 
@@ -258,6 +273,55 @@ __device__ __forceinline__ void load_stage(const C *sm, int ldc, int c, int t, C
     load_stage<L, S, REV>(sm, ColLayout{ldc, c}, t, v);
 }
 
+// Exchange from a radix-16 stage to a closing radix-2 stage (plans
+// ..., 16, 2) when a transform's TPC threads are the consecutive lanes
+// t = lane % TPC of one warp.  Register r of thread t holds row
+// 16 Ns (t / Ns) + t % Ns + r Ns (Ns = TPC / 2); the radix-2 stage wants in
+// register 2k + b of thread t' the row t' + k TPC + b L/2.  So thread t keeps
+// its registers of parity t / Ns and trades the other eight with thread
+// t ^ Ns: sixteen warp shuffles per thread instead of a round trip through
+// shared memory.
+template <int L, typename C> __device__ __forceinline__ void swap_exchange(C *v, int t) {
+    constexpr int NS2 = L / 32;   // partner distance (the radix-16 stage's Ns)
+    const bool lo = (t & NS2) == 0;
+#pragma unroll
+    for (int k = 0; k < E / 2; ++k) {
+        const C a = v[2 * k], b = v[2 * k + 1];
+        C snd, rcv;
+        snd.x = lo ? b.x : a.x;
+        snd.y = lo ? b.y : a.y;
+        rcv.x = __shfl_xor_sync(0xffffffffu, snd.x, NS2);
+        rcv.y = __shfl_xor_sync(0xffffffffu, snd.y, NS2);
+        v[2 * k].x = lo ? a.x : rcv.x;
+        v[2 * k].y = lo ? a.y : rcv.y;
+        v[2 * k + 1].x = lo ? rcv.x : b.x;
+        v[2 * k + 1].y = lo ? rcv.y : b.y;
+    }
+}
+
+// Registers of a forward transform's last stage (natural-order rows) renamed
+// to the first stage of the same (unreversed) plan: an inverse transform
+// with the forward plan starts from the forward outputs without an
+// exchange.  Last stage radix RL: register kk*RL + q holds row
+// t + kk TPC + q L/RL, which is row t + (kk + q E/RL) L/16 of the radix-16
+// first stage.
+template <int L, typename C> __device__ __forceinline__ void regs_last_to_first(C *v) {
+    constexpr int RL = radix(L, nstages(L) - 1, false);
+    C u[E];
+#pragma unroll
+    for (int kk = 0; kk < E / RL; ++kk)
+#pragma unroll
+        for (int q = 0; q < RL; ++q) u[kk + q * (E / RL)] = v[kk * RL + q];
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = u[e];
+}
+// An inverse transform of length L whose input comes from the forward's
+// registers runs the forward (unreversed) plan when that plan closes with a
+// radix-2 stage: its exchanges are then one through shared memory and one
+// by shuffles (swap_exchange), against two through shared memory for the
+// reversed plan.
+__host__ __device__ constexpr bool inv_fwd_plan(int L) { return nstages(L) > 1 && fwd_radix(L, nstages(L) - 1) == 2; }
+
 // Runs stages 0..NS-1 given stage 0's inputs in registers; exchanges through
 // shared memory (layout lay) between stages.  On return the registers hold
 // the last stage's outputs (natural order rows in_row of the last stage).
@@ -266,8 +330,10 @@ __device__ __forceinline__ void load_stage(const C *sm, int ldc, int c, int t, C
 // data; the first stage is radix 16 and only registers r < 8 are read).
 // HOUT: only the outputs of rows < L/2 are used (inverse transforms; the
 // last stage of a reversed plan is radix 16, outputs in registers r < 8).
-// WSYNC: the exchange area of a transform is touched by one warp only, so
-// the exchanges synchronise the warp instead of the block.
+// WSYNC: a transform's TPC threads are the consecutive lanes t = lane % TPC
+// of one warp and its exchange area is touched by that warp only, so the
+// exchanges synchronise the warp instead of the block, and an exchange into
+// a closing radix-2 stage goes by warp shuffles (swap_exchange).
 template <bool WSYNC> __device__ __forceinline__ void xsync() {
     if (WSYNC) __syncwarp(); else __syncthreads();
 }
@@ -276,17 +342,25 @@ __device__ __forceinline__ void fft_core(C *v, C *sm, const LAY &lay, int t, con
     constexpr int NS = nstages(L);
     stage_butterflies<L, 0, REV, SIGN, ZIN, HOUT && NS == 1>(v, t, tw);
     if (NS > 1) {
-        store_stage<L, 0, REV>(sm, lay, t, v);
-        xsync<WSYNC>();
-        load_stage<L, (NS > 1 ? 1 : 0), REV>(sm, lay, t, v);
-        xsync<WSYNC>();
+        if constexpr (WSYNC && NS == 2 && radix(L, 0, REV) == 16 && radix(L, NS - 1, REV) == 2) {
+            swap_exchange<L>(v, t);
+        } else {
+            store_stage<L, 0, REV>(sm, lay, t, v);
+            xsync<WSYNC>();
+            load_stage<L, (NS > 1 ? 1 : 0), REV>(sm, lay, t, v);
+            xsync<WSYNC>();
+        }
         stage_butterflies<L, (NS > 1 ? 1 : 0), REV, SIGN, false, HOUT && NS == 2>(v, t, tw);
     }
     if (NS > 2) {
-        store_stage<L, (NS > 1 ? 1 : 0), REV>(sm, lay, t, v);
-        xsync<WSYNC>();
-        load_stage<L, (NS > 2 ? 2 : 0), REV>(sm, lay, t, v);
-        xsync<WSYNC>();
+        if constexpr (WSYNC && radix(L, 1, REV) == 16 && radix(L, NS - 1, REV) == 2) {
+            swap_exchange<L>(v, t);
+        } else {
+            store_stage<L, (NS > 1 ? 1 : 0), REV>(sm, lay, t, v);
+            xsync<WSYNC>();
+            load_stage<L, (NS > 2 ? 2 : 0), REV>(sm, lay, t, v);
+            xsync<WSYNC>();
+        }
         stage_butterflies<L, (NS > 2 ? 2 : 0), REV, SIGN, false, HOUT>(v, t, tw);
     }
 }

@@ -166,21 +166,24 @@ __global__ void __launch_bounds__(NT) k_xinv(const __grid_constant__ PassBatch B
         const long long z = valid ? r >> lny : 0, y = valid ? r & (ny - 1) : 0;
         const C *in = work + ((size_t)z * 2 * ny + y) * L;
         C v[E];
-        constexpr int R0 = radix(L, 0, true);
+        // the reversed plan, or the forward one where it closes with radix 2
+        // (its exchange into that stage goes by shuffles)
+        constexpr bool IREV = !pmfft::inv_fwd_plan(L);
+        constexpr int R0 = radix(L, 0, IREV);
 #pragma unroll
         for (int kk = 0; kk < E / R0; ++kk)
 #pragma unroll
             for (int q = 0; q < R0; ++q)
-                v[kk * R0 + q] = valid ? __ldg(in + pmfft::in_row<L, 0, true>(t, kk, q)) : czero<C>();
-        pmfft::fft_core<L, true, 1, false, true, true>(v, sm, pmfft::RowLayout{line * S::LDR}, t, tw);
+                v[kk * R0 + q] = valid ? __ldg(in + pmfft::in_row<L, 0, IREV>(t, kk, q)) : czero<C>();
+        pmfft::fft_core<L, IREV, 1, false, true, true>(v, sm, pmfft::RowLayout{line * S::LDR}, t, tw);
         if (valid) {
             T *phi_s = phi_sum + r * NX;
-            constexpr int RL = radix(L, NS - 1, true);
+            constexpr int RL = radix(L, NS - 1, IREV);
 #pragma unroll
             for (int kk = 0; kk < E / RL; ++kk)
 #pragma unroll
-                for (int q = 0; q < RL / 2; ++q) {   // outputs x < nx: registers q < 8 of the radix-16 last stage
-                    const int x = pmfft::in_row<L, NS - 1, true>(t, kk, q);
+                for (int q = 0; q < RL / 2; ++q) {   // outputs x < nx: registers q < RL/2 of the last stage
+                    const int x = pmfft::in_row<L, NS - 1, IREV>(t, kk, q);
                     const C val = v[kk * RL + q];
                     // the arrays are global memory (pointers read from shared memory: say so)
                     if (split) {
@@ -512,6 +515,11 @@ __global__ void __launch_bounds__(WShape<T, L>::THREADS, (L >= 512 ? 2 : 3))
     typedef typename S::C C;
     constexpr int NS = nstages(L), NWARPS = S::THREADS / 32;
     constexpr bool FREE = S::FREE;
+    // the inverse runs the reversed plan (its first stage takes the forward's
+    // last-stage registers as they are), or the forward plan where that
+    // closes with radix 2 (registers renamed; the exchange into the radix-2
+    // stage goes by shuffles)
+    constexpr bool IREV = !pmfft::inv_fwd_plan(L);
     extern __shared__ __align__(128) unsigned char smraw[];
     unsigned char *base = reinterpret_cast<unsigned char *>(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
     C *xch = reinterpret_cast<C *>(base + 2 * S::BUF);
@@ -698,7 +706,8 @@ __global__ void __launch_bounds__(WShape<T, L>::THREADS, (L >= 512 ? 2 : 3))
             const T *hz = reinterpret_cast<const T *>(in) + (k0 < a.nx ? c : S::COLS - 1 - c) * S::HS;
 #pragma unroll
             for (int e = 0; e < E; ++e) hmul(e, hz[kz_mirror(e)]);
-            pmfft::fft_core<L, true, 1, false, true, true>(v, xch, lay, t, tw);
+            if constexpr (!IREV) pmfft::regs_last_to_first<L>(v);
+            pmfft::fft_core<L, IREV, 1, false, true, true>(v, xch, lay, t, tw);
             // every H-hat read done before the outputs overwrite the buffer
             if (!__syncthreads_and(hok ? 1 : 0)) {
                 failed = true;
@@ -739,17 +748,18 @@ __global__ void __launch_bounds__(WShape<T, L>::THREADS, (L >= 512 ? 2 : 3))
 #pragma unroll
                 for (int e = 0; e < E; ++e) hmul(e, __ldg(hcol + kz_mirror(e)));
             }
-            pmfft::fft_core<L, true, 1, false, true, true>(v, xch, lay, t, tw);
+            if constexpr (!IREV) pmfft::regs_last_to_first<L>(v);
+            pmfft::fft_core<L, IREV, 1, false, true, true>(v, xch, lay, t, tw);
         }
         {
-            // inverse outputs below L/2: registers r < RL/2 of the radix-16
-            // last stage of the reversed plan
-            constexpr int RL = radix(L, NS - 1, true);
+            // inverse outputs below L/2: registers r < RL/2 of the last
+            // stage of the inverse's plan
+            constexpr int RL = radix(L, NS - 1, IREV);
 #pragma unroll
             for (int kk = 0; kk < E / RL; ++kk)
 #pragma unroll
                 for (int r = 0; r < RL / 2; ++r)
-                    *reinterpret_cast<C *>(in + woff<T, L, S::RIN>(pmfft::in_row<L, NS - 1, true>(t, kk, r), c)) =
+                    *reinterpret_cast<C *>(in + woff<T, L, S::RIN>(pmfft::in_row<L, NS - 1, IREV>(t, kk, r), c)) =
                         v[kk * RL + r];
         }
         fence_async_smem();   // the staged outputs are visible to the tensor copies
