@@ -355,10 +355,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 1) k_recentre(PartK<
 // rule selects for each galaxy (Sec. 2.1), then
 //   MODE 0: leap-frog kick-drift   MODE 1: write acceleration
 //   MODE 2: kick only              MODE 3: energy / angular momentum sums
-// The FP32 kick-drift fits 64 registers without spilling: four blocks per
-// SM hide more of the stencil gathers' latency.
+// The FP32 kick-drift fits 48 registers without spilling: five blocks per
+// SM hide more of the stencil gathers' latency than four at 64.
 template <typename T, int MODE>
-__global__ void __launch_bounds__(256, (MODE == 0 && sizeof(T) == 4) ? 4 : 3)
+__global__ void __launch_bounds__(256, (MODE == 0 && sizeof(T) == 4) ? 5 : 3)
     k_force(PartK<T> p, const __grid_constant__ SysK s, const CenK *cen, T dt, T *ax, T *ay, T *az, double *diag) {
     double dsum[7] = {0, 0, 0, 0, 0, 0, 0};
     const long long stride = (long long)gridDim.x * blockDim.x;
