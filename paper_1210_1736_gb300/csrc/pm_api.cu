@@ -130,7 +130,7 @@ struct Pair {
     int gi, a, b;
     bool diff = false;
     void *work = nullptr, *work2 = nullptr;
-    CUtensorMap yfwd, yinv, zmap, yinv2, zmap2;
+    CUtensorMap yfwd, yinv, zmap, yfwd2, yinv2, zmap2;
 };
 
 struct GeoBuf {
@@ -403,7 +403,7 @@ template <typename T> int launch_pass(pm_ctx *c, int pass, cudaStream_t st, int 
                         break;
                     case PASS_YFWD:
                         a.tw = c->d_tw[tw_index(2 * sg.ny)];
-                        main.add(a, &pr.yfwd);
+                        main.add(a, &pr.yfwd, &pr.yinv);   // stores: boxes of 2ny rows
                         break;
                     case PASS_ZCONV:
                         a.tw = c->d_tw[tw_index(2 * sg.nz)];
@@ -418,10 +418,10 @@ template <typename T> int launch_pass(pm_ctx *c, int pass, cudaStream_t st, int 
                         break;
                     case PASS_YINV:
                         a.tw = c->d_tw[tw_index(2 * sg.ny)];
-                        main.add(a, &pr.yinv);
+                        main.add(a, &pr.yinv, &pr.yfwd);   // stores: boxes of ny rows
                         if (pr.diff) {
                             a.work = pr.work2;
-                            main.add(a, &pr.yinv2);
+                            main.add(a, &pr.yinv2, &pr.yfwd2);
                         }
                         break;
                     default:
@@ -1124,11 +1124,10 @@ int pm_create_grids(const pm_system *sys, const pm_galaxy *gals, void *stream, p
                                          &pr.zmap)))
                 return cleanup(rc);
             if (!pr.diff) continue;
-            CUtensorMap unused;
             if ((rc = dev_alloc(c, &pr.work2, bytes))) return cleanup(rc);
             if (cudaMemsetAsync(pr.work2, 0, bytes, c->user) != cudaSuccess)
                 return cleanup(fail(PM_E_CUDA, "memset failed"));
-            if ((rc = pm_encode_col_maps(pr.work2, gb.g.nx, gb.g.ny, gb.g.nz, (int)c->esz, &unused, &pr.yinv2,
+            if ((rc = pm_encode_col_maps(pr.work2, gb.g.nx, gb.g.ny, gb.g.nz, (int)c->esz, &pr.yfwd2, &pr.yinv2,
                                          &pr.zmap2)))
                 return cleanup(rc);
             for (int k = 0; k < 3; ++k)

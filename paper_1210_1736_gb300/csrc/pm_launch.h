@@ -35,7 +35,7 @@ enum { COL_YFWD = 0, COL_ZCONV = 1, COL_YINV = 2 };
 // same shape (nx, ny, nz), e.g. the grids of the same size of every galaxy
 // (Sec. 2.1: all galaxies use the same kinds of grid).  Each item has its own
 // arrays, H-hat table and tensor maps (lmap: the column passes' loads; smap:
-// the z pass's stores); the launch walks the items' tiles (or x-pass row
+// their stores); the launch walks the items' tiles (or x-pass row
 // groups) as one index space, 2^lgi per item (set by the launcher).
 #ifndef PM_BATCH
 #define PM_BATCH 8
@@ -70,11 +70,13 @@ int pm_encode_col_maps(void *work, int nx, int ny, int nz, int esz, CUtensorMap 
                        CUtensorMap *zmap);
 
 template <typename T> cudaError_t pm_set_attrs();
-// Batched passes: x forward, column pass `mode` (y forward through lmap =
-// the items' yfwd maps, y inverse through their yinv maps, z through lmap
-// for loads and smap for stores: the same map in place, another work
-// array's for the first difference-field pass), x inverse.  Every item of a
-// batch has the same shape, precision and, in the z pass, dmode.
+// Batched passes: x forward, column pass `mode` (y forward: loads through
+// the items' yfwd maps, stores through their yinv maps, whose boxes hold
+// the 2ny output rows; y inverse: loads through yinv, stores through yfwd
+// (ny rows kept); z: loads through lmap and stores through smap, the same
+// map in place or another work array's for the first difference-field
+// pass), x inverse.  Every item of a batch has the same shape, precision
+// and, in the z pass, dmode.
 template <typename T> cudaError_t pm_launch_xfwd(PassBatch b, cudaStream_t st);
 template <typename T> cudaError_t pm_launch_col(PassBatch b, int mode, cudaStream_t st);
 template <typename T> cudaError_t pm_launch_xinv(PassBatch b, cudaStream_t st);

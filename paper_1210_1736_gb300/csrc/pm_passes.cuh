@@ -292,7 +292,10 @@ template <typename T, int L, int MODE> constexpr size_t col_smem() {
 // Persistent y pass (forward or inverse) over a batch: the items' maps
 // B.lmap are 2D tensor maps over 8-byte elements whose box is
 // (COLS * EPC, min(rows, 256)); an item's tile covers COLS columns of one z
-// plane.
+// plane.  The outputs are staged in the exchange buffer, laid out [row][COLS]
+// as a tile, and leave by tensor stores through B.smap (boxes of the output
+// rows: 2ny for the forward, ny for the inverse; columns beyond nx2 are
+// clipped by the copy).
 template <typename T, int L, int MODE>
 __global__ void __launch_bounds__(CShape<T, L>::THREADS, 3) k_col(const __grid_constant__ PassBatch B) {
     typedef typename cplx_t<T>::type C;
@@ -370,6 +373,7 @@ __global__ void __launch_bounds__(CShape<T, L>::THREADS, 3) k_col(const __grid_c
         const C *in = b ? buf1 : buf0;
         C v[E];
         constexpr int R0 = radix(L, 0, REV_IN);
+        constexpr int OROWS = (MODE == COL_YFWD) ? L : L / 2, OBOX = OROWS < 256 ? OROWS : 256;
 #pragma unroll
         for (int kk = 0; kk < E / R0; ++kk)
 #pragma unroll
@@ -377,6 +381,9 @@ __global__ void __launch_bounds__(CShape<T, L>::THREADS, 3) k_col(const __grid_c
                 const bool need = (MODE == COL_YINV) || r < R0 / 2;   // forward inputs above L/2 are padding
                 v[kk * R0 + r] = need ? in[pmfft::in_row<L, 0, REV_IN>(t, kk, r) * COLS + c] : czero<C>();
             }
+        // the previous tile's outputs have been read out of the exchange
+        // buffer before this tile's stages write to it
+        if (tid == 0) bulk_wait_read();
         __syncthreads();   // buffer b consumed, previous tile's exchange done
         if (tid == 0 && tile + 2 * (long long)gridDim.x < ntiles) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -384,46 +391,31 @@ __global__ void __launch_bounds__(CShape<T, L>::THREADS, 3) k_col(const __grid_c
             ++issued[b];
         }
 
-        // column of this thread
-        long long q;
-        bool valid;
-        C *col;
-        size_t stride;
-        {
-            const long long lt = tile & lmask;
-            const long long z = lt >> ltpz, kx = (lt & (tiles_per_z - 1)) * COLS + c;
-            q = kx;
-            valid = kx < nx2;
-            col = iwork[tile >> B.lgi] + (size_t)z * ny2 * nx2 + kx;
-            stride = (size_t)nx2;
-        }
-
-        static_assert(MODE == COL_YFWD || MODE == COL_YINV, "the z pass is k_zconv");
+        static_assert(MODE == COL_YFWD || MODE == COL_YINV, "the z pass is k_colw");
         pmfft::fft_core<L, REV_IN, SIGN_IN, MODE != COL_YINV, MODE == COL_YINV>(v, sm, COLS, c, t, tw);
-        if (MODE == COL_YFWD) {
-            constexpr int RL = radix(L, NS - 1, false);
-            if (valid) {
-                C *colt = col + (size_t)t * stride;
-#pragma unroll
-                for (int kk = 0; kk < E / RL; ++kk)
-#pragma unroll
-                    for (int r = 0; r < RL; ++r)
-                        __stcg(colt + (size_t)pmfft::in_row<L, NS - 1, false>(0, kk, r) * stride, v[kk * RL + r]);
-            }
-            continue;
-        }
-        // inverse outputs (COL_YINV): the reversed plan ends with radix 16,
-        // whose outputs below L/2 are registers r < 8
-        constexpr int RL = radix(L, NS - 1, true);
-        if (valid) {
-            C *colt = col + (size_t)t * stride;
+        // fft_core ends with a block barrier after its last exchange reads:
+        // the exchange buffer takes the outputs, rows in_row of the last
+        // stage (the inverse keeps rows < L/2: registers r < RL/2)
+        {
+            constexpr bool REV_OUT = (MODE == COL_YINV);
+            constexpr int RL = radix(L, NS - 1, REV_OUT), RK = (MODE == COL_YFWD) ? RL : RL / 2;
 #pragma unroll
             for (int kk = 0; kk < E / RL; ++kk)
 #pragma unroll
-                for (int r = 0; r < RL / 2; ++r)
-                    __stcg(colt + (size_t)pmfft::in_row<L, NS - 1, true>(0, kk, r) * stride, v[kk * RL + r]);
+                for (int r = 0; r < RK; ++r) sm[pmfft::in_row<L, NS - 1, REV_OUT>(t, kk, r) * COLS + c] = v[kk * RL + r];
+        }
+        fence_async_smem();   // the staged outputs are visible to the tensor copies
+        __syncthreads();
+        if (tid == 0) {
+            int x, y;
+            coords(tile & lmask, x, y);
+            const CUtensorMap *smap = &B.smap[tile >> B.lgi];
+#pragma unroll
+            for (int k = 0; k < OROWS / OBOX; ++k) tma_store_2d(smap, x, y + k * OBOX, sm + k * OBOX * COLS);
+            bulk_commit();
         }
     }
+    if (tid == 0) bulk_wait_all();   // the stores have read the buffer before the block leaves
 }
 
 

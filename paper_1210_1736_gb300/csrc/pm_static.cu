@@ -159,11 +159,11 @@ int run(const int64_t *rho, void *phi, int nx, int ny, int nz, double l_xy, doub
     a.tw = twx;
     SCK(pm_launch_xfwd<T>(pm_single_batch(a, nullptr, nullptr), st));
     a.tw = twy;
-    SCK(pm_launch_col<T>(pm_single_batch(a, &yfwd, nullptr), COL_YFWD, st));
+    SCK(pm_launch_col<T>(pm_single_batch(a, &yfwd, &yinv), COL_YFWD, st));
     a.tw = twz;
     SCK(pm_launch_col<T>(pm_single_batch(a, &zmap, nullptr), COL_ZCONV, st));
     a.tw = twy;
-    SCK(pm_launch_col<T>(pm_single_batch(a, &yinv, nullptr), COL_YINV, st));
+    SCK(pm_launch_col<T>(pm_single_batch(a, &yinv, &yfwd), COL_YINV, st));
     a.tw = twx;
     SCK(pm_launch_xinv<T>(pm_single_batch(a, nullptr, nullptr), st));
     SCK(launch_settle<T>(err, status, phi, (long long)nx * ny * nz, st));
