@@ -309,6 +309,20 @@ def launches(w, steps, sort_every, batched=True):
     return per_step * steps + 6 * sorts
 
 
+def request_block_from(parts):
+    """One request's particle state as a pinned host block (9, n) float32,
+    copied from a device particle set: x, y, z, vx, vy, vz, m, galaxy id and
+    flags (the last two as int32), in the set's current (spatially sorted)
+    order."""
+    import torch
+    hbuf = torch.empty((9, parts.n), dtype=torch.float32).pin_memory()
+    for k, t in enumerate((parts.x, parts.y, parts.z, parts.vx, parts.vy, parts.vz, parts.m)):
+        hbuf[k].copy_(t)
+    hbuf[7].view(torch.int32).copy_(parts.gal)
+    hbuf[8].view(torch.int32).copy_(parts.flags)
+    return hbuf
+
+
 def request_block(host, m32, gal):
     """One request's particle state as a pinned host block (9, n) float32:
     x, y, z, vx, vy, vz, m, galaxy id and flags (the last two as int32)."""
@@ -518,14 +532,19 @@ def run_ours(args):
     achieved = pb[dom] / (phase_ms[dom] / 1e3) / 1e9
 
     # ---- end to end through the C ABI with host buffers (RequestPipeline) ----
-    hbuf = request_block(host, m32, w["gal"])
+    # every request carries the state as the device-resident run left it:
+    # spatially sorted, as a client that keeps the library's particle order
+    # sends it
+    hbuf = request_block_from(parts)
     pipe = RequestPipeline(ctx, hbuf, dt)
     h2d, d2h = pipe.h2d_bytes, pipe.d2h_bytes
     Ke = max(1, min(K, 200))
 
     def e2e_run(overlap):
         pipe.reset()
-        for k in range(pipe.NB):              # untimed: every buffer's step is captured here
+        # untimed: every buffer's captured steps (with and without the sort
+        # of every args.sort_every-th step) are made here
+        for k in range(pipe.NB * max(1, args.sort_every)):
             pipe.request(k, overlap)
         torch.cuda.synchronize()
         barrier()
@@ -569,7 +588,9 @@ def run_ours(args):
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": Ke, "serial_value": e2e_serial,
                 "pipeline": "one-step requests rotating over three device buffers: upload of k+1 and download "
-                            "of k-1 on their own streams overlap the step of k; serial_value without the overlap"},
+                            "of k-1 on their own streams overlap the step of k; serial_value without the overlap; "
+                            "each request uploads the full particle state (spatially sorted, as the device-resident "
+                            "run left it) and downloads positions and velocities"},
         "gpu_launches": launches(w, K, args.sort_every, bool(ctx.info()["batched"])),
         "clocks": clocks,
     }

@@ -529,6 +529,10 @@ void set_units(pm_ctx *c, bool batched) {
 
 // Times each solve schedule (one warm-up solve, then five between events,
 // on zeroed densities) with and without batching, and keeps the fastest.
+// Chooses the solve's launch configuration by timing: batched or per-pair
+// launches, and the two branch schedules.  Every configuration is timed
+// (four solves after one untimed) in three interleaved rounds and keeps its
+// fastest round, so that a transient slowdown does not decide the choice.
 template <typename T> int tune_schedule(pm_ctx *c) {
     set_units(c, true);
     c->sched = 0;
@@ -537,34 +541,35 @@ template <typename T> int tune_schedule(pm_ctx *c) {
     cudaEvent_t e0, e1;
     PM_CK(cudaEventCreate(&e0));
     PM_CK(cudaEventCreate(&e1));
-    float best = 0.f;
-    int best_s = 0, best_b = 1;
-    bool first = true;
-    int rc = PM_OK;
-    for (int bt = 1; bt >= 0 && rc == PM_OK; --bt) {
+    struct Cfg { int bt, sc; float ms; };
+    std::vector<Cfg> cfg;
+    for (int bt = 1; bt >= 0; --bt) {
         set_units(c, bt != 0);
-        for (int sc = 0; sc < (c->units.size() < 2 ? 1 : 2) && rc == PM_OK; ++sc) {
-            c->sched = sc;
+        for (int sc = 0; sc < (c->units.size() < 2 ? 1 : 2); ++sc) cfg.push_back({bt, sc, -1.f});
+    }
+    int rc = PM_OK;
+    for (int round = 0; round < 3 && rc == PM_OK; ++round)
+        for (Cfg &f : cfg) {
+            if (rc != PM_OK) break;
+            set_units(c, f.bt != 0);
+            c->sched = f.sc;
             rc = enqueue_solve<T>(c, c->user, nullptr);
             if (rc == PM_OK && cudaEventRecord(e0, c->user) != cudaSuccess) rc = fail(PM_E_CUDA, "event record failed");
-            for (int k = 0; k < 5 && rc == PM_OK; ++k) rc = enqueue_solve<T>(c, c->user, nullptr);
+            for (int k = 0; k < 4 && rc == PM_OK; ++k) rc = enqueue_solve<T>(c, c->user, nullptr);
             if (rc == PM_OK && cudaEventRecord(e1, c->user) != cudaSuccess) rc = fail(PM_E_CUDA, "event record failed");
             float ms = 0.f;
             if (rc == PM_OK &&
                 (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
                 rc = fail(PM_E_CUDA, "schedule timing failed");
-            if (rc == PM_OK && (first || ms < best)) {
-                best = ms;
-                best_s = sc;
-                best_b = bt;
-                first = false;
-            }
+            if (rc == PM_OK && (f.ms < 0.f || ms < f.ms)) f.ms = ms;
         }
-    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    set_units(c, best_b != 0);
-    c->sched = best_s;
+    const Cfg *best = &cfg[0];
+    for (const Cfg &f : cfg)
+        if (f.ms >= 0.f && (best->ms < 0.f || f.ms < best->ms)) best = &f;
+    set_units(c, best->bt != 0);
+    c->sched = best->sc;
     if (rc != PM_OK) return rc;
     return check_device_error(c);
 }
