@@ -318,33 +318,48 @@ static __global__ void __launch_bounds__(256) k_com_apply(const __grid_constant_
 // registers (a particle of another galaxy first sends the running sums to
 // the block's accumulator row); the warps reduce once, at the end.
 template <typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 1) k_recentre(PartK<T> p, const __grid_constant__ SysK s, CenK *cen,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 1) k_recentre(PartK<T> p, const __grid_constant__ SysK s, CenK *cen,
                                                   long long *part) {
     __shared__ unsigned long long red[PM_MAX_GALAXIES][4];
     if (threadIdx.x < PM_MAX_GALAXIES * 4) (&red[0][0])[threadIdx.x] = 0;
     int ag = -1;
     unsigned long long S[4] = {0, 0, 0, 0};
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += stride) {
-        // every load of the particle issued before the flag test (one memory
-        // latency per particle, not two); volatile loads cannot be sunk
-        // into the branch that uses them
-        const uint32_t f = ld_early(p.flags + i);
-        const int gi = ld_early(p.gal + i);
-        const T x = ld_early(p.x + i), y = ld_early(p.y + i), z = ld_early(p.z + i), m = ld_early(p.m + i);
-        if (f & PM_FLAG_LOST) continue;
-        int Dx, Dy, Dz;
-        long long M;
-        const int g = com_contrib(s, cen, gi, x, y, z, m, M, Dx, Dy, Dz);
-        if (g < 0) continue;
-        if (g != ag) {
-            if (ag >= 0) com_flush(part, ag, S);
-            ag = g;
+    // U particles per round: all their loads are issued before any is used
+    // (volatile loads stay where they are written), so a thread keeps U
+    // particles' reads in flight
+    constexpr int U = 4;
+    for (long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; i0 < p.n; i0 += U * stride) {
+        uint32_t f[U];
+        int gi[U];
+        T x[U], y[U], z[U], m[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const long long i = i0 + u * stride;
+            f[u] = PM_FLAG_LOST;
+            if (i < p.n) {
+                f[u] = ld_early(p.flags + i);
+                gi[u] = ld_early(p.gal + i);
+                x[u] = ld_early(p.x + i); y[u] = ld_early(p.y + i); z[u] = ld_early(p.z + i);
+                m[u] = ld_early(p.m + i);
+            }
         }
-        S[0] += (unsigned long long)M;
-        S[1] += (unsigned long long)(M * Dx);
-        S[2] += (unsigned long long)(M * Dy);
-        S[3] += (unsigned long long)(M * Dz);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (f[u] & PM_FLAG_LOST) continue;
+            int Dx, Dy, Dz;
+            long long M;
+            const int g = com_contrib(s, cen, gi[u], x[u], y[u], z[u], m[u], M, Dx, Dy, Dz);
+            if (g < 0) continue;
+            if (g != ag) {
+                if (ag >= 0) com_flush(part, ag, S);
+                ag = g;
+            }
+            S[0] += (unsigned long long)M;
+            S[1] += (unsigned long long)(M * Dx);
+            S[2] += (unsigned long long)(M * Dy);
+            S[3] += (unsigned long long)(M * Dz);
+        }
     }
     __syncthreads();
     com_warp_add(s, red, ag, S);
@@ -863,8 +878,9 @@ template <typename T>
 cudaError_t pm_launch_recentre(const PartK<T> &p, const SysK &sk, CenK *cen, long long *part, int phase,
                                cudaStream_t st) {
     if ((phase & 1) && p.n > 0) {
-        // one full wave of resident blocks (8 per SM in FP32): each thread
-        // sums several particles in registers before the one warp reduction
+        // one full wave of resident blocks (5 per SM in FP32, 48 registers
+        // for four particles' loads in flight): each thread sums several
+        // particles in registers before the one warp reduction
         static int bps = 0;
         if (!bps && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, pmk::k_recentre<T>, 256, 0) != cudaSuccess ||
                      bps < 1))
