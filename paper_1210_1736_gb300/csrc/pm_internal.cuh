@@ -134,6 +134,10 @@ __device__ __forceinline__ int pm_region(const GalK &G, float dx, float dy, floa
                                          Cell &cf, Cell &cm) {
     float r2 = pm_r2(dx, dy, dz);
     cm.ok = false; cf.ok = false;
+    // at or beyond R_out neither test below can pass (rc2 <= ro2, as
+    // R_core <= R_out and rounding to FP32 is monotonic): outer, whatever
+    // the cells (a NaN distance lands here as it did through them)
+    if (!(r2 < G.ro2)) return REG_OUTER;
     if (G.med.nx) cm = pm_cells(G.med, dx, dy, dz);
     if (G.fine.nx && G.med.nx) {
         cf = pm_cells(G.fine, dx, dy, dz);
