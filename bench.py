@@ -676,20 +676,26 @@ def oracle_sampled_rate(w, workload, steps):
                       f"{os.cpu_count()} cores (H-hat tables built before timing)"}
 
 
+REF_SAMPLES = 20
+
+
 def run_reference(args):
     from paper_1210_1736_gb300 import workloads as W
     rank, _, world = env_rank()
     if rank != 0:
         return
     w = getattr(W, args.workload)()
-    cb = oracle_sampled_rate(w, args.workload, max(1, args.steps))
+    # at most REF_SAMPLES sampled oracle steps (at least one per distinct
+    # geometry), whatever --steps asks for: a sampled large_16m step takes a
+    # few seconds on one host core, and the run must end within minutes
+    cb = oracle_sampled_rate(w, args.workload, max(1, min(args.steps, REF_SAMPLES)))
     line = {"metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic (seeded disc-bulge-halo galaxy)", "impl": "reference",
             "config": bench_config(w, args.workload, len(w["m"]), world),
             "note": "the oracle needs no warm-up (no compilation, no caches beyond the H-hat tables, which "
                     "are built before timing); each timed step is a bounded sample of a full step (see "
-                    "cpu_baseline.sample)",
+                    "cpu_baseline.sample), and at most %d such samples run whatever --steps asks for" % REF_SAMPLES,
             "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
