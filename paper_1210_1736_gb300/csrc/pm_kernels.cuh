@@ -728,6 +728,11 @@ template <typename T, int L> cudaError_t attrs_L() {
     e = cudaFuncSetAttribute(pmk::k_colw<T, L, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)pmk::colw_smem<T, L>());
     if (e) return e;
+    if constexpr (L == 128 || L == 256) {
+        e = cudaFuncSetAttribute(pmk::k_colw<T, L, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)pmk::colw_smem<T, L>());
+        if (e) return e;
+    }
     e = cudaFuncSetAttribute(pmk::k_col<T, L, COL_YINV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)pmk::col_smem<T, L, COL_YINV>());
     if (e) return e;
@@ -797,6 +802,15 @@ template <typename T, int L> cudaError_t zconv_L(PassBatch b, cudaStream_t st) {
     b.lgi = ilog2(((long long)4 * b.a[0].ny * b.a[0].nx) / S::COLS);   // COLS divides the 2ny x 2nx columns
     const long long ntiles = (long long)b.n << b.lgi;
     const bool dm = b.a[0].dmode != 0;
+    if constexpr (L == 128 || L == 256) {
+        if (b.a[0].dmode == 3) {   // both difference fields in one pass (see PairArgs)
+            long long g2 = (long long)colw_blocks_per_sm<T, L, 2>() * num_sms();
+            if (g2 > ntiles) g2 = ntiles;
+            if (g2 < 1) g2 = 1;
+            return launch_pdl(pmk::k_colw<T, L, 2>, (unsigned)g2, S::THREADS, pmk::colw_smem<T, L>(), st, b);
+        }
+    }
+    if (b.a[0].dmode == 3) return cudaErrorInvalidValue;
     long long grid = (long long)(dm ? colw_blocks_per_sm<T, L, 1>() : colw_blocks_per_sm<T, L, 0>()) * num_sms();
     if (grid > ntiles) grid = ntiles;
     if (grid < 1) grid = 1;

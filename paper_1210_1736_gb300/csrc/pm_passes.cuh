@@ -501,7 +501,7 @@ __device__ __forceinline__ uint32_t woff(int row, int c) {
 // The modes are separate instantiations so that the plain pass carries no
 // mode branch.
 template <typename T, int L, int DM>
-__global__ void __launch_bounds__(WShape<T, L>::THREADS, (L >= 512 ? 2 : 3))
+__global__ void __launch_bounds__(WShape<T, L>::THREADS, ((L >= 512 || DM == 2) ? 2 : 3))
     k_colw(const __grid_constant__ PassBatch B) {
     typedef WShape<T, L> S;
     typedef typename S::C C;
@@ -540,8 +540,8 @@ __global__ void __launch_bounds__(WShape<T, L>::THREADS, (L >= 512 ? 2 : 3))
                 tma_load_2d(base + b * S::BUF + s * S::RIN * S::P + k * S::BOXI * S::P, map,
                             (int)((lt * S::COLS + s * S::SW) * S::EPC), k * S::BOXI, &full[b]);
     };
-    auto issue_store = [&](int tile, const unsigned char *src) {
-        const CUtensorMap *smap = &B.smap[tile >> lgi];
+    auto issue_store = [&](int tile, const unsigned char *src, bool to_lmap = false) {
+        const CUtensorMap *smap = to_lmap ? &B.lmap[tile >> lgi] : &B.smap[tile >> lgi];
         const int lt = tile & lmask;
 #pragma unroll
         for (int s = 0; s < S::NSUB; ++s)
@@ -572,6 +572,10 @@ __global__ void __launch_bounds__(WShape<T, L>::THREADS, (L >= 512 ? 2 : 3))
     // BUF bytes; it is copied into the tile's input buffer once the inputs
     // are in registers and read from there for the multiply
     const bool hstage = !FREE && L >= 128 && S::COLS <= a.nx;
+    if (DM == 2 && !hstage) {   // the fused mode reads H-hat from the staged rows only (the host checks)
+        if (threadIdx.x == 0) atomicExch(a.err, 1);
+        return;
+    }
     bool hpend = false;   // thread 0: an H-hat copy not yet seen complete
     pmfft::expand_twiddles<L>(tw, static_cast<const C *>(a.tw));
     __syncthreads();
@@ -659,7 +663,7 @@ __global__ void __launch_bounds__(WShape<T, L>::THREADS, (L >= 512 ? 2 : 3))
         // (column constant) or D_z + i (per register: kz of register e is
         // the last forward stage's output row)
         C dxy = czero<C>();
-        if (DM == 1 && a.dmode == 1) {
+        if ((DM == 1 && a.dmode == 1) || DM == 2) {
             const int qc = lt * S::COLS + c;
             const C ex = static_cast<const C *>(a.dtx)[qc & (nx2 - 1)];
             const C ey = static_cast<const C *>(a.dty)[qc >> lnx2];
@@ -696,15 +700,62 @@ __global__ void __launch_bounds__(WShape<T, L>::THREADS, (L >= 512 ? 2 : 3))
             hok = mbar_wait(&hfull[b], phase);
             if (hok && tid == 0) hpend = false;
             const T *hz = reinterpret_cast<const T *>(in) + (k0 < a.nx ? c : S::COLS - 1 - c) * S::HS;
+            if constexpr (DM == 2) {
+                // both difference fields from the one forward transform:
+                // u = S H-hat (D_x + i D_y) -> fx + i fy (work2, through
+                // smap), then v = S H-hat (D_z + i) -> fz + i Phi_1 (in
+                // place, through lmap, below)
+                C u[E];
 #pragma unroll
-            for (int e = 0; e < E; ++e) hmul(e, hz[kz_mirror(e)]);
-            if constexpr (!IREV) pmfft::regs_last_to_first<L>(v);
-            pmfft::fft_core<L, IREV, 1, false, true, true>(v, xch, lay, t, tw);
-            // every H-hat read done before the outputs overwrite the buffer
-            if (!__syncthreads_and(hok ? 1 : 0)) {
-                failed = true;
-                if (tid == 0 && hpend) mbar_wait(&hfull[b], phase);   // let the copy land (bounded)
-                break;
+                for (int e = 0; e < E; ++e) {
+                    constexpr int RLF = radix(L, NS - 1, false);
+                    const int kz = pmfft::in_row<L, NS - 1, false>(t, e / RLF, e % RLF);
+                    const T h = hz[kz <= L / 2 ? kz : L - kz];
+                    C f1 = dxy, f2 = static_cast<const C *>(a.dtz)[kz];
+                    f2.y += (T)1;
+                    f1.x *= h; f1.y *= h;
+                    f2.x *= h; f2.y *= h;
+                    u[e] = cmul(v[e], f1);
+                    v[e] = cmul(v[e], f2);
+                }
+                if constexpr (!IREV) pmfft::regs_last_to_first<L>(u);
+                pmfft::fft_core<L, IREV, 1, false, true, true>(u, xch, lay, t, tw);
+                // every H-hat read done before the outputs overwrite the buffer
+                if (!__syncthreads_and(hok ? 1 : 0)) {
+                    failed = true;
+                    if (tid == 0 && hpend) mbar_wait(&hfull[b], phase);   // let the copy land (bounded)
+                    break;
+                }
+                {
+                    constexpr int RL = radix(L, NS - 1, IREV);
+#pragma unroll
+                    for (int kk = 0; kk < E / RL; ++kk)
+#pragma unroll
+                        for (int r = 0; r < RL / 2; ++r)
+                            *reinterpret_cast<C *>(
+                                in + woff<T, L, S::RIN>(pmfft::in_row<L, NS - 1, IREV>(t, kk, r), c)) = u[kk * RL + r];
+                }
+                fence_async_smem();
+                __syncthreads();
+                if (tid == 0) {
+                    issue_store(tile, in);
+                    bulk_commit();
+                    bulk_wait_read();   // read out before the second outputs overwrite the buffer
+                }
+                __syncthreads();
+                if constexpr (!IREV) pmfft::regs_last_to_first<L>(v);
+                pmfft::fft_core<L, IREV, 1, false, true, true>(v, xch, lay, t, tw);
+            } else {
+#pragma unroll
+                for (int e = 0; e < E; ++e) hmul(e, hz[kz_mirror(e)]);
+                if constexpr (!IREV) pmfft::regs_last_to_first<L>(v);
+                pmfft::fft_core<L, IREV, 1, false, true, true>(v, xch, lay, t, tw);
+                // every H-hat read done before the outputs overwrite the buffer
+                if (!__syncthreads_and(hok ? 1 : 0)) {
+                    failed = true;
+                    if (tid == 0 && hpend) mbar_wait(&hfull[b], phase);   // let the copy land (bounded)
+                    break;
+                }
             }
         } else {
             // H-hat of column (kyr, kxr), stored by pm_store_hhat in the
@@ -763,7 +814,7 @@ __global__ void __launch_bounds__(WShape<T, L>::THREADS, (L >= 512 ? 2 : 3))
         }
         if (tid == 0) {
             if (FREE && !mbar_wait(&staged[b], phase)) { failed = true; break; }
-            issue_store(tile, in);
+            issue_store(tile, in, DM == 2);   // the fused pass's second outputs go back in place
             bulk_commit();
             if (b) ++done1; else ++done0;
             if (FREE) {
