@@ -272,12 +272,21 @@ def fft_pairs(w):
     return n
 
 
+def fused_diff(spec):
+    """A fine grid whose two difference-field z products come from one
+    forward transform in one launch (z length 128 or 256 with the tile's
+    H-hat rows staged: FP32 tile columns 4096 / L <= nx), as the library
+    plans it."""
+    nx, nz = spec[0], spec[2]
+    return nz in (64, 128) and min(4096 // (2 * nz), 256) <= nx
+
+
 def fft_launches(w, batched=True):
     """FFT launches per step: the pairs of mass sets of all galaxies are
     grouped by grid shape (nx, ny, nz) and each pass of a shape is one launch
     per 8 pairs; a fine grid (grid 1, solved for its difference fields) adds
-    a second work array to the y and x inverse passes and two z passes of
-    its own."""
+    a second work array to the y and x inverse passes and one z pass of its
+    own (two where its two products are not fused, see fused_diff)."""
     shapes = {}
     for g in w["galaxies"]:
         pairs = [(g["coarse"], False)]
@@ -288,13 +297,14 @@ def fft_launches(w, batched=True):
         for spec, diff in pairs:
             p, d = shapes.get(tuple(spec[:3]), (0, 0))
             shapes[tuple(spec[:3])] = (p + 1, d + int(diff))
-    if not batched:   # a launch per pair: five passes, three more for a fine grid
-        return sum(5 * p + 3 * d for p, d in shapes.values())
+    zd = {s: (1 if fused_diff(s) else 2) for s in shapes}   # z launches per batch of fine grids
+    if not batched:   # a launch per pair: five passes, two or three more for a fine grid
+        return sum(5 * p + (zd[s] + 1) * d for s, (p, d) in shapes.items())
     up = lambda k: (k + 7) // 8  # noqa: E731
     n = 0
-    for p, d in shapes.values():
+    for s, (p, d) in shapes.items():
         n += 2 * up(p)                                   # x and y forward
-        n += up(p - d) + (2 * up(d) if d else 0)         # z: plain, then the two difference passes
+        n += up(p - d) + (zd[s] * up(d) if d else 0)     # z: plain, then the difference-field pass(es)
         n += 2 * up(p + d)                               # y and x inverse over both work arrays
     return n
 
