@@ -202,6 +202,16 @@ int pm_count_lost(pm_ctx *ctx, const pm_particles *p, int64_t *host_out);
  * branches). */
 int pm_info(pm_ctx *ctx, int64_t *host_out);
 
+/* Sets the solve's launch configuration in place of the one chosen by timing
+ * at creation: batched (1: the pairs of one grid shape share each pass's
+ * launches; 0: a launch per pair) and schedule (0: one branch stream per
+ * unit; 1: two staggered lanes; ignored with a single unit).  Every
+ * configuration computes the same results bit for bit (the same arithmetic
+ * per pair; only the launch grouping and the stream order differ).  Waits
+ * for the context's stream and drops its captured step graphs.  PM_E_ARG
+ * for values other than 0 and 1. */
+int pm_set_launch_config(pm_ctx *ctx, int32_t batched, int32_t schedule);
+
 /* Self-test of failure detection (no counterpart in the paper): launches one
  * block that waits, with the bounded wait the FFT passes use for their
  * tensor copies (2 s limit), on a barrier that nothing arrives at.  The wait

@@ -531,8 +531,6 @@ void set_units(pm_ctx *c, bool batched) {
     c->lanes = plan_lanes(c->units, c->geos);
 }
 
-// Times each solve schedule (one warm-up solve, then five between events,
-// on zeroed densities) with and without batching, and keeps the fastest.
 // Chooses the solve's launch configuration by timing: batched or per-pair
 // launches, and the two branch schedules.  Every configuration is timed
 // (four solves after one untimed) in three interleaved rounds and keeps its
@@ -1258,6 +1256,17 @@ void pm_destroy(pm_ctx *c) {
     for (cudaEvent_t e : c->ev_join) cudaEventDestroy(e);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     delete c;
+}
+
+int pm_set_launch_config(pm_ctx *c, int32_t batched, int32_t schedule) {
+    if (!c) return fail(PM_E_ARG, "ctx is NULL");
+    if ((batched != 0 && batched != 1) || (schedule != 0 && schedule != 1))
+        return fail(PM_E_ARG, "batched and schedule must be 0 or 1");
+    PM_CK(cudaStreamSynchronize(c->user));
+    destroy_graph(c);   // captured with the previous configuration's launches
+    set_units(c, batched != 0);
+    c->sched = c->units.size() < 2 ? 0 : schedule;
+    return PM_OK;
 }
 
 int pm_set_stream(pm_ctx *c, void *stream) {

@@ -75,6 +75,7 @@ _SIGS.update({
     "pm_set_centres": (C.c_int, [_vp, _P(C.c_double)]),
     "pm_count_lost": (C.c_int, [_vp, _P(pm_particles), _P(C.c_int64)]),
     "pm_info": (C.c_int, [_vp, _P(C.c_int64)]),
+    "pm_set_launch_config": (C.c_int, [_vp, C.c_int32, C.c_int32]),
     "pm_step_timed": (C.c_int, [_vp, _P(pm_particles), C.c_double, C.c_int32, _P(C.c_float)]),
     "pm_sort": (C.c_int, [_vp, _P(pm_particles), _vp]),
     "pm_set_sort_interval": (C.c_int, [_vp, C.c_int32]),
@@ -399,6 +400,11 @@ class Context:
         """Status of the bounded-wait self-test (PM_E_TIMEOUT is the expected
         result: the wait gave up and the host saw it); see include/pm.h."""
         return int(lib().pm_selftest_wait_expiry(self.h))
+
+    def set_launch_config(self, batched, schedule):
+        """The solve's launch grouping (batched 1/0) and branch schedule
+        (0/1) in place of the ones timed fastest at creation."""
+        _check(lib().pm_set_launch_config(self.h, int(batched), int(schedule)))
 
     def info(self):
         out = (C.c_int64 * 6)()
