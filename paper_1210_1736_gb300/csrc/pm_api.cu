@@ -239,6 +239,7 @@ int check_device_error(pm_ctx *c) {
     int h = 0;
     PM_CK(cudaMemcpyAsync(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->user));
     PM_CK(cudaStreamSynchronize(c->user));
+    if (h == 2) return fail(PM_E_STATE, "an FFT pass was launched with a configuration it does not support");
     if (h) return fail(PM_E_TIMEOUT, "a tensor copy of an FFT pass did not complete within its time limit");
     return PM_OK;
 }

@@ -17,7 +17,7 @@ struct PairArgs {
     const void *tw;                       // exp(-2 pi i m / L), m < L, this pass's L
     int nx, ny, nz;
     double scale;                         // 2^-s
-    int *err;                             // set to 1 if a tensor copy never completes
+    int *err;                             // 1: a tensor copy never completed; 2: an unsupported launch
     // Difference fields of an unpaired grid (rho_b null).  D_L(k) =
     // exp(2 pi i k / L) - 1 multiplies the spectrum of a field f into that of
     // its forward difference f[n+1] - f[n]; dtx, dty, dtz are tables of D for

@@ -573,7 +573,7 @@ __global__ void __launch_bounds__(WShape<T, L>::THREADS, ((L >= 512 || DM == 2) 
     // are in registers and read from there for the multiply
     const bool hstage = !FREE && L >= 128 && S::COLS <= a.nx;
     if (DM == 2 && !hstage) {   // the fused mode reads H-hat from the staged rows only (the host checks)
-        if (threadIdx.x == 0) atomicExch(a.err, 1);
+        if (threadIdx.x == 0) atomicExch(a.err, 2);   // a launch the kernel does not support (not a wait)
         return;
     }
     bool hpend = false;   // thread 0: an H-hat copy not yet seen complete
