@@ -274,11 +274,11 @@ def fft_pairs(w):
 
 def fused_diff(spec):
     """A fine grid whose two difference-field z products come from one
-    forward transform in one launch (z length 128 or 256 with the tile's
-    H-hat rows staged: FP32 tile columns 4096 / L <= nx), as the library
-    plans it."""
+    forward transform in one launch (z length up to 64, or 128 and 256 with
+    the tile's H-hat rows staged: FP32 tile columns 4096 / L <= nx), as the
+    library plans it."""
     nx, nz = spec[0], spec[2]
-    return nz in (64, 128) and min(4096 // (2 * nz), 256) <= nx
+    return nz <= 32 or (nz in (64, 128) and min(4096 // (2 * nz), 256) <= nx)
 
 
 def fft_launches(w, batched=True):

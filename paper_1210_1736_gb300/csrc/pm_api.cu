@@ -410,8 +410,10 @@ template <typename T> int launch_pass(pm_ctx *c, int pass, cudaStream_t st, int 
                         a.tw = c->d_tw[tw_index(2 * sg.nz)];
                         if (!pr.diff) {
                             main.add(a, &pr.zmap);
-                        } else if ((sg.nz == 64 || sg.nz == 128) && pm_col_cols(2 * sg.nz, (int)c->esz) <= sg.nx) {
-                            // both difference fields from one forward transform
+                        } else if (sg.nz <= 32 ||
+                                   ((sg.nz == 64 || sg.nz == 128) && pm_col_cols(2 * sg.nz, (int)c->esz) <= sg.nx)) {
+                            // both difference fields from one forward transform (H-hat read from the
+                            // thread-major table, L <= 64, or from the tile's staged rows)
                             a.dmode = 3;
                             d1.add(a, &pr.zmap, &pr.zmap2);
                         } else {

@@ -728,7 +728,7 @@ template <typename T, int L> cudaError_t attrs_L() {
     e = cudaFuncSetAttribute(pmk::k_colw<T, L, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)pmk::colw_smem<T, L>());
     if (e) return e;
-    if constexpr (L == 128 || L == 256) {
+    if constexpr (L <= 256) {
         e = cudaFuncSetAttribute(pmk::k_colw<T, L, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)pmk::colw_smem<T, L>());
         if (e) return e;
@@ -802,7 +802,7 @@ template <typename T, int L> cudaError_t zconv_L(PassBatch b, cudaStream_t st) {
     b.lgi = ilog2(((long long)4 * b.a[0].ny * b.a[0].nx) / S::COLS);   // COLS divides the 2ny x 2nx columns
     const long long ntiles = (long long)b.n << b.lgi;
     const bool dm = b.a[0].dmode != 0;
-    if constexpr (L == 128 || L == 256) {
+    if constexpr (L <= 256) {
         if (b.a[0].dmode == 3) {   // both difference fields in one pass (see PairArgs)
             long long g2 = (long long)colw_blocks_per_sm<T, L, 2>() * num_sms();
             if (g2 > ntiles) g2 = ntiles;

@@ -24,9 +24,10 @@ struct PairArgs {
     // the x, y and z lengths.  dmode (z pass): 0 multiplies by H-hat,
     // 1 by H-hat (D_x + i D_y), 2 by H-hat (D_z + i); the inverse of a real
     // field's spectrum times such a factor is fx + i fy, or fz + i Phi.
-    // 3: both from one forward transform (L = 128 and 256 when the tile's
-    // H-hat rows are staged, COLS <= nx): fx + i fy through smap, then
-    // fz + i Phi in place through lmap.
+    // 3: both from one forward transform (L <= 64, H-hat from the
+    // thread-major table; L = 128 and 256 when the tile's H-hat rows are
+    // staged, COLS <= nx): fx + i fy through smap, then fz + i Phi in place
+    // through lmap.
     const void *dtx, *dty, *dtz;
     int dmode;
     int split;                            // x inverse: phi_sum = Re, phi_b = Im (no sum)

@@ -572,7 +572,7 @@ __global__ void __launch_bounds__(WShape<T, L>::THREADS, ((L >= 512 || DM == 2) 
     // BUF bytes; it is copied into the tile's input buffer once the inputs
     // are in registers and read from there for the multiply
     const bool hstage = !FREE && L >= 128 && S::COLS <= a.nx;
-    if (DM == 2 && !hstage) {   // the fused mode reads H-hat from the staged rows only (the host checks)
+    if (DM == 2 && !hstage && !hhat_thread_major(L)) {   // the fused mode's H-hat sources (the host checks)
         if (threadIdx.x == 0) atomicExch(a.err, 2);   // a launch the kernel does not support (not a wait)
         return;
     }
@@ -693,6 +693,55 @@ __global__ void __launch_bounds__(WShape<T, L>::THREADS, ((L >= 512 || DM == 2) 
             f.y *= h;
             v[e] = cmul(v[e], f);
         };
+        // DM == 2: both difference fields from the one forward transform:
+        // u = S H-hat (D_x + i D_y) -> fx + i fy (work2, through smap), then
+        // v = S H-hat (D_z + i) -> fz + i Phi_1 (in place, through lmap, by
+        // the common code below).  hz: the column's H-hat values, indexed by
+        // the mirrored kz (staged rows) or by the register (thread-major
+        // table); false after an expired wait (the caller stops).
+        auto fused = [&](const T *hz, bool mirrored, bool ok) -> bool {
+            C u[E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                constexpr int RLF = radix(L, NS - 1, false);
+                const int kz = pmfft::in_row<L, NS - 1, false>(t, e / RLF, e % RLF);
+                const T h = mirrored ? hz[kz <= L / 2 ? kz : L - kz] : __ldg(hz + e);
+                C f1 = dxy, f2 = static_cast<const C *>(a.dtz)[kz];
+                f2.y += (T)1;
+                f1.x *= h; f1.y *= h;
+                f2.x *= h; f2.y *= h;
+                u[e] = cmul(v[e], f1);
+                v[e] = cmul(v[e], f2);
+            }
+            if constexpr (!IREV) pmfft::regs_last_to_first<L>(u);
+            pmfft::fft_core<L, IREV, 1, false, true, true>(u, xch, lay, t, tw);
+            // every H-hat read done before the outputs overwrite the buffer
+            if (!__syncthreads_and(ok ? 1 : 0)) {
+                failed = true;
+                if (tid == 0 && hpend) mbar_wait(&hfull[b], phase);   // let the copy land (bounded)
+                return false;
+            }
+            {
+                constexpr int RL = radix(L, NS - 1, IREV);
+#pragma unroll
+                for (int kk = 0; kk < E / RL; ++kk)
+#pragma unroll
+                    for (int r = 0; r < RL / 2; ++r)
+                        *reinterpret_cast<C *>(in + woff<T, L, S::RIN>(pmfft::in_row<L, NS - 1, IREV>(t, kk, r), c)) =
+                            u[kk * RL + r];
+            }
+            fence_async_smem();
+            __syncthreads();
+            if (tid == 0) {
+                issue_store(tile, in);
+                bulk_commit();
+                bulk_wait_read();   // read out before the second outputs overwrite the buffer
+            }
+            __syncthreads();
+            if constexpr (!IREV) pmfft::regs_last_to_first<L>(v);
+            pmfft::fft_core<L, IREV, 1, false, true, true>(v, xch, lay, t, tw);
+            return true;
+        };
         bool hok = true;
         if (hstage) {
             // H-hat of column c from the staged rows (row c, or COLS-1-c
@@ -701,50 +750,7 @@ __global__ void __launch_bounds__(WShape<T, L>::THREADS, ((L >= 512 || DM == 2) 
             if (hok && tid == 0) hpend = false;
             const T *hz = reinterpret_cast<const T *>(in) + (k0 < a.nx ? c : S::COLS - 1 - c) * S::HS;
             if constexpr (DM == 2) {
-                // both difference fields from the one forward transform:
-                // u = S H-hat (D_x + i D_y) -> fx + i fy (work2, through
-                // smap), then v = S H-hat (D_z + i) -> fz + i Phi_1 (in
-                // place, through lmap, below)
-                C u[E];
-#pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    constexpr int RLF = radix(L, NS - 1, false);
-                    const int kz = pmfft::in_row<L, NS - 1, false>(t, e / RLF, e % RLF);
-                    const T h = hz[kz <= L / 2 ? kz : L - kz];
-                    C f1 = dxy, f2 = static_cast<const C *>(a.dtz)[kz];
-                    f2.y += (T)1;
-                    f1.x *= h; f1.y *= h;
-                    f2.x *= h; f2.y *= h;
-                    u[e] = cmul(v[e], f1);
-                    v[e] = cmul(v[e], f2);
-                }
-                if constexpr (!IREV) pmfft::regs_last_to_first<L>(u);
-                pmfft::fft_core<L, IREV, 1, false, true, true>(u, xch, lay, t, tw);
-                // every H-hat read done before the outputs overwrite the buffer
-                if (!__syncthreads_and(hok ? 1 : 0)) {
-                    failed = true;
-                    if (tid == 0 && hpend) mbar_wait(&hfull[b], phase);   // let the copy land (bounded)
-                    break;
-                }
-                {
-                    constexpr int RL = radix(L, NS - 1, IREV);
-#pragma unroll
-                    for (int kk = 0; kk < E / RL; ++kk)
-#pragma unroll
-                        for (int r = 0; r < RL / 2; ++r)
-                            *reinterpret_cast<C *>(
-                                in + woff<T, L, S::RIN>(pmfft::in_row<L, NS - 1, IREV>(t, kk, r), c)) = u[kk * RL + r];
-                }
-                fence_async_smem();
-                __syncthreads();
-                if (tid == 0) {
-                    issue_store(tile, in);
-                    bulk_commit();
-                    bulk_wait_read();   // read out before the second outputs overwrite the buffer
-                }
-                __syncthreads();
-                if constexpr (!IREV) pmfft::regs_last_to_first<L>(v);
-                pmfft::fft_core<L, IREV, 1, false, true, true>(v, xch, lay, t, tw);
+                if (!fused(hz, true, hok)) break;
             } else {
 #pragma unroll
                 for (int e = 0; e < E; ++e) hmul(e, hz[kz_mirror(e)]);
@@ -765,7 +771,9 @@ __global__ void __launch_bounds__(WShape<T, L>::THREADS, ((L >= 512 || DM == 2) 
             const int kyr = ky <= a.ny ? ky : ny2 - ky;
             const int kxr = kx <= a.nx ? kx : nx2 - kx;
             const T *hcol = hhat + ((size_t)kyr * (a.nx + 1) + kxr) * S::HS;
-            if constexpr (hhat_thread_major(L)) {
+            if constexpr (DM == 2 && hhat_thread_major(L)) {
+                if (!fused(hcol + t * E, false, true)) break;
+            } else if constexpr (hhat_thread_major(L)) {
                 const T *hz = hcol + t * E;   // 16-byte aligned: L, E multiples of 16
                 if constexpr (sizeof(T) == 4) {
 #pragma unroll
@@ -791,8 +799,10 @@ __global__ void __launch_bounds__(WShape<T, L>::THREADS, ((L >= 512 || DM == 2) 
 #pragma unroll
                 for (int e = 0; e < E; ++e) hmul(e, __ldg(hcol + kz_mirror(e)));
             }
-            if constexpr (!IREV) pmfft::regs_last_to_first<L>(v);
-            pmfft::fft_core<L, IREV, 1, false, true, true>(v, xch, lay, t, tw);
+            if constexpr (DM != 2) {   // (the fused mode ran both inverses)
+                if constexpr (!IREV) pmfft::regs_last_to_first<L>(v);
+                pmfft::fft_core<L, IREV, 1, false, true, true>(v, xch, lay, t, tw);
+            }
         }
         {
             // inverse outputs below L/2: registers r < RL/2 of the last

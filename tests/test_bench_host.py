@@ -42,12 +42,12 @@ def test_launch_count_per_pair():
     g = W.galaxy_small()
     assert bench.fft_pairs(g) == 3
     # galaxy_small: shapes 32^3 (coarse and medium pairs) and 32x32x8 (the
-    # fine grid): x, y forward 2 + 2, z 1 + 2, y, x inverse 2 + 2 -> 11;
+    # fine grid): x, y forward 2 + 2, z 1 + 1, y, x inverse 2 + 2 -> 10;
     # per step also recentre (2), deposit (1), force (1); six sort kernels
     # every sort_every-th step
-    assert bench.fft_launches(g) == 11
-    assert bench.launches(g, 10, 0) == 10 * (2 + 1 + 11 + 1)
-    assert bench.launches(g, 10, 5) == 10 * 15 + 2 * 6
+    assert bench.fft_launches(g) == 10
+    assert bench.launches(g, 10, 0) == 10 * (2 + 1 + 10 + 1)
+    assert bench.launches(g, 10, 5) == 10 * 14 + 2 * 6
     # large_16m: the satellites' six 128^3 pairs (two of them fine grids)
     # share launches: x 1, y 1, z 1 + 1 (both difference fields of the two
     # fine grids in one launch), y inverse 1, x inverse 1; the galaxy's
@@ -57,10 +57,11 @@ def test_launch_count_per_pair():
         dict(coarse=(128, 128, 128, 32, 1), medium=(128, 128, 128, 0.5, 1), fine=(128, 128, 128, 0.125, 1)),
         dict(coarse=(128, 128, 128, 32, 1), medium=(128, 128, 128, 0.5, 1), fine=(128, 128, 128, 0.125, 1))])
     assert bench.fused_diff((256, 256, 64)) and bench.fused_diff((128, 128, 128))
-    assert not bench.fused_diff((32, 32, 8)) and not bench.fused_diff((128, 128, 32))
+    assert bench.fused_diff((32, 32, 8)) and bench.fused_diff((128, 128, 32))
     assert not bench.fused_diff((16, 16, 64))   # 32 tile columns > nx: two launches
+    assert not bench.fused_diff((256, 256, 256))   # length 512: two launches
     assert bench.fft_launches(spec) == (2 + 1 + 2) + (2 + 1 + 2) + (2 + 2 + 2)
     # unbatched: five launches per pair and two more per fused fine grid
     # (three where the two difference-field products take two launches)
     assert bench.fft_launches(spec, batched=False) == 5 * 9 + 2 * 3
-    assert bench.fft_launches(W.galaxy_small(), batched=False) == 5 * 3 + 3
+    assert bench.fft_launches(W.galaxy_small(), batched=False) == 5 * 3 + 2

@@ -1,9 +1,10 @@
 """The fine grid's two difference-field convolutions (the spectral factors
 H-hat (D_x + i D_y) and H-hat (D_z + i) of Eq. eqn:diff's forward
-differences) from one forward z transform, at the two lengths that take that
-path (z transforms of 128 and 256 with the tile's H-hat rows staged): nested
-galaxies with fine grids of 32 x 32 x 64 and 16 x 16 x 128 cells against the
-oracle, FP64 and FP32."""
+differences) from one forward z transform, through both H-hat sources of
+that path (the tile's staged rows at z lengths 128 and 256, the thread-major
+table at 64 and below): nested galaxies with fine grids of 32 x 32 x 64,
+16 x 16 x 128, 32 x 32 x 32 and 16 x 16 x 16 cells against the oracle, FP64
+and FP32."""
 import numpy as np
 import pytest
 
@@ -23,14 +24,14 @@ def _galaxy_with_fine(fine, precision):
     return w
 
 
-@pytest.mark.parametrize("fine", [(32, 32, 64, 0.25), (16, 16, 128, 0.1)])
+@pytest.mark.parametrize("fine", [(32, 32, 64, 0.25), (16, 16, 128, 0.1), (32, 32, 32, 0.5), (16, 16, 16, 1.0)])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_fused_difference_fields(precision, fine):
     w = _galaxy_with_fine(fine, precision)
     ctx, parts = gpu_setup(w)
     system, state = oracle_setup(w)
     rho, phi, flags, own, s = oracle_fields(system, state)
-    assert np.count_nonzero(rho[0][1]) > 1000   # grid 1 holds mass
+    assert np.count_nonzero(rho[0][1]) > 500   # grid 1 holds mass
     a_gpu = _gpu_fields(ctx, parts)
     _compare_density_and_flags(ctx, parts, system, rho, flags)
     a_ref = O.accelerations(state, system, phi, flags)
