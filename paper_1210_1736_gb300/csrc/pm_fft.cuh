@@ -5,7 +5,8 @@
 // Each transform of length L is done by L/16 threads holding 16 values each;
 // stages are radix-16 (plus one radix-2/4/8 stage where L is not a power of
 // 16) in the self-sorting Stockham order, exchanging through shared memory
-// laid out [row][column] so that a warp's accesses are contiguous.
+// laid out so that a warp's accesses are conflict-free, or, into a closing
+// radix-2 stage of a transform held by one warp, by warp shuffles.
 #pragma once
 
 #include "pm_internal.cuh"
@@ -328,8 +329,9 @@ __host__ __device__ constexpr bool inv_fwd_plan(int L) { return nstages(L) > 1 &
 // All threads of the block must call it (it synchronises).
 // ZIN: the inputs of rows >= L/2 are zero (forward transforms of padded
 // data; the first stage is radix 16 and only registers r < 8 are read).
-// HOUT: only the outputs of rows < L/2 are used (inverse transforms; the
-// last stage of a reversed plan is radix 16, outputs in registers r < 8).
+// HOUT: only the outputs of rows < L/2 are used (inverse transforms: a
+// radix-16 last stage keeps registers r < 8, a closing radix-2 stage its
+// registers 2k).
 // WSYNC: a transform's TPC threads are the consecutive lanes t = lane % TPC
 // of one warp and its exchange area is touched by that warp only, so the
 // exchanges synchronise the warp instead of the block, and an exchange into
