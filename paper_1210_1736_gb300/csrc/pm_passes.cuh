@@ -427,8 +427,10 @@ __global__ void __launch_bounds__(CShape<T, L>::THREADS, 3) k_col(const __grid_c
 // kernel's address function agree, so the first-stage reads are free of bank
 // conflicts).  The L/16 threads of a column are consecutive lanes of one
 // warp, so the stage exchanges use a private padded row per column and
-// synchronise the warp only.  For L = 128, 256 the tile's H-hat rows arrive
-// by one bulk copy into the consumed input buffer during the forward FFT.
+// synchronise the warp only (and the exchange into a closing radix-2 stage,
+// at L = 32 and 512, goes by shuffles).  For L = 128, 256 the tile's H-hat
+// rows arrive by one bulk copy into the consumed input buffer during the
+// forward FFT.
 // The outputs (rows < L/2) are staged into the tile's own buffer and leave by
 // TMA store; the buffer then takes the prefetch of the tile two steps ahead.
 // (The same structure measured slower than k_col for the y passes, so those
@@ -497,9 +499,11 @@ __device__ __forceinline__ uint32_t woff(int row, int c) {
 // for the loads; B.smap, the same boxes, for the stores (the same map in
 // place, another work array's for the first difference-field pass).  DM = 0:
 // the spectral factor is H-hat; DM = 1 (difference fields): H-hat
-// (D_x + i D_y) for dmode 1, H-hat (D_z + i) for dmode 2 (see PairArgs).
-// The modes are separate instantiations so that the plain pass carries no
-// mode branch.
+// (D_x + i D_y) for dmode 1, H-hat (D_z + i) for dmode 2 (see PairArgs);
+// DM = 2 (dmode 3, L <= 256): both from one forward transform, the first
+// products' outputs stored through smap, the second's in place through
+// lmap.  The modes are separate instantiations so that the plain pass
+// carries no mode branch.
 template <typename T, int L, int DM>
 __global__ void __launch_bounds__(WShape<T, L>::THREADS, ((L >= 512 || DM == 2) ? 2 : 3))
     k_colw(const __grid_constant__ PassBatch B) {
