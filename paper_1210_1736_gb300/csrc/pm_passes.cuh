@@ -282,11 +282,22 @@ template <> struct ColRows<COL_YFWD> { __host__ __device__ static constexpr int 
 template <> struct ColRows<COL_ZCONV> { __host__ __device__ static constexpr int of(int L) { return L / 2; } };
 template <> struct ColRows<COL_YINV> { __host__ __device__ static constexpr int of(int L) { return L; } };
 
+// Input buffers of the y pass: two (a tile prefetched two ahead), or one
+// for the FP32 512-point inverse, whose 32 KB tiles would otherwise hold it
+// to two blocks per SM by shared memory (one buffer: three, as its registers
+// allow; the next tile's load still runs during this tile's transform, which
+// has read its inputs into registers first).
+template <typename T, int L, int MODE> __host__ __device__ constexpr int col_nbuf() {
+    return (MODE == COL_YINV && L == 512 && sizeof(T) == 4) ? 1 : 2;
+}
+// Shared memory of a y pass: the input buffers, the exchange buffer and the
+// stage twiddles of the one plan the pass runs (forward, or reversed for the
+// inverse).
 template <typename T, int L, int MODE> constexpr size_t col_smem() {
     typedef typename cplx_t<T>::type C;
     constexpr int COLS = CShape<T, L>::COLS;
-    return 128 + (size_t)pmfft::tw_total(L) * sizeof(C) + (size_t)L * COLS * sizeof(C) +
-           2 * (size_t)ColRows<MODE>::of(L) * COLS * sizeof(C) + 3 * 128;
+    return 128 + (size_t)pmfft::tw_dir_size(L, MODE == COL_YINV) * sizeof(C) + (size_t)L * COLS * sizeof(C) +
+           col_nbuf<T, L, MODE>() * (size_t)ColRows<MODE>::of(L) * COLS * sizeof(C) + 3 * 128;
 }
 
 // Persistent y pass (forward or inverse) over a batch: the items' maps
@@ -305,14 +316,18 @@ __global__ void __launch_bounds__(CShape<T, L>::THREADS, 3) k_col(const __grid_c
     constexpr unsigned TILE_BYTES = (unsigned)(ROWS * COLS * sizeof(C));
     constexpr bool REV_IN = (MODE == COL_YINV);
     constexpr int SIGN_IN = (MODE == COL_YINV) ? 1 : -1;
+    constexpr int NBUF = col_nbuf<T, L, MODE>();
 
     extern __shared__ __align__(128) unsigned char smraw[];
     unsigned char *base = reinterpret_cast<unsigned char *>(((uintptr_t)smraw + 127) & ~(uintptr_t)127);
     uint64_t *bar = reinterpret_cast<uint64_t *>(base);                 // 2 mbarriers
     C *buf0 = reinterpret_cast<C *>(base + 128);
-    C *buf1 = buf0 + ROWS * COLS;
-    C *sm = buf1 + ROWS * COLS;
-    C *tw = sm + L * COLS;
+    C *buf1 = NBUF == 2 ? buf0 + ROWS * COLS : buf0;
+    C *sm = buf0 + NBUF * ROWS * COLS;
+    // only this pass's plan's tables follow the exchange buffer: for the
+    // reversed plan, the forward tables' offsets fall on the exchange
+    // buffer's tail and are never read
+    C *tw = sm + L * COLS - (REV_IN ? pmfft::tw_dir_size(L, false) : 0);
     const int tid = threadIdx.x;
     const int c = tid % COLS, t = tid / COLS;
     const int nx2 = 2 * B.a[0].nx, ny2 = 2 * B.a[0].ny;   // the items' common shape, read once
@@ -346,27 +361,30 @@ __global__ void __launch_bounds__(CShape<T, L>::THREADS, 3) k_col(const __grid_c
         mbar_init(&bar[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    pmfft::expand_twiddles<L>(tw, static_cast<const C *>(B.a[0].tw));
+    pmfft::expand_stage_twiddles<L, 1, REV_IN>(tw, static_cast<const C *>(B.a[0].tw));
+    pmfft::expand_stage_twiddles<L, 2, REV_IN>(tw, static_cast<const C *>(B.a[0].tw));
     __syncthreads();
     pdl_wait();
     int issued[2] = {0, 0};   // loads issued per buffer (thread 0's count)
     if (tid == 0) {
         if (blockIdx.x < ntiles) { issue(blockIdx.x, 0); ++issued[0]; }
-        if (blockIdx.x + gridDim.x < ntiles) { issue(blockIdx.x + gridDim.x, 1); ++issued[1]; }
+        if (NBUF == 2 && blockIdx.x + gridDim.x < ntiles) { issue(blockIdx.x + gridDim.x, 1); ++issued[1]; }
     }
 
     int it = 0;
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
         if (tile + gridDim.x >= ntiles) pdl_release();
-        const int b = it & 1;
-        const unsigned phase = (unsigned)((it >> 1) & 1);
+        const int b = NBUF == 2 ? (it & 1) : 0;
+        const unsigned phase = NBUF == 2 ? (unsigned)((it >> 1) & 1) : (unsigned)(it & 1);
         // a tensor copy that never lands: report, wait (bounded) for the other
         // copy in flight, stop; the decision is the same for the whole block
         if (!__syncthreads_and(mbar_wait(&bar[b], phase) ? 1 : 0)) {
             if (tid == 0) {
                 atomicExch(err, 1);
-                const int o = b ^ 1, used_o = it >> 1;   // uses of buffer o completed so far
-                if (issued[o] > used_o) mbar_wait(&bar[o], (unsigned)(used_o & 1));
+                if (NBUF == 2) {
+                    const int o = b ^ 1, used_o = it >> 1;   // uses of buffer o completed so far
+                    if (issued[o] > used_o) mbar_wait(&bar[o], (unsigned)(used_o & 1));
+                }
             }
             break;
         }
@@ -385,9 +403,9 @@ __global__ void __launch_bounds__(CShape<T, L>::THREADS, 3) k_col(const __grid_c
         // buffer before this tile's stages write to it
         if (tid == 0) bulk_wait_read();
         __syncthreads();   // buffer b consumed, previous tile's exchange done
-        if (tid == 0 && tile + 2 * (long long)gridDim.x < ntiles) {
+        if (tid == 0 && tile + NBUF * (long long)gridDim.x < ntiles) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            issue(tile + 2 * (long long)gridDim.x, b);
+            issue(tile + NBUF * (long long)gridDim.x, b);
             ++issued[b];
         }
 
