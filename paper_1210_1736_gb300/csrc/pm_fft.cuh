@@ -242,6 +242,21 @@ struct ColLayout {              // [row][ldc] array, transform = column c
     int ldc, c;
     __device__ __forceinline__ int operator()(int row) const { return row * ldc + c; }
 };
+// [row][ldc] array of 64-byte rows (half the banks; 8-byte accesses run in
+// half-warps, two rows of a column group at once).  Row `row` is stored at
+// row ^ flip(row), flip = parity of row bits 1 and 4, so that the two rows a
+// half-warp touches (1 apart from an even row, 2 apart in a radix-2 first
+// stage, 16 apart in a radix-16 first stage) land on different bank halves;
+// a bijection of [0, L).  Every exchange row of a stage is X | K, X from the
+// thread and K a compile-time constant on disjoint bits, and flip is linear
+// in the bits, so the offset is one of two per-thread bases plus a constant
+// (store_stage / load_stage below): no address arithmetic per access.
+struct ColLayoutHalf {
+    int ldc, c;
+    __host__ __device__ static constexpr int flip(int x) { return ((x >> 1) ^ (x >> 4)) & 1; }
+    // offset of X | K = base(X, flip(K) ^ (K & 1)) + (K & ~1) * ldc
+    __device__ __forceinline__ int base(int X, int b) const { return (X ^ flip(X) ^ b) * ldc + c; }
+};
 struct RowLayout {              // one transform per padded row: a pad element
     int base;                   // after every 16 keeps the strides of the
     __device__ __forceinline__ int operator()(int row) const { return base + row + (row >> 4); }
@@ -264,6 +279,36 @@ __device__ __forceinline__ void load_stage(const C *sm, const LAY &lay, int t, C
     for (int kk = 0; kk < E / R; ++kk)
 #pragma unroll
         for (int r = 0; r < R; ++r) v[kk * R + r] = sm[lay(in_row<L, S, REV>(t, kk, r))];
+}
+// The stage exchanges with ColLayoutHalf (t < TPC): a store of stage S
+// writes row X | K with X = (t / Ns) Ns R + t mod Ns, K = kk TPC R + r Ns
+// (Ns divides TPC in every stage that stores); a load reads X = t,
+// K = kk TPC + r L/R.
+template <int L, int S, bool REV, typename C>
+__device__ __forceinline__ void store_stage(C *sm, const ColLayoutHalf &lay, int t, const C *v) {
+    constexpr int R = radix(L, S, REV), Ns = stride_before(L, S, REV), TPC = L / E;
+    static_assert(TPC % Ns == 0, "a stage that stores has Ns dividing TPC");
+    const int X = (t / Ns) * Ns * R + t % Ns;
+    const int b0 = lay.base(X, 0), b1 = lay.base(X, 1);
+#pragma unroll
+    for (int kk = 0; kk < E / R; ++kk)
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int K = kk * TPC * R + r * Ns;
+            sm[((ColLayoutHalf::flip(K) ^ (K & 1)) ? b1 : b0) + (K & ~1) * lay.ldc] = v[kk * R + r];
+        }
+}
+template <int L, int S, bool REV, typename C>
+__device__ __forceinline__ void load_stage(const C *sm, const ColLayoutHalf &lay, int t, C *v) {
+    constexpr int R = radix(L, S, REV), TPC = L / E;
+    const int b0 = lay.base(t, 0), b1 = lay.base(t, 1);
+#pragma unroll
+    for (int kk = 0; kk < E / R; ++kk)
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int K = kk * TPC + r * (L / R);
+            v[kk * R + r] = sm[((ColLayoutHalf::flip(K) ^ (K & 1)) ? b1 : b0) + (K & ~1) * lay.ldc];
+        }
 }
 template <int L, int S, bool REV, typename C>
 __device__ __forceinline__ void store_stage(C *sm, int ldc, int c, int t, const C *v) {

@@ -410,7 +410,11 @@ __global__ void __launch_bounds__(CShape<T, L>::THREADS, 3) k_col(const __grid_c
         }
 
         static_assert(MODE == COL_YFWD || MODE == COL_YINV, "the z pass is k_colw");
-        pmfft::fft_core<L, REV_IN, SIGN_IN, MODE != COL_YINV, MODE == COL_YINV>(v, sm, COLS, c, t, tw);
+        if constexpr (COLS * sizeof(C) == 64)   // FP32, L = 512: rows of 8 columns
+            pmfft::fft_core<L, REV_IN, SIGN_IN, MODE != COL_YINV, MODE == COL_YINV, false>(
+                v, sm, pmfft::ColLayoutHalf{COLS, c}, t, tw);
+        else
+            pmfft::fft_core<L, REV_IN, SIGN_IN, MODE != COL_YINV, MODE == COL_YINV>(v, sm, COLS, c, t, tw);
         // fft_core ends with a block barrier after its last exchange reads:
         // the exchange buffer takes the outputs, rows in_row of the last
         // stage (the inverse keeps rows < L/2: registers r < RL/2)
