@@ -214,9 +214,12 @@ def phase_bytes(w, n, esz):
     """Algorithmic HBM bytes per step of each phase (byte model): spectra are
     complex of 2*esz bytes; per mass set A = nx ny nz, S1 = (nx+1) ny nz,
     S2 = (nx+1) 2ny nz; H-hat read once per geometry launch.  Grid 1 (the
-    fine grid, solved for its difference fields) adds a second z pass that
-    reads the spectrum again and writes a second one, a second y inverse,
-    and x inverse passes that write four real fields (fx, fy, fz, Phi_1)."""
+    fine grid, solved for its difference fields) is counted as two real
+    fields' chains from the z pass on (z: 4 S2, y inverse: 2 (S2 + S1), x
+    inverse: 2 S1 reads and four real fields fx, fy, fz, Phi_1 written),
+    below the R2C minimum for the four real fields it produces from one
+    spectrum (z: one read and four writes, 5 S2; y inverse: 4 (S2 + S1); x
+    inverse: 4 S1 + 4 A), so its fractions are understated, not inflated."""
     cz = 2 * esz
     b = dict.fromkeys(PHASES, 0.0)
     geoms = {}
