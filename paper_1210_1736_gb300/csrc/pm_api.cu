@@ -383,8 +383,10 @@ template <typename T> cudaError_t launch_items(int pass, const BatchItems &it, s
 // One pass of every pair of the units (only >= 0: of unit `only`); a
 // unit's pairs share each pass's launches when the context batches (the
 // pairs of a unit then have one shape).  A grid 1 pair (diff) takes part in
-// the forward passes like any other; its z pass runs twice (H-hat
-// (D_x + i D_y) into work2, then H-hat (D_z + i) in place), and its inverse
+// the forward passes like any other; its z pass forms H-hat (D_x + i D_y)
+// into work2 and H-hat (D_z + i) in place, in one launch from one forward
+// transform (dmode 3: z lengths up to 64, and 128 and 256 where a tile's
+// columns fit in nx) or else in two launches (dmode 1, then 2); its inverse
 // passes run on both work arrays: fx + i fy -> fx, fy; fz + i Phi_1 -> fz,
 // Phi_1.
 template <typename T> int launch_pass(pm_ctx *c, int pass, cudaStream_t st, int only = -1, int shift = INT_MIN) {
