@@ -12,11 +12,17 @@
 //   y inverse : columns (z, kx), all 2ny inputs, outputs y < ny
 //   x inverse : rows (z, y < ny), outputs x < nx: Phi_b = Im, Phi_a + Phi_b
 //
+// Grid 1 (the fine grid, a set without partner) is solved for its
+// difference fields: its z pass writes H-hat (D_x + i D_y) rho-hat to a
+// second work array and H-hat (D_z + i) rho-hat in place, and its inverse
+// passes run on both (fx + i fy, fz + i Phi_1).
+//
 // The column passes are persistent: each block walks tiles of COLS adjacent
 // columns; a TMA tensor copy brings the next-but-one tile's input rows into
-// shared memory (double buffer, mbarrier completion) while the block
-// transforms the current one; the y passes store their outputs from
-// registers, the z pass stages them in shared memory for a TMA store.
+// shared memory (two buffers, mbarrier completion; the FP32 512-point y
+// inverse keeps one and loads the next tile) while the block transforms the
+// current one; every column pass stages its outputs in shared memory and
+// sends them by TMA store.
 #pragma once
 
 #include <cuda.h>
