@@ -155,7 +155,12 @@ int pm_kick_drift(pm_ctx *ctx, const pm_particles *p, double dt);
 int pm_deposit(pm_ctx *ctx, const pm_particles *p);
 
 /* Steps a4-a7 (Sec. 2.1): for every grid, zero-pad, forward real 3D FFT,
- * multiply by H-hat, inverse FFT, keep the active region -> Phi. */
+ * multiply by H-hat, inverse FFT, keep the active region -> Phi.  Grid 1
+ * (the fine grid) is also solved for the forward differences of Phi_1
+ * along x, y and z (its spectrum times H-hat (e^{2 pi i k/L} - 1) per axis,
+ * the same discrete values as differencing Phi_1), which pm_force uses for
+ * Eq. eqn:diff on that grid; Phi_1 itself is kept as well.  Enqueued on the
+ * context's stream, in the launch configuration pm_info reports. */
 int pm_solve(pm_ctx *ctx);
 
 /* Step a8 (Eq. eqn:diff + combination rule): acceleration of each particle
