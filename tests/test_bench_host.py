@@ -1,5 +1,6 @@
-"""Host logic of bench.py (CPU): the byte model behind the roofline numbers
-and the count of kernel launches it claims.
+"""Host logic of bench.py (CPU): the byte model behind the roofline numbers,
+the count of kernel launches it claims, and the rule that a stored DRAM
+traffic figure is used only on the kernel code it was captured on.
 
 Byte model per mass set of A = nx ny nz active cells (8-byte complex
 spectra, S1 = (nx+1) ny nz): x forward 8A + 8 S1, y forward 8 S1 + 16 S1,
@@ -65,3 +66,45 @@ def test_launch_count_per_pair():
     # (three where the two difference-field products take two launches)
     assert bench.fft_launches(spec, batched=False) == 5 * 9 + 2 * 3
     assert bench.fft_launches(W.galaxy_small(), batched=False) == 5 * 3 + 2
+
+
+def test_grid1_counted_below_its_r2c_minimum():
+    # grid 1 gives four real fields (fx, fy, fz, Phi_1) from one spectrum;
+    # the byte model counts its z, y-inverse and x-inverse passes as two
+    # real fields' chains, below the R2C minimum of four
+    base = dict(coarse=(64, 64, 64, 32.0, 1.0), medium=(64, 64, 64, 6.0, 0.25))
+    with1 = bench.phase_bytes(dict(galaxies=[dict(base, fine=(64, 64, 16, 1.5, 1.0))]), 0, 4)
+    without = bench.phase_bytes(dict(galaxies=[dict(base, fine=None)]), 0, 4)
+    nx, ny, nz = 64, 64, 16
+    A, S1 = nx * ny * nz, (nx + 1) * ny * nz
+    S2 = 2 * S1
+    hhat = 4 * (nx + 1) * (ny + 1) * (nz + 1)
+    d = {p: with1[p] - without[p] for p in with1}
+    assert d["fft_z_conv"] - hhat == 4 * 8 * S2 < 5 * 8 * S2
+    assert d["fft_y_inv"] == 2 * 8 * (S2 + S1) < 4 * 8 * (S2 + S1)
+    assert d["fft_x_inv"] == 2 * 8 * S1 + 4 * 4 * A < 4 * 8 * S1 + 4 * 4 * A
+
+
+def test_traffic_record_follows_the_kernel_code(tmp_path, monkeypatch):
+    # the stored DRAM traffic is used only while the kernel sources' code is
+    # the one it was captured on: comments do not count, code does
+    import json
+    import os
+    import shutil
+    csrc = os.path.join(tmp_path, "paper_1210_1736_gb300", "csrc")
+    shutil.copytree(os.path.join(bench.ROOT, "paper_1210_1736_gb300", "csrc"), csrc)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h0 = bench.kernel_source_hash()
+    os.makedirs(os.path.join(tmp_path, "profiles"))
+    rec = dict(source_hash=h0, workload="large_16m", phases=dict(fft_z_conv=1.5e9))
+    json.dump(rec, open(os.path.join(tmp_path, "profiles", "traffic.json"), "w"))
+    assert bench.ncu_traffic("fft_z_conv", "large_16m") == 1.5e9
+    assert bench.ncu_traffic("fft_z_conv", "galaxy_1m") is None
+    f = os.path.join(csrc, "pm_passes.cuh")
+    src = open(f).read()
+    open(f, "w").write(src + "\n// a comment\n/* and a\n   block comment */\n")
+    assert bench.kernel_source_hash() == h0
+    assert bench.ncu_traffic("fft_z_conv", "large_16m") == 1.5e9
+    open(f, "w").write(src + "\nstatic const int pm_unused_constant = 1;\n")
+    assert bench.kernel_source_hash() != h0
+    assert bench.ncu_traffic("fft_z_conv", "large_16m") is None
