@@ -252,6 +252,15 @@ def phase_bytes(w, n, esz):
     return b
 
 
+def phase_hbm_fracs(phase_ms, pb, peak):
+    """Each phase's byte-model bytes per step over its time per step, as a
+    fraction of the HBM peak (GB/s).  The particle phases count only their
+    streamed particle bytes (the gathers and atomics that L2 serves are not
+    in the model), so theirs are lower bounds; phases without a byte model
+    (the spatial sort) are left out."""
+    return {p: pb[p] / (t / 1e3) / 1e9 / peak for p, t in phase_ms.items() if pb.get(p) and t > 0}
+
+
 def bench_config(w, workload, n, world):
     """The `config` object of the JSON line, identical in both arms."""
     geoms = {tuple(g[k]) for g in w["galaxies"] for k in ("coarse", "medium", "fine") if g.get(k)}
@@ -484,7 +493,7 @@ def extra_workload(name, K, Wm, sort_every, fp64_steps):
                             "span_ms_per_step": dm["span_ms"]},
            "step_bound_frac": sum(dm["pb"].values()) / (peak * 1e9) * 1e3 / ms,
            "solve_schedule": ctx.info()["solve_schedule"], "batched": ctx.info()["batched"],
-           "phase_ms_per_step": dm["phase_ms"]}
+           "phase_ms_per_step": dm["phase_ms"], "phase_hbm_frac": phase_hbm_fracs(dm["phase_ms"], dm["pb"], peak)}
     if fp64 is not None:
         fp64["speedup_fp32"] = fp64["ms_per_step"] / ms
         out["fp64_path"] = fp64
@@ -598,6 +607,7 @@ def run_ours(args):
                          "note": "gbs/frac: the five pass phases timed one after another; span: pm_solve as "
                                  "the step runs it (geometry chains overlapping), byte model over time"},
         "phase_ms_per_step": phase_ms,
+        "phase_hbm_frac": phase_hbm_fracs(phase_ms, pb, peak),
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": Ke, "serial_value": e2e_serial,
                 "pipeline": "one-step requests rotating over three device buffers: upload of k+1 and download "

@@ -108,3 +108,13 @@ def test_traffic_record_follows_the_kernel_code(tmp_path, monkeypatch):
     open(f, "w").write(src + "\nstatic const int pm_unused_constant = 1;\n")
     assert bench.kernel_source_hash() != h0
     assert bench.ncu_traffic("fft_z_conv", "large_16m") is None
+
+
+def test_phase_fractions():
+    # 6.7934 GB in 1 ms is the measured copy bandwidth exactly; a phase
+    # without bytes (the sort) or without time is left out
+    f = bench.phase_hbm_fracs({"fft_x_fwd": 1.0, "fft_y_fwd": 2.0, "spatial_sort": 0.1, "deposit": 0.0},
+                              {"fft_x_fwd": 6.7934e9, "fft_y_fwd": 6.7934e9, "spatial_sort": 0.0,
+                               "deposit": 1e9}, 6793.4)
+    assert set(f) == {"fft_x_fwd", "fft_y_fwd"}
+    assert abs(f["fft_x_fwd"] - 1.0) < 1e-12 and abs(f["fft_y_fwd"] - 0.5) < 1e-12
